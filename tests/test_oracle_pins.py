@@ -1,0 +1,333 @@
+"""Pins for the CPU oracle: facts fixed by the paper's rules and by
+mathematics, independent of the oracle's own code.
+
+  * closed-form firing period of one LIF neuron under constant input
+  * spike arrival along delay chains = sum of the delays (Section 2.1 proxies,
+    Section 2.2 delay registers)
+  * no spike inside a refractory period (Section 2.1)
+  * the matrix formulation with proxy neurons (Section 2.1) and the literal
+    per-synapse shift-register formulation (Section 2.2) give identical rasters
+  * linear superposition of delivered weights against a float64 matrix product
+  * exhaustive brute force on 2-neuron networks
+  * hand-computed pair-based STDP updates and clipping
+  * the published SplitMix64 test vector and the Poisson source rate
+"""
+
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from oracle.formulations import abm_registers, mat_proxy
+from paper_2305_02510_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+MODES = [O.F64, O.F32, O.INT]
+
+
+def single_neuron(theta, leak, reset, refr, inp, steps, dtype):
+    wl = W._base(1, dtype, theta, leak, reset, refr, 1, steps)
+    wl.update(pre=np.zeros(0, np.int32), post=np.zeros(0, np.int32),
+              weight=np.zeros(0), delay=np.zeros(0, np.int32))
+    wl["events"] = dict(step=np.arange(steps, dtype=np.int32),
+                        neuron=np.zeros(steps, np.int32), value=np.full(steps, float(inp)))
+    return wl
+
+
+def closed_form_spikes(theta, leak, reset, refr, inp, steps):
+    """Spike steps of one neuron started at rest under input `inp` per step.
+
+    From rest V = reset: V_k = reset + I + (k-1)(I - leak) while I > leak, so
+    the first crossing after a reset is k* = 1 if reset + I > theta, else
+    floor((theta - reset - I)/(I - leak)) + 2.  With I <= leak the state stays
+    at reset + I.  A spike at t blocks t+1..t+R and the state keeps rising
+    meanwhile, so consecutive spikes are max(k*, R+1) apart."""
+    if reset + inp > theta:
+        k = 1
+    elif inp <= leak:
+        return []
+    else:
+        k = math.floor((theta - reset - inp) / (inp - leak)) + 2
+    period = max(k, refr + 1)
+    return list(range(k - 1, steps, period))
+
+
+CASES = [
+    # theta, leak, reset, R, I
+    (1.0, 0.125, 0.0, 0, 0.25),
+    (1.0, 0.125, 0.0, 3, 0.25),
+    (1.0, 0.125, 0.0, 9, 0.25),
+    (1.0, 0.25, 0.0, 0, 0.25),      # I == leak: never fires
+    (0.5, 0.25, 0.0, 2, 0.75),      # I > theta: fires every R+1
+    (1.0, 0.0, 0.0, 0, 0.5),
+    (1.0, 0.0625, -0.5, 1, 0.375),  # negative reset
+    (3.0, 0.5, 0.0, 0, 0.625),
+]
+INT_CASES = [(10, 1, 0, 1, 3), (10, 1, 0, 0, 11), (20, 1, -5, 4, 2), (7, 2, 0, 0, 2)]
+
+
+@pytest.mark.parametrize("mode", [O.F64, O.F32])
+@pytest.mark.parametrize("case", CASES)
+def test_closed_form_period(case, mode):
+    th, lk, rs, R, I = case
+    steps = 200
+    wl = single_neuron(th, lk, rs, R, I, steps, "f32")
+    _, raster, _ = O.run(wl, mode, steps)
+    got = list(np.nonzero(raster[:, 0])[0])
+    assert got == closed_form_spikes(th, lk, rs, R, I, steps)
+
+
+@pytest.mark.parametrize("case", INT_CASES)
+def test_closed_form_period_int(case):
+    th, lk, rs, R, I = case
+    steps = 300
+    wl = single_neuron(th, lk, rs, R, I, steps, "i32")
+    _, raster, _ = O.run(wl, O.INT, steps)
+    assert list(np.nonzero(raster[:, 0])[0]) == closed_form_spikes(th, lk, rs, R, I, steps)
+
+
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("delays", [[1], [3, 1, 4, 2], [5, 5, 5], [2, 7, 1, 1, 6, 3]])
+def test_delay_chain_arrival(delays, mode):
+    m = len(delays)
+    n = m + 1
+    D = max(delays)
+    dtype = "i32" if mode == O.INT else "f32"
+    wl = W._base(n, dtype, 1, 1, 0, 0, D, 0)
+    wl.update(pre=np.arange(m, dtype=np.int32), post=np.arange(1, n, dtype=np.int32),
+              weight=np.full(m, 2.0), delay=np.array(delays, np.int32))
+    t0 = 5
+    wl["events"] = dict(step=np.array([t0], np.int32), neuron=np.array([0], np.int32),
+                        value=np.array([2.0]))
+    steps = t0 + sum(delays) + 10
+    _, raster, _ = O.run(wl, mode, steps)
+    for k in range(n):
+        assert list(np.nonzero(raster[:, k])[0]) == [t0 + sum(delays[:k])]
+
+
+def _check_isi(raster, refr):
+    for j in range(raster.shape[1]):
+        t = np.nonzero(raster[:, j])[0]
+        if t.size > 1:
+            assert np.diff(t).min() >= refr[j] + 1
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_refractory_invariant_random(seed):
+    wl = W.random_small(seed, integer=bool(seed % 2), steps=300, events_rate=0.5)
+    mode = O.INT if seed % 2 else O.F32
+    _, raster, _ = O.run(wl, mode, 300)
+    _check_isi(raster, wl["refractory"])
+
+
+def test_refractory_invariant_tiny():
+    for integer in (False, True):
+        wl = W.tiny(integer=integer)
+        _, raster, _ = O.run(wl, O.INT if integer else O.F32, 1000)
+        assert raster.sum() > 0
+        _check_isi(raster, wl["refractory"])
+
+
+@pytest.mark.parametrize("block", range(4))
+def test_mat_proxy_matches_oracle(block):
+    """Integer mode: bit-identical rasters and final states on 50 random
+    networks per block (N <= 20, D <= 4, T = 120)."""
+    for seed in range(block * 50, block * 50 + 50):
+        wl = W.random_small(1000 + seed, integer=True, steps=120, events_rate=0.6)
+        st, raster, _ = O.run(wl, O.INT, 120)
+        mraster, mv, mr = mat_proxy(wl, 120, integer=True)
+        assert np.array_equal(raster, mraster), seed
+        assert np.array_equal(st.v, mv.astype(np.float64)), seed
+        assert np.array_equal(st.r, mr), seed
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_abm_registers_match_oracle(seed):
+    wl = W.random_small(2000 + seed, integer=True, steps=80, events_rate=0.6)
+    st, raster, _ = O.run(wl, O.INT, 80)
+    araster, av, ar = abm_registers(wl, 80)
+    assert np.array_equal(raster, araster)
+    assert np.array_equal(st.v, av)
+    assert np.array_equal(st.r, ar)
+
+
+def test_mat_proxy_float_close():
+    """Float64 oracle vs float64 matrix form on float nets: same rasters while
+    no state sits within 1e-9 of its threshold."""
+    for seed in range(20):
+        wl = W.random_small(3000 + seed, integer=False, steps=60, events_rate=0.6)
+        st, raster, _ = O.run(wl, O.F64, 60, record_v=True)
+        mraster, _, _ = mat_proxy(wl, 60, integer=False)
+        bad = np.nonzero((raster != mraster).any(axis=1))[0]
+        if bad.size:
+            t = bad[0]
+            j = np.nonzero(raster[t] != mraster[t])[0]
+            assert np.all(np.abs(st.ctrace[t, j] - wl["threshold"][j]) < 1e-9)
+
+
+@pytest.mark.parametrize("mode", [O.F64, O.INT])
+def test_linear_superposition(mode):
+    """Receivers with an unreachable threshold and no leak accumulate every
+    delivered weight: V_j(T) = sum_k w_k * #{t < T - d_k + 1 : pre_k spiked at t}."""
+    rng = np.random.default_rng(7)
+    nd, nr = 12, 9
+    n = nd + nr
+    m = 80
+    pre = rng.integers(0, nd, m).astype(np.int32)
+    post = rng.integers(nd, n, m).astype(np.int32)
+    delay = rng.integers(1, 6, m).astype(np.int32)
+    integer = mode == O.INT
+    w = rng.integers(-4, 6, m).astype(np.float64) if integer else rng.normal(0, 1, m)
+    th = np.concatenate([np.full(nd, 1.0), np.full(nr, 1e30 if not integer else 2.0**40)])
+    wl = W._base(n, "i32" if integer else "f32", th, 0, 0, 0, 5, 0)
+    wl["leak"][:nd] = 1.0
+    wl.update(pre=pre, post=post, weight=w, delay=delay)
+    T = 150
+    ev_t = rng.integers(0, T, 300).astype(np.int32)
+    ev_j = rng.integers(0, nd, 300).astype(np.int32)
+    wl["events"] = dict(step=ev_t, neuron=ev_j, value=np.full(300, 2.0))
+    st, raster, _ = O.run(wl, mode, T)
+    wq = np.asarray(w, np.float32).astype(np.float64) if not integer else w
+    # counts[k] = spikes of pre_k early enough to arrive by step T-1
+    cum = np.cumsum(raster[:, :nd], axis=0)
+    cnt = np.array([cum[T - 1 - delay[k], pre[k]] if T - 1 - delay[k] >= 0 else 0
+                    for k in range(m)], np.float64)
+    M = np.zeros((m, nr))
+    M[np.arange(m), post - nd] = 1.0
+    expect = (cnt * wq) @ M
+    got = st.v[nd:]
+    if integer:
+        assert np.array_equal(got, expect)
+    else:
+        np.testing.assert_allclose(got, expect, rtol=1e-12, atol=1e-12)
+    assert raster[:, nd:].sum() == 0
+
+
+def test_brute_force_two_neurons():
+    """Every 2-neuron network with synapses 0->1 and/or 1->0, delays 1..3,
+    weights in {-2, 1, 3}, refractory 0/1, leak 0/1: the C oracle and the
+    literal shift-register formulation agree."""
+    rng = np.random.default_rng(3)
+    ev_t = rng.integers(0, 30, 12).astype(np.int32)
+    ev_j = rng.integers(0, 2, 12).astype(np.int32)
+    count = 0
+    for links in ([(0, 1)], [(1, 0)], [(0, 1), (1, 0)], [(0, 1), (0, 1)]):
+        for ds in np.ndindex(*(3,) * len(links)):
+            for ws in np.ndindex(*(3,) * len(links)):
+                for R in (0, 1):
+                    for lk in (0, 1):
+                        wl = W._base(2, "i32", 2, lk, 0, R, 3, 30)
+                        wl.update(pre=np.array([a for a, _ in links], np.int32),
+                                  post=np.array([b for _, b in links], np.int32),
+                                  weight=np.array([(-2, 1, 3)[x] for x in ws], np.float64),
+                                  delay=np.array([d + 1 for d in ds], np.int32))
+                        wl["events"] = dict(step=ev_t, neuron=ev_j, value=np.full(12, 3.0))
+                        _, raster, _ = O.run(wl, O.INT, 30)
+                        araster, _, _ = abm_registers(wl, 30)
+                        assert np.array_equal(raster, araster)
+                        count += 1
+    assert count > 300
+
+
+def _stdp_pair(t_pre, t_post, w0, a_plus=0.01, a_minus=0.012, decay=0.9, steps=30):
+    wl = W._base(2, "f32", 1.0, 10.0, 0.0, 0, 1, steps)
+    wl.update(pre=np.array([0], np.int32), post=np.array([1], np.int32),
+              weight=np.array([w0]), delay=np.array([1], np.int32))
+    wl["events"] = dict(step=np.array([t_pre, t_post], np.int32),
+                        neuron=np.array([0, 1], np.int32), value=np.array([2.0, 2.0]))
+    wl["stdp"] = dict(decay=decay, a_plus=a_plus, a_minus=a_minus, wmin=-1.0, wmax=1.0)
+    st, raster, _ = O.run(wl, O.F64, steps)
+    assert raster[t_pre, 0] == 1 and raster[t_post, 1] == 1
+    return st
+
+
+@pytest.mark.parametrize("dt", [1, 2, 5])
+def test_stdp_pre_before_post(dt):
+    st = _stdp_pair(3, 3 + dt, 0.0)
+    assert st.w[0] == pytest.approx(0.01 * 0.9 ** (dt - 1), rel=1e-12)
+
+
+@pytest.mark.parametrize("dt", [1, 3, 6])
+def test_stdp_post_before_pre(dt):
+    st = _stdp_pair(3 + dt, 3, 0.0)
+    assert st.w[0] == pytest.approx(-0.012 * 0.9 ** (dt - 1), rel=1e-12)
+
+
+def test_stdp_simultaneous_and_clip():
+    assert _stdp_pair(4, 4, 0.0).w[0] == 0.0          # both traces still 0
+    assert _stdp_pair(3, 4, 0.995).w[0] == 1.0        # 0.995 + 0.01 clipped
+    assert _stdp_pair(4, 3, -0.995).w[0] == -1.0      # -0.995 - 0.012 clipped
+
+
+def test_stdp_trace_decay():
+    st = _stdp_pair(2, 9, 0.0, steps=15)
+    # trace of neuron 0 after its spike at 2, read after step 14: 0.9^12
+    assert st.trace[0] == pytest.approx(0.9 ** 12, rel=1e-12)
+    assert st.trace[1] == pytest.approx(0.9 ** 5, rel=1e-12)
+
+
+def test_event_sum_order_fp32():
+    """Explicit events of one (t, j) add in the order given, in float32 when
+    mirroring float: (1e8 + 1) - 1e8 = 0 in float32 but 1 in float64."""
+    wl = W._base(1, "f32", 1e30, 0.0, 0.0, 0, 1, 1)
+    wl.update(pre=np.zeros(0, np.int32), post=np.zeros(0, np.int32),
+              weight=np.zeros(0), delay=np.zeros(0, np.int32))
+    wl["events"] = dict(step=np.zeros(3, np.int32), neuron=np.zeros(3, np.int32),
+                        value=np.array([1e8, 1.0, -1e8]))
+    assert O.run(wl, O.F32, 1)[0].v[0] == 0.0
+    assert O.run(wl, O.F64, 1)[0].v[0] == 1.0
+
+
+def test_splitmix64_published_vector():
+    vals = [int(x) for x in open(os.path.join(GOLDEN, "splitmix64_seed1234567.txt"))
+            if x.strip() and not x.startswith("#")]
+    g = 0x9E3779B97F4A7C15
+    assert [O.splitmix64((1234567 + k * g) % 2**64) for k in range(5)] == vals
+
+
+def test_poisson_rate_and_streams():
+    L = O.lib()
+    thr = int(O.rate_to_u32(0.05))
+    n = 0
+    hits = 0
+    for t in range(200):
+        for j in range(500):
+            hits += L.orc_poisson_u32(99, 3, t, j) < thr
+            n += 1
+    p = hits / n
+    assert abs(p - 0.05) < 5 * math.sqrt(0.05 * 0.95 / n)
+    a = [L.orc_poisson_u32(99, 3, 7, j) for j in range(64)]
+    b = [L.orc_poisson_u32(99, 4, 7, j) for j in range(64)]
+    c = [L.orc_poisson_u32(99, 3, 8, j) for j in range(64)]
+    assert a != b and a != c
+    assert O.rate_to_u32(1.0) == 2**32 - 1 and O.rate_to_u32(0.0) == 0
+
+
+def test_resume_equals_single_run():
+    """Running T steps equals running T1 then T - T1 from the saved state."""
+    wl = W.tiny(integer=False)
+    st, r_all, _ = O.run(wl, O.F32, 400)
+    st1, r1, _ = O.run(wl, O.F32, 150)
+    st2, r2, _ = O.run(wl, O.F32, 250, state=st1)
+    assert np.array_equal(r_all, np.concatenate([r1, r2]))
+    assert np.array_equal(st.v, st2.v)
+
+
+def test_fp32_mirror_tracks_fp64():
+    """The float32 mirror stays within 1e-5 (relative to max(|V|, theta)) of
+    the float64 trajectory until the first step where they spike differently,
+    and that step has a state within 1e-4 * theta of its threshold."""
+    wl = W.tiny(integer=False)
+    s64, r64, v64 = O.run(wl, O.F64, 1000, record_v=True)
+    _, r32, v32 = O.run(wl, O.F32, 1000, record_v=True)
+    diff = np.nonzero((r64 != r32).any(axis=1))[0]
+    end = diff[0] if diff.size else 1000
+    th = np.asarray(wl["threshold"])
+    scale = np.maximum(np.abs(v64[:end]), th)
+    assert np.all(np.abs(v32[:end] - v64[:end]) <= 1e-5 * scale)
+    if diff.size:
+        t = diff[0]
+        j = np.nonzero(r64[t] != r32[t])[0]
+        assert np.all(np.abs(s64.ctrace[t, j] - th[j]) < 1e-4 * th[j])
