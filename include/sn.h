@@ -1,0 +1,217 @@
+/*
+ * sn.h - C ABI of the GB300 spiking-network simulator (libsn.so).
+ *
+ * The library simulates networks of leaky integrate-and-fire (LIF) neurons
+ * joined by synapses that carry a weight and an integer delay, driven by
+ * external input spikes, optionally with pair-based STDP, on one GPU
+ * (sm_103a).  The rules follow SuperNeuro (arXiv 2305.02510):
+ *
+ *   Section 2.1, "The MAT Mode": four neuron parameters (threshold, leak,
+ *     reset state, refractory period); a constant leak that moves the state
+ *     toward the reset state; synapses with a weight and a delay; the order of
+ *     one timestep: leak, add previous spikes times weights, add external
+ *     spikes, compare with the threshold, zero the spikes of refractory
+ *     neurons; built-in STDP.
+ *   Section 2.2, "The ABM Mode": the spike condition is "greater than" the
+ *     threshold; delay registers deliver a spike to the post-neuron after the
+ *     synaptic delay.
+ *
+ * Semantics of one timestep t for neuron j (the library's reading of those
+ * passages, identical to the CPU oracle):
+ *   V_j <- L(V_j) + sum_{synapses i->j, delay d} w * s_i(t - d) + ext_j(t)
+ *   L(V) = max(V - leak, reset) if V > reset; min(V + leak, reset) if V < reset
+ *   s_j(t) = [V_j > threshold_j] and (refractory countdown r_j == 0)
+ *   on a spike: V_j <- reset_j, r_j <- refractory_j; otherwise r_j <- max(r_j - 1, 0)
+ * A spike at step t arrives at t + d (d >= 1).  A neuron that spiked at t
+ * cannot spike at t+1 .. t+refractory.  Initial state: V = reset, r = 0, no
+ * spikes before step 0.  ext_j(t) = (explicit events of (t, j) summed in the
+ * order given) + (amplitude of j's Poisson source if it fires at t).
+ *
+ * Conventions for every entry point:
+ *   - All input arrays are caller-owned host memory and are copied before
+ *     the call returns, unless a parameter says it is a device pointer.
+ *   - The context owns all device memory it allocates; sn_destroy frees it.
+ *   - Work is issued on the context's CUDA stream (sn_config.cuda_stream, or
+ *     the legacy default stream when NULL).  sn_run returns once the work is
+ *     queued; sn_sync waits for it.  Host-buffer getters synchronise.
+ *   - No exception crosses the ABI.  Each call returns an sn_status;
+ *     sn_last_error gives a message for the last failure of a context.
+ *     Device-side failures (a timed-out grid barrier, an integer overflow)
+ *     latch in a device status word and are reported by the next sn_sync or
+ *     getter; after that the context refuses further runs (SN_ESTATE).
+ */
+#ifndef SN_H
+#define SN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sn_ctx sn_ctx;
+
+typedef enum {
+    SN_OK = 0,
+    SN_EINVAL = 1,        /* an argument is out of range or inconsistent       */
+    SN_ENOMEM = 2,        /* a device or host allocation failed                */
+    SN_ECUDA = 3,         /* a CUDA runtime call failed                        */
+    SN_ESTATE = 4,        /* the context is in an error state or wrong kind    */
+    SN_ETIMEOUT = 5,      /* a device-side wait gave up (bounded spin)         */
+    SN_EUNSUPPORTED = 6,  /* valid request this build or context cannot serve  */
+    SN_EOVERFLOW = 7      /* an integer-mode state left the int32 range        */
+} sn_status;
+
+/* Arithmetic of the membrane state. */
+typedef enum {
+    SN_F32 = 0,  /* float state; synaptic sums are exact fixed-point (2^-32)
+                    accumulations rounded once to float, so results do not
+                    depend on thread timing                                  */
+    SN_I32 = 1   /* exact integer state; parameters and weights must be
+                    integral (checked)                                       */
+} sn_dtype;
+
+/* sn_config.flags */
+#define SN_AUTO 0u          /* the library picks the executor                      */
+#define SN_EXEC_CTA 1u      /* force the one-block executor (small networks)       */
+#define SN_EXEC_GRID 2u     /* force the grid-wide persistent executor             */
+
+#define SN_MAX_DELAY 64     /* largest supported synaptic delay                    */
+
+typedef struct {
+    int32_t dtype;          /* sn_dtype                                            */
+    int32_t max_delay;      /* D: every synaptic delay lies in 1..D, D <= 64       */
+    uint32_t flags;         /* SN_AUTO or one SN_EXEC_* value                      */
+    int32_t record_steps;   /* spike-raster capacity in steps (a ring); sn_get_spikes
+                               can return any of the last record_steps steps; 0
+                               means 1                                              */
+    void *cuda_stream;      /* cudaStream_t for all work, NULL = default stream    */
+} sn_config;
+
+/* Neuron parameters, each an array of n values (Section 2.1: threshold, leak,
+ * reset state, refractory period).  In SN_I32 mode the float values must be
+ * integers of magnitude below 2^24.  leak >= 0 and refractory >= 0. */
+typedef struct {
+    int32_t n;
+    const float *threshold;
+    const float *leak;
+    const float *reset;
+    const int32_t *refractory;
+} sn_neurons;
+
+/* Synapse list (Section 2.1: each synapse has a weight and a delay; the
+ * weight matrix has the pre-neuron as row and the post-neuron as column).
+ * Synapse k joins pre[k] -> post[k] with weight[k] and delay[k] in 1..D.
+ * Duplicated pairs are allowed and act as separate synapses.  Neuron
+ * indices must lie in [0, n). */
+typedef struct {
+    int64_t m;
+    const int32_t *pre;
+    const int32_t *post;
+    const float *weight;
+    const int32_t *delay;
+} sn_synapses;
+
+/* Create a network from a synapse list.  The synapses are stored grouped by
+ * pre-neuron (CSR) for event-driven propagation.  Returns SN_EINVAL for an
+ * index, delay or parameter out of range (n < 1, n >= 2^26, D outside 1..64,
+ * non-integral values in SN_I32 mode, NaN weights).  *out is set only on
+ * success. */
+sn_status sn_create(const sn_config *cfg, const sn_neurons *neurons,
+                    const sn_synapses *synapses, sn_ctx **out);
+
+/* Create an all-to-all network from a dense row-major n x n weight matrix
+ * (w[i*n + j] is the weight of i -> j, Section 2.1).  Every synapse has delay
+ * `delay` (1..cfg->max_delay).  The diagonal takes part in propagation like
+ * any entry (pass zeros for no self-synapses) but is never changed by STDP.
+ * Only SN_F32 is supported (SN_EUNSUPPORTED otherwise). */
+sn_status sn_create_dense(const sn_config *cfg, const sn_neurons *neurons,
+                          const float *w, int32_t delay, sn_ctx **out);
+
+/* Replace the explicit external input (Section 2.1, third step of a
+ * timestep): event e adds value[e] to neuron[e] at absolute step step[e] >= 0.
+ * Events of one (step, neuron) are summed in the order given.  nev = 0 clears
+ * the input.  SN_I32 contexts require integral values. */
+sn_status sn_set_input(sn_ctx *ctx, int64_t nev, const int32_t *step,
+                       const int32_t *neuron, const float *value);
+
+/* Replace the Poisson sources.  Source k drives neuron[k] (each neuron at most
+ * once): at absolute step t it adds amplitude[k] when
+ *   u = SplitMix64(key ^ ((t << 32) | j)) >> 32  <  floor(rate[k] * 2^32)
+ * with key = SplitMix64(seed ^ SplitMix64(net)), j the neuron index within its
+ * network and net the network's index (0 for a single network, the train or
+ * network index in batched contexts).  SplitMix64(x) is the published mixer:
+ * z = x + 0x9E3779B97F4A7C15; z = (z ^ z>>30) * 0xBF58476D1CE4E5B9;
+ * z = (z ^ z>>27) * 0x94D049BB133111EB; return z ^ z>>31.  rate is clamped to
+ * [0, 1).  nsrc = 0 clears the sources. */
+sn_status sn_set_poisson(sn_ctx *ctx, int32_t nsrc, const int32_t *neuron,
+                         const float *rate, const float *amplitude, uint64_t seed);
+
+/* Enable (enable = 1) or disable pair-based STDP (Section 2.1 names STDP but
+ * gives no formula; this is the trace form).  Each neuron keeps a trace
+ * x <- decay * x + s after every step.  When i or j spikes at step t, the
+ * weight of every synapse i -> j changes once, from the traces before the
+ * step:  w <- clip(w + A+ * x_i * s_j(t) - A- * x_j * s_i(t), wmin, wmax).
+ * Spike times are emission times (delays do not enter).  The new weight is
+ * used from step t + 1.  Supported for SN_F32 networks (sparse and dense). */
+sn_status sn_stdp(sn_ctx *ctx, float decay, float a_plus, float a_minus,
+                  float wmin, float wmax, int32_t enable);
+
+/* Advance `steps` timesteps (steps >= 0) from the current step.  Queued on the
+ * context's stream; a step counter makes repeated calls continue the run. */
+sn_status sn_run(sn_ctx *ctx, int32_t steps);
+
+/* Wait for queued work; report a latched device status (SN_ETIMEOUT,
+ * SN_EOVERFLOW) if any. */
+sn_status sn_sync(sn_ctx *ctx);
+
+/* Spike raster of steps [t0, t1): row k holds ceil(n/32) 32-bit words for
+ * step t0 + k; bit (j % 32) of word (j / 32) is s_j.  Batched contexts lay
+ * out each network's (or train's) words one after another in every row.
+ * The steps must have been run and lie within the last record_steps steps.
+ * on_device = 1: `bits` is a device pointer and the copy is queued on the
+ * stream; 0: host memory, the call synchronises. */
+sn_status sn_get_spikes(sn_ctx *ctx, int64_t t0, int64_t t1, uint32_t *bits,
+                        int32_t on_device);
+
+/* Current state: v (float, or int32 in SN_I32 mode) and the refractory
+ * countdown r, n values each (batched: concatenated).  Either pointer may be
+ * NULL. */
+sn_status sn_get_state(sn_ctx *ctx, void *v, int32_t *refractory, int32_t on_device);
+
+/* STDP traces x (n floats). */
+sn_status sn_get_trace(sn_ctx *ctx, float *trace, int32_t on_device);
+
+/* Current weights: m floats in the order the synapses were given to
+ * sn_create, or n*n floats row-major for a dense network. */
+sn_status sn_get_weights(sn_ctx *ctx, float *w, int32_t on_device);
+
+/* Steps run so far, total spikes and total synaptic events (one event = one
+ * spike delivered along one synapse), counted on the device. */
+sn_status sn_get_counters(sn_ctx *ctx, int64_t *steps, int64_t *spikes, int64_t *events);
+
+/* Checkpoint: sn_save with buf == NULL stores the needed size in *size;
+ * otherwise it writes the full dynamic state (step counter, V, refractory
+ * countdowns, pending synaptic input, STDP traces, weights, counters) into
+ * buf.  sn_load restores it into a context created with the same network.
+ * A run of T steps equals a run of T1 steps, save, load into a fresh
+ * context, and a run of T - T1 steps. */
+sn_status sn_save(sn_ctx *ctx, void *buf, size_t *size);
+sn_status sn_load(sn_ctx *ctx, const void *buf, size_t size);
+
+/* Message for the last failure of ctx (or of the last failed create call
+ * when ctx is NULL).  Valid until the next call on the same context. */
+const char *sn_last_error(const sn_ctx *ctx);
+
+/* Free the context and its device memory (NULL is ignored). */
+void sn_destroy(sn_ctx *ctx);
+
+/* Library version string. */
+const char *sn_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SN_H */

@@ -1,0 +1,110 @@
+"""Comparison rules between a simulator run and the oracle.
+
+TEST INFRASTRUCTURE ONLY (used by tests/, the smoke check and the benchmark's
+parity probe).  Inputs are plain arrays; nothing here touches the GPU path.
+
+Integer networks: rasters and states must be identical.
+Float networks:   spikes identical except at neurons whose oracle state at the
+                  threshold test lies within NEAR * |theta| of theta; states
+                  within RTOL * max(|V|, |theta|) of the float32 mirror.  After
+                  the first divergence the trajectories are chaotic, so later
+                  steps are checked one at a time from the simulator's own
+                  state (teacher forcing).
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+from . import oracle as O
+
+RTOL = 1e-5
+NEAR = 1e-4
+
+
+class Divergence(AssertionError):
+    pass
+
+
+def _theta(wl):
+    return np.asarray(np.asarray(wl["threshold"], np.float32), np.float64)
+
+
+def check_int_run(wl, raster, v, r, steps, state=None):
+    """Whole-run equality for integer networks.  Returns the oracle state."""
+    st, want, _ = O.run(wl, O.INT, steps, state=state)
+    bad = np.nonzero((raster != want).any(axis=1))[0]
+    if bad.size:
+        t = int(bad[0])
+        j = np.nonzero(raster[t] != want[t])[0][:8]
+        raise Divergence(f"integer raster differs first at step {st.t - steps + t}, neurons {j.tolist()}")
+    if not np.array_equal(np.asarray(v, np.float64), st.v):
+        j = np.nonzero(np.asarray(v, np.float64) != st.v)[0][:8]
+        raise Divergence(f"integer state differs at neurons {j.tolist()}")
+    if not np.array_equal(np.asarray(r), st.r):
+        raise Divergence("refractory countdowns differ")
+    return st
+
+
+def check_float_run(wl, raster, v, r, steps):
+    """Whole-run comparison for float networks.  Returns (first divergence
+    step or None, oracle float32 state).  Raises on a violation."""
+    st, want, _ = O.run(wl, O.F32, steps, record_v=True)
+    th = _theta(wl)
+    bad = np.nonzero((raster != want).any(axis=1))[0]
+    if bad.size == 0:
+        vv = np.asarray(v, np.float64)
+        tol = RTOL * np.maximum(np.abs(st.v), np.abs(th))
+        if not np.all(np.abs(vv - st.v) <= tol):
+            j = int(np.argmax(np.abs(vv - st.v) / tol))
+            raise Divergence(f"state of neuron {j}: {vv[j]!r} vs oracle {st.v[j]!r}")
+        if not np.array_equal(np.asarray(r), st.r):
+            raise Divergence("refractory countdowns differ")
+        return None, st
+    t = int(bad[0])
+    j = np.nonzero(raster[t] != want[t])[0]
+    gap = np.abs(st.ctrace[t, j] - th[j])
+    if not np.all(gap < NEAR * np.abs(th[j])):
+        k = int(np.argmax(gap))
+        raise Divergence(f"spike of neuron {int(j[k])} at step {t} differs with oracle state "
+                         f"{st.ctrace[t, j[k]]!r} not near threshold {th[j[k]]!r}")
+    return t, st
+
+
+def teacher_forced_step(wl, t, v_prev, r_prev, hist_rows, row, v, r, mode,
+                        trace_prev=None, w_prev=None, w=None, trace=None):
+    """One oracle step t from the simulator's state after step t-1, compared
+    with the simulator's step t.  hist_rows: spikes of steps t-D .. t-1 as
+    uint8 [D, n].  Returns the number of spikes compared."""
+    st = O.state_from(wl, t, v_prev, r_prev, hist_rows, trace=trace_prev, w=w_prev)
+    st, want, _ = O.run(wl, mode, 1, state=st, record_v=True)
+    th = _theta(wl)
+    if mode == O.INT:
+        assert np.array_equal(row, want[0]), f"step {t}: integer spikes differ"
+        assert np.array_equal(np.asarray(v, np.float64), st.v), f"step {t}: integer state differs"
+        assert np.array_equal(np.asarray(r), st.r)
+        return int(want[0].sum())
+    diff = np.nonzero(row != want[0])[0]
+    if diff.size:
+        gap = np.abs(st.ctrace[0, diff] - th[diff])
+        if not np.all(gap < NEAR * np.abs(th[diff])):
+            k = int(np.argmax(gap))
+            raise Divergence(f"teacher-forced step {t}: neuron {int(diff[k])} spike differs, oracle "
+                             f"state {st.ctrace[0, diff[k]]!r} vs threshold {th[diff[k]]!r}")
+    same = np.ones(row.shape, bool)
+    same[diff] = False
+    vv = np.asarray(v, np.float64)
+    tol = RTOL * np.maximum(np.abs(st.v), np.abs(th))
+    ok = (np.abs(vv - st.v) <= tol) | ~same
+    if not np.all(ok):
+        j = int(np.nonzero(~ok)[0][0])
+        raise Divergence(f"teacher-forced step {t}: state of neuron {j}: {vv[j]!r} vs {st.v[j]!r}")
+    assert np.array_equal(np.asarray(r)[same], st.r[same])
+    if w is not None:
+        # weights changed by STDP: identical where both sides saw the same spikes
+        ww = np.asarray(w, np.float64).reshape(-1)
+        if diff.size == 0:
+            assert np.array_equal(ww, st.w), f"step {t}: STDP weights differ"
+    if trace is not None and diff.size == 0:
+        assert np.array_equal(np.asarray(trace, np.float64), st.trace), f"step {t}: traces differ"
+    return int(want[0].sum())

@@ -164,7 +164,8 @@ def run(wl, mode: int, steps: int, state: State | None = None, record_v: bool = 
     net.nev, net.ev_step, net.ev_neuron, net.ev_value = es.size, _p(es), _p(en), _p(evv)
     po = wl["poisson"]
     sn = np.ascontiguousarray(po["neuron"], np.int32)
-    su = rate_to_u32(po["rate"])
+    # sn_set_poisson takes the rate as a float32: threshold of the rounded rate
+    su = rate_to_u32(np.asarray(po["rate"], np.float32).astype(np.float64))
     sa = f(po["amplitude"])
     keep += [sn, su, sa]
     net.nsrc, net.src_neuron, net.src_rate_u32, net.src_amp = sn.size, _p(sn), _p(su), _p(sa)

@@ -1,0 +1,731 @@
+// Host side of the C ABI declared in include/sn.h: argument checking, network
+// construction on the device, executor sizing, launches, getters and
+// checkpoints.  All device memory of a context is allocated here at creation
+// (or when inputs / STDP are configured) and freed by sn_destroy; sn_run
+// allocates nothing.
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sn_internal.h"
+
+using namespace sn;
+
+struct sn_ctx {
+    int kind = KIND_SPARSE;
+    int dtype = SN_F32;
+    int n = 0;
+    int D = 1, D1 = 2;
+    unsigned flags = 0;
+    int cap = 1, words = 1;
+    cudaStream_t stream = nullptr;
+    long long step = 0;            // steps run so far (absolute step of the next run)
+    long long raster_from = 0;     // first step whose raster row is valid
+    long long m = 0;
+    bool all_delay_one = true;
+    int dense_delay = 1;
+    // executor
+    int grid = 1, block = 256, chunk = 32, S = 1;
+    // device memory
+    void *V = nullptr;
+    int *r = nullptr;
+    void *th = nullptr, *lk = nullptr, *rs = nullptr;
+    int *R = nullptr;
+    unsigned *prate = nullptr;
+    void *pamp = nullptr;
+    unsigned long long pkey = 0;
+    int *ev_off = nullptr, *ev_neuron = nullptr;
+    void *ev_val = nullptr;
+    int ev_nsteps = 0;
+    long long *rowptr = nullptr;
+    uint2 *syn = nullptr;
+    long long *colptr = nullptr;
+    uint2 *csc = nullptr;
+    long long *perm_inv = nullptr;  // input index -> CSR position (device)
+    void *ring = nullptr;
+    size_t ring_bytes = 0;
+    float *W = nullptr, *partial = nullptr;
+    unsigned *raster = nullptr;
+    float *trace = nullptr;
+    Control *ctl = nullptr;
+    // host copies
+    std::vector<long long> h_perm_inv;
+    // STDP
+    int stdp = 0;
+    float decay = 0, a_plus = 0, a_minus = 0, wmin = 0, wmax = 0;
+    int failed = 0;                // sticky device failure seen
+    std::string err;
+    std::vector<void *> allocs;
+};
+
+static thread_local std::string g_create_err;
+
+namespace {
+
+sn_status fail(sn_ctx *c, sn_status s, const std::string &msg) {
+    if (c) c->err = msg; else g_create_err = msg;
+    return s;
+}
+
+sn_status cuda_fail(sn_ctx *c, cudaError_t e, const char *what) {
+    return fail(c, SN_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define SN_CUDA(ctx, call)                                           \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);   \
+    } while (0)
+
+template <typename T>
+sn_status dalloc(sn_ctx *c, T **p, size_t bytes) {
+    void *q = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(c, SN_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    }
+    c->allocs.push_back(q);
+    *p = (T *)q;
+    return SN_OK;
+}
+
+void dfree(sn_ctx *c, void *p) {
+    if (!p) return;
+    auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
+    if (it != c->allocs.end()) c->allocs.erase(it);
+    cudaFree(p);
+}
+
+bool is_int_valued(float x) { return std::isfinite(x) && std::floor(x) == x && std::fabs(x) < 16777216.0f; }
+
+unsigned long long splitmix64(unsigned long long x) {
+    unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+unsigned rate_threshold(float rate) {
+    double r = std::floor((double)rate * 4294967296.0);
+    if (!(r > 0)) return 0u;
+    if (r > 4294967295.0) return 4294967295u;
+    return (unsigned)r;
+}
+
+sn_status check_config(const sn_config *cfg) {
+    if (!cfg) return fail(nullptr, SN_EINVAL, "cfg is NULL");
+    if (cfg->dtype != SN_F32 && cfg->dtype != SN_I32) return fail(nullptr, SN_EINVAL, "bad dtype");
+    if (cfg->max_delay < 1 || cfg->max_delay > SN_MAX_DELAY)
+        return fail(nullptr, SN_EINVAL, "max_delay must be in 1..64");
+    if (cfg->record_steps < 0) return fail(nullptr, SN_EINVAL, "record_steps < 0");
+    if (cfg->flags & ~(SN_EXEC_CTA | SN_EXEC_GRID)) return fail(nullptr, SN_EINVAL, "unknown flags");
+    if ((cfg->flags & SN_EXEC_CTA) && (cfg->flags & SN_EXEC_GRID))
+        return fail(nullptr, SN_EINVAL, "SN_EXEC_CTA and SN_EXEC_GRID are exclusive");
+    return SN_OK;
+}
+
+// Neuron parameters to device arrays (float or int32 according to dtype).
+sn_status upload_neurons(sn_ctx *c, const sn_neurons *nr) {
+    const int n = c->n;
+    if (!nr->threshold || !nr->leak || !nr->reset || !nr->refractory)
+        return fail(nullptr, SN_EINVAL, "neuron parameter array is NULL");
+    for (int j = 0; j < n; ++j) {
+        const bool th_inf = std::isinf(nr->threshold[j]) && nr->threshold[j] > 0;
+        if (!std::isfinite(nr->threshold[j]) && !th_inf)
+            return fail(nullptr, SN_EINVAL, "threshold must not be NaN or -inf");
+        if (!std::isfinite(nr->leak[j]) || nr->leak[j] < 0)
+            return fail(nullptr, SN_EINVAL, "leak must be finite and >= 0");
+        if (!std::isfinite(nr->reset[j])) return fail(nullptr, SN_EINVAL, "reset must be finite");
+        if (nr->refractory[j] < 0) return fail(nullptr, SN_EINVAL, "refractory must be >= 0");
+        if (c->dtype == SN_I32 &&
+            !((th_inf || is_int_valued(nr->threshold[j])) && is_int_valued(nr->leak[j]) &&
+              is_int_valued(nr->reset[j])))
+            return fail(nullptr, SN_EINVAL, "SN_I32 parameters must be integers below 2^24");
+    }
+    const size_t vb = (size_t)n * 4;
+    sn_status s;
+    if ((s = dalloc(c, &c->V, vb)) || (s = dalloc(c, &c->r, vb)) || (s = dalloc(c, &c->th, vb)) ||
+        (s = dalloc(c, &c->lk, vb)) || (s = dalloc(c, &c->rs, vb)) || (s = dalloc(c, &c->R, vb)) ||
+        (s = dalloc(c, &c->prate, vb)) || (s = dalloc(c, &c->pamp, vb)))
+        return fail(nullptr, s, "neuron arrays: " + c->err);
+    // +inf thresholds in integer mode become INT32_MAX: V > INT32_MAX never holds
+    auto up = [&](void *dst, const float *src) -> cudaError_t {
+        if (c->dtype == SN_F32) return cudaMemcpy(dst, src, vb, cudaMemcpyHostToDevice);
+        std::vector<int> tmp(n);
+        for (int j = 0; j < n; ++j) tmp[j] = std::isinf(src[j]) ? 2147483647 : (int)src[j];
+        return cudaMemcpy(dst, tmp.data(), vb, cudaMemcpyHostToDevice);
+    };
+    cudaError_t e;
+    if ((e = up(c->th, nr->threshold)) || (e = up(c->lk, nr->leak)) || (e = up(c->rs, nr->reset)) ||
+        (e = up(c->V, nr->reset)) ||
+        (e = cudaMemcpy(c->R, nr->refractory, vb, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemset(c->r, 0, vb)) || (e = cudaMemset(c->prate, 0, vb)) ||
+        (e = cudaMemset(c->pamp, 0, vb)))
+        return fail(nullptr, SN_ECUDA, std::string("neuron upload: ") + cudaGetErrorString(e));
+    return SN_OK;
+}
+
+sn_status alloc_common(sn_ctx *c, const sn_config *cfg) {
+    c->cap = cfg->record_steps > 0 ? cfg->record_steps : 1;
+    c->words = (c->n + 31) / 32;
+    sn_status s;
+    if ((s = dalloc(c, &c->raster, (size_t)c->cap * c->words * 4)) || (s = dalloc(c, &c->ctl, sizeof(Control))))
+        return fail(nullptr, s, c->err);
+    cudaError_t e;
+    if ((e = cudaMemset(c->raster, 0, (size_t)c->cap * c->words * 4)) ||
+        (e = cudaMemset(c->ctl, 0, sizeof(Control))))
+        return fail(nullptr, SN_ECUDA, cudaGetErrorString(e));
+    return SN_OK;
+}
+
+void destroy_all(sn_ctx *c) {
+    for (void *p : c->allocs) cudaFree(p);
+    c->allocs.clear();
+}
+
+sn_status size_sparse_executor(sn_ctx *c) {
+    const int n = c->n;
+    c->block = 256;
+    const bool cta = (c->flags & SN_EXEC_CTA) || (!(c->flags & SN_EXEC_GRID) && n <= 2048);
+    if (cta) {
+        c->grid = 1;
+        c->chunk = (n + 31) / 32 * 32;
+        if (c->chunk > 16384) return fail(nullptr, SN_EINVAL, "SN_EXEC_CTA supports n <= 16384");
+        return SN_OK;
+    }
+    int gmax = 0;
+    cudaError_t e = max_grid_sparse(c->dtype, 1, c->block, &gmax);
+    if (e != cudaSuccess) return fail(nullptr, SN_ECUDA, std::string("occupancy: ") + cudaGetErrorString(e));
+    if (gmax < 1) return fail(nullptr, SN_ECUDA, "no resident blocks possible");
+    int g = std::min(gmax, (n + 31) / 32);
+    int chunk = ((n + g - 1) / g + 31) / 32 * 32;
+    if (chunk > 1024) return fail(nullptr, SN_EUNSUPPORTED, "network too large for the grid executor");
+    c->chunk = chunk;
+    c->grid = (n + chunk - 1) / chunk;
+    return SN_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sn_version(void) { return "sn-gb300 0.1 (sm_103a)"; }
+
+const char *sn_last_error(const sn_ctx *ctx) {
+    return ctx ? ctx->err.c_str() : g_create_err.c_str();
+}
+
+sn_status sn_create(const sn_config *cfg, const sn_neurons *nr, const sn_synapses *sy, sn_ctx **out) {
+    sn_status s = check_config(cfg);
+    if (s) return s;
+    if (!nr || !sy || !out) return fail(nullptr, SN_EINVAL, "NULL argument");
+    const int n = nr->n;
+    if (n < 1 || n >= (1 << kPostBits)) return fail(nullptr, SN_EINVAL, "n must be in 1 .. 2^26-1");
+    if (sy->m < 0) return fail(nullptr, SN_EINVAL, "m < 0");
+    if (sy->m > 0 && (!sy->pre || !sy->post || !sy->weight || !sy->delay))
+        return fail(nullptr, SN_EINVAL, "synapse array is NULL");
+    const long long m = sy->m;
+    bool all1 = true;
+    for (long long k = 0; k < m; ++k) {
+        if (sy->pre[k] < 0 || sy->pre[k] >= n || sy->post[k] < 0 || sy->post[k] >= n)
+            return fail(nullptr, SN_EINVAL, "synapse " + std::to_string(k) + ": neuron index out of range");
+        if (sy->delay[k] < 1 || sy->delay[k] > cfg->max_delay)
+            return fail(nullptr, SN_EINVAL, "synapse " + std::to_string(k) + ": delay outside 1..max_delay");
+        const float w = sy->weight[k];
+        if (!std::isfinite(w) || std::fabs(w) > 1e9f)
+            return fail(nullptr, SN_EINVAL, "synapse " + std::to_string(k) + ": weight not finite or too large");
+        if (cfg->dtype == SN_I32 && !is_int_valued(w))
+            return fail(nullptr, SN_EINVAL, "SN_I32 weights must be integers below 2^24");
+        if (sy->delay[k] != 1) all1 = false;
+    }
+    sn_ctx *c = new (std::nothrow) sn_ctx();
+    if (!c) return fail(nullptr, SN_ENOMEM, "host allocation failed");
+    c->kind = KIND_SPARSE;
+    c->dtype = cfg->dtype;
+    c->n = n;
+    c->D = cfg->max_delay;
+    c->D1 = c->D + 1;
+    c->flags = cfg->flags;
+    c->m = m;
+    c->all_delay_one = all1;
+    c->stream = (cudaStream_t)cfg->cuda_stream;
+    auto bail = [&](sn_status st) { std::string msg = c->err.empty() ? g_create_err : c->err;
+                                    destroy_all(c); delete c; g_create_err = msg; return st; };
+    if ((s = upload_neurons(c, nr))) return bail(s);
+    if ((s = alloc_common(c, cfg))) return bail(s);
+    // CSR by pre-neuron, input order kept within a row
+    std::vector<long long> rowptr(n + 1, 0);
+    for (long long k = 0; k < m; ++k) rowptr[sy->pre[k] + 1]++;
+    for (int i = 0; i < n; ++i) rowptr[i + 1] += rowptr[i];
+    std::vector<uint2> syn(m > 0 ? m : 1);
+    c->h_perm_inv.assign(m, 0);
+    {
+        std::vector<long long> fill(rowptr.begin(), rowptr.end() - 1);
+        for (long long k = 0; k < m; ++k) {
+            const long long p = fill[sy->pre[k]]++;
+            uint2 e;
+            e.x = (unsigned)sy->post[k] | ((unsigned)(sy->delay[k] - 1) << kPostBits);
+            if (cfg->dtype == SN_F32) { float w = sy->weight[k]; memcpy(&e.y, &w, 4); }
+            else { int w = (int)sy->weight[k]; memcpy(&e.y, &w, 4); }
+            syn[p] = e;
+            c->h_perm_inv[k] = p;
+        }
+    }
+    c->ring_bytes = (size_t)c->D1 * n * (cfg->dtype == SN_F32 ? 8 : 4);
+    if ((s = dalloc(c, &c->rowptr, (size_t)(n + 1) * 8)) || (s = dalloc(c, &c->syn, (size_t)(m > 0 ? m : 1) * 8)) ||
+        (s = dalloc(c, &c->ring, c->ring_bytes)))
+        return bail(s);
+    cudaError_t e;
+    if ((e = cudaMemcpy(c->rowptr, rowptr.data(), (size_t)(n + 1) * 8, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemcpy(c->syn, syn.data(), (size_t)(m > 0 ? m : 1) * 8, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemset(c->ring, 0, c->ring_bytes))) {
+        c->err = std::string("upload: ") + cudaGetErrorString(e);
+        return bail(SN_ECUDA);
+    }
+    if ((s = size_sparse_executor(c))) return bail(s);
+    *out = c;
+    return SN_OK;
+}
+
+sn_status sn_create_dense(const sn_config *cfg, const sn_neurons *nr, const float *w, int32_t delay,
+                          sn_ctx **out) {
+    sn_status s = check_config(cfg);
+    if (s) return s;
+    if (!nr || !w || !out) return fail(nullptr, SN_EINVAL, "NULL argument");
+    if (cfg->dtype != SN_F32) return fail(nullptr, SN_EUNSUPPORTED, "dense networks are SN_F32 only");
+    const int n = nr->n;
+    if (n < 1 || n > 200000) return fail(nullptr, SN_EINVAL, "dense n must be in 1 .. 200000");
+    if (delay < 1 || delay > cfg->max_delay) return fail(nullptr, SN_EINVAL, "delay outside 1..max_delay");
+    const size_t nn = (size_t)n * n;
+    for (size_t q = 0; q < nn; ++q)
+        if (!std::isfinite(w[q]) || std::fabs(w[q]) > 1e9f) return fail(nullptr, SN_EINVAL, "weight not finite");
+    sn_ctx *c = new (std::nothrow) sn_ctx();
+    if (!c) return fail(nullptr, SN_ENOMEM, "host allocation failed");
+    c->kind = KIND_DENSE;
+    c->dtype = SN_F32;
+    c->n = n;
+    c->D = cfg->max_delay;
+    c->D1 = c->D + 1;
+    c->flags = cfg->flags;
+    c->m = (long long)nn;
+    c->dense_delay = delay;
+    c->all_delay_one = delay == 1;
+    c->stream = (cudaStream_t)cfg->cuda_stream;
+    auto bail = [&](sn_status st) { std::string msg = c->err.empty() ? g_create_err : c->err;
+                                    destroy_all(c); delete c; g_create_err = msg; return st; };
+    if ((s = upload_neurons(c, nr))) return bail(s);
+    if ((s = alloc_common(c, cfg))) return bail(s);
+    // executor: one block per 32-aligned neuron chunk for the update, work
+    // items (column tile x spike chunk) for the gather
+    c->block = 256;
+    size_t smem_words = (size_t)c->words;
+    int gmax = 0;
+    cudaError_t e = max_grid_dense(c->block, &gmax, &smem_words);
+    if (e != cudaSuccess) { c->err = std::string("occupancy: ") + cudaGetErrorString(e); return bail(SN_ECUDA); }
+    if (gmax < 1) { c->err = "dense executor: no resident blocks"; return bail(SN_EUNSUPPORTED); }
+    const bool cta = (cfg->flags & SN_EXEC_CTA) != 0;
+    int g = cta ? 1 : std::min(gmax, (n + 31) / 32);
+    c->chunk = ((n + g - 1) / g + 31) / 32 * 32;
+    if (c->chunk > 2048) { c->err = "dense executor: chunk too large"; return bail(SN_EUNSUPPORTED); }
+    c->grid = cta ? 1 : gmax;          // every resident block takes gather items
+    const int ntile = (n + 1023) / 1024;
+    c->S = std::max(1, (c->grid + ntile - 1) / ntile);
+    c->ring_bytes = (size_t)c->D1 * n * 4;
+    if ((s = dalloc(c, &c->W, nn * 4)) || (s = dalloc(c, &c->partial, (size_t)c->S * n * 4)) ||
+        (s = dalloc(c, &c->ring, c->ring_bytes)))
+        return bail(s);
+    if ((e = cudaMemcpy(c->W, w, nn * 4, cudaMemcpyHostToDevice)) ||
+        (e = cudaMemset(c->partial, 0, (size_t)c->S * n * 4)) || (e = cudaMemset(c->ring, 0, c->ring_bytes))) {
+        c->err = std::string("upload: ") + cudaGetErrorString(e);
+        return bail(SN_ECUDA);
+    }
+    *out = c;
+    return SN_OK;
+}
+
+sn_status sn_set_input(sn_ctx *c, int64_t nev, const int32_t *step, const int32_t *neuron, const float *value) {
+    if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
+    if (c->kind != KIND_SPARSE && c->kind != KIND_DENSE) return fail(c, SN_ESTATE, "explicit events: single networks only");
+    if (nev < 0 || (nev > 0 && (!step || !neuron || !value))) return fail(c, SN_EINVAL, "bad event arrays");
+    int max_step = -1;
+    for (long long e = 0; e < nev; ++e) {
+        if (step[e] < 0 || step[e] >= (1 << 27)) return fail(c, SN_EINVAL, "event step outside 0 .. 2^27-1");
+        if (neuron[e] < 0 || neuron[e] >= c->n) return fail(c, SN_EINVAL, "event neuron out of range");
+        if (!std::isfinite(value[e])) return fail(c, SN_EINVAL, "event value not finite");
+        if (c->dtype == SN_I32 && !is_int_valued(value[e])) return fail(c, SN_EINVAL, "SN_I32 event values must be integers");
+        max_step = std::max(max_step, (int)step[e]);
+    }
+    // stable order by (step, neuron); values of one (step, neuron) summed in input order
+    std::vector<long long> idx(nev);
+    for (long long e = 0; e < nev; ++e) idx[e] = e;
+    std::stable_sort(idx.begin(), idx.end(), [&](long long a, long long b) {
+        return step[a] != step[b] ? step[a] < step[b] : neuron[a] < neuron[b];
+    });
+    std::vector<int> off(max_step + 2, 0), nu;
+    std::vector<float> vf;
+    std::vector<int> vi;
+    for (long long q = 0; q < nev;) {
+        long long e = idx[q];
+        const int st = step[e], j = neuron[e];
+        float sf = value[e];
+        long long si = (long long)value[e];
+        ++q;
+        while (q < nev && step[idx[q]] == st && neuron[idx[q]] == j) {
+            sf = sf + value[idx[q]];        // float addition in the order given
+            si += (long long)value[idx[q]];
+            ++q;
+        }
+        if (c->dtype == SN_I32 && (si > 2147483647ll || si < -2147483648ll))
+            return fail(c, SN_EINVAL, "summed integer event value overflows int32");
+        off[st + 1]++;
+        nu.push_back(j);
+        vf.push_back(sf);
+        vi.push_back((int)si);
+    }
+    for (int t = 0; t <= max_step; ++t) off[t + 1] += off[t];
+    dfree(c, c->ev_off); dfree(c, c->ev_neuron); dfree(c, c->ev_val);
+    c->ev_off = c->ev_neuron = nullptr;
+    c->ev_val = nullptr;
+    c->ev_nsteps = 0;
+    if (nev == 0) return SN_OK;
+    sn_status s;
+    const size_t ne = nu.size();
+    if ((s = dalloc(c, &c->ev_off, off.size() * 4)) || (s = dalloc(c, &c->ev_neuron, ne * 4)) ||
+        (s = dalloc(c, &c->ev_val, ne * 4)))
+        return s;
+    SN_CUDA(c, cudaMemcpy(c->ev_off, off.data(), off.size() * 4, cudaMemcpyHostToDevice));
+    SN_CUDA(c, cudaMemcpy(c->ev_neuron, nu.data(), ne * 4, cudaMemcpyHostToDevice));
+    SN_CUDA(c, cudaMemcpy(c->ev_val, c->dtype == SN_F32 ? (const void *)vf.data() : (const void *)vi.data(),
+                          ne * 4, cudaMemcpyHostToDevice));
+    c->ev_nsteps = max_step + 1;
+    return SN_OK;
+}
+
+sn_status sn_set_poisson(sn_ctx *c, int32_t nsrc, const int32_t *neuron, const float *rate,
+                         const float *amp, uint64_t seed) {
+    if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
+    if (c->kind != KIND_SPARSE && c->kind != KIND_DENSE) return fail(c, SN_ESTATE, "wrong context kind");
+    if (nsrc < 0 || (nsrc > 0 && (!neuron || !rate || !amp))) return fail(c, SN_EINVAL, "bad source arrays");
+    const int n = c->n;
+    std::vector<unsigned> thr(n, 0u);
+    std::vector<float> af(n, 0.0f);
+    std::vector<int> ai(n, 0);
+    std::vector<char> used(n, 0);
+    for (int k = 0; k < nsrc; ++k) {
+        const int j = neuron[k];
+        if (j < 0 || j >= n) return fail(c, SN_EINVAL, "source neuron out of range");
+        if (used[j]) return fail(c, SN_EINVAL, "a neuron may have at most one Poisson source");
+        if (!(rate[k] >= 0.0f) || !std::isfinite(rate[k])) return fail(c, SN_EINVAL, "rate must be finite and >= 0");
+        if (!std::isfinite(amp[k])) return fail(c, SN_EINVAL, "amplitude not finite");
+        if (c->dtype == SN_I32 && !is_int_valued(amp[k])) return fail(c, SN_EINVAL, "SN_I32 amplitudes must be integers");
+        used[j] = 1;
+        thr[j] = rate_threshold(rate[k]);
+        af[j] = amp[k];
+        ai[j] = (int)amp[k];
+    }
+    SN_CUDA(c, cudaMemcpy(c->prate, thr.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
+    SN_CUDA(c, cudaMemcpy(c->pamp, c->dtype == SN_F32 ? (const void *)af.data() : (const void *)ai.data(),
+                          (size_t)n * 4, cudaMemcpyHostToDevice));
+    c->pkey = splitmix64(seed ^ splitmix64(0ull));
+    return SN_OK;
+}
+
+sn_status sn_stdp(sn_ctx *c, float decay, float a_plus, float a_minus, float wmin, float wmax, int32_t enable) {
+    if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
+    if (c->kind != KIND_SPARSE && c->kind != KIND_DENSE) return fail(c, SN_ESTATE, "wrong context kind");
+    if (!enable) { c->stdp = 0; return SN_OK; }
+    if (c->dtype != SN_F32) return fail(c, SN_EUNSUPPORTED, "STDP needs an SN_F32 network");
+    if (!c->all_delay_one)
+        return fail(c, SN_EUNSUPPORTED, "STDP needs every synaptic delay to be 1 (weights apply at emission)");
+    if (!(std::isfinite(decay) && std::isfinite(a_plus) && std::isfinite(a_minus) && std::isfinite(wmin) &&
+          std::isfinite(wmax) && wmin <= wmax))
+        return fail(c, SN_EINVAL, "bad STDP parameters");
+    if (!c->trace) {
+        sn_status s = dalloc(c, &c->trace, (size_t)2 * c->n * 4);
+        if (s) return s;
+        SN_CUDA(c, cudaMemset(c->trace, 0, (size_t)2 * c->n * 4));
+    }
+    if (c->kind == KIND_SPARSE && !c->csc) {
+        // CSC by post: {pre, CSR position}
+        const int n = c->n;
+        const long long m = c->m;
+        std::vector<uint2> syn(m > 0 ? m : 1);
+        std::vector<long long> rowptr(n + 1);
+        SN_CUDA(c, cudaMemcpy(syn.data(), c->syn, (size_t)(m > 0 ? m : 1) * 8, cudaMemcpyDeviceToHost));
+        SN_CUDA(c, cudaMemcpy(rowptr.data(), c->rowptr, (size_t)(n + 1) * 8, cudaMemcpyDeviceToHost));
+        if (m >= (1ll << 32)) return fail(c, SN_EUNSUPPORTED, "STDP supports m < 2^32");
+        std::vector<long long> colptr(n + 1, 0);
+        for (long long p = 0; p < m; ++p) colptr[(syn[p].x & kPostMask) + 1]++;
+        for (int j = 0; j < n; ++j) colptr[j + 1] += colptr[j];
+        std::vector<uint2> csc(m > 0 ? m : 1);
+        std::vector<long long> fill(colptr.begin(), colptr.end() - 1);
+        for (int i = 0; i < n; ++i)
+            for (long long p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+                const int j = (int)(syn[p].x & kPostMask);
+                csc[fill[j]++] = make_uint2((unsigned)i, (unsigned)p);
+            }
+        sn_status s;
+        if ((s = dalloc(c, &c->colptr, (size_t)(n + 1) * 8)) || (s = dalloc(c, &c->csc, (size_t)(m > 0 ? m : 1) * 8)))
+            return s;
+        SN_CUDA(c, cudaMemcpy(c->colptr, colptr.data(), (size_t)(n + 1) * 8, cudaMemcpyHostToDevice));
+        SN_CUDA(c, cudaMemcpy(c->csc, csc.data(), (size_t)(m > 0 ? m : 1) * 8, cudaMemcpyHostToDevice));
+    }
+    c->stdp = 1;
+    c->decay = decay; c->a_plus = a_plus; c->a_minus = a_minus; c->wmin = wmin; c->wmax = wmax;
+    return SN_OK;
+}
+
+static sn_status read_status(sn_ctx *c) {
+    Control h;
+    SN_CUDA(c, cudaMemcpy(&h, c->ctl, sizeof(Control), cudaMemcpyDeviceToHost));
+    if (h.status != 0) {
+        c->failed = h.status;
+        return fail(c, (sn_status)h.status, h.status == SN_ETIMEOUT ? "a grid barrier wait timed out on the device"
+                                            : h.status == SN_EOVERFLOW ? "integer state overflowed int32"
+                                                                       : "device status latched");
+    }
+    return SN_OK;
+}
+
+sn_status sn_run(sn_ctx *c, int32_t steps) {
+    if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
+    if (c->failed) return fail(c, SN_ESTATE, "context has a latched device error");
+    if (steps < 0) return fail(c, SN_EINVAL, "steps < 0");
+    if (steps == 0) return SN_OK;
+    if (c->step + steps >= (1ll << 31)) return fail(c, SN_EINVAL, "step counter would exceed 2^31");
+    if (c->kind != KIND_SPARSE && c->kind != KIND_DENSE) return fail(c, SN_ESTATE, "wrong context kind");
+    NetArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n = c->n; a.D1 = c->D1; a.words = c->words; a.cap = c->cap;
+    a.t0 = (int)c->step; a.steps = steps; a.chunk = c->chunk;
+    a.V = c->V; a.r = c->r; a.th = c->th; a.lk = c->lk; a.rs = c->rs; a.R = c->R;
+    a.prate = c->prate; a.pamp = c->pamp; a.pkey = c->pkey;
+    a.ev_off = c->ev_off; a.ev_nsteps = c->ev_nsteps; a.ev_neuron = c->ev_neuron; a.ev_val = c->ev_val;
+    a.rowptr = c->rowptr; a.syn = c->syn; a.colptr = c->colptr; a.csc = c->csc;
+    a.ring = c->ring;
+    a.W = c->W; a.partial = c->partial; a.S = c->S; a.dense_delay = c->dense_delay;
+    a.raster = c->raster;
+    a.stdp = c->stdp; a.decay = c->decay; a.a_plus = c->a_plus; a.a_minus = c->a_minus;
+    a.wmin = c->wmin; a.wmax = c->wmax; a.trace = c->trace;
+    a.ctl = c->ctl;
+    cudaError_t e = c->kind == KIND_SPARSE ? launch_sparse(a, c->dtype, c->grid, c->block, c->stream)
+                                           : launch_dense(a, c->grid, c->block, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "simulation launch");
+    c->step += steps;
+    if (c->step - c->raster_from > c->cap) c->raster_from = c->step - c->cap;
+    return SN_OK;
+}
+
+sn_status sn_sync(sn_ctx *c) {
+    if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
+    SN_CUDA(c, cudaStreamSynchronize(c->stream));
+    return read_status(c);
+}
+
+static sn_status copy_out(sn_ctx *c, void *dst, const void *src, size_t bytes, int on_device) {
+    if (on_device) {
+        SN_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, c->stream));
+        return SN_OK;
+    }
+    SN_CUDA(c, cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, c->stream));
+    SN_CUDA(c, cudaStreamSynchronize(c->stream));
+    return read_status(c);
+}
+
+sn_status sn_get_spikes(sn_ctx *c, int64_t t0, int64_t t1, uint32_t *bits, int32_t on_device) {
+    if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
+    if (t0 < 0 || t1 < t0 || t1 > c->step) return fail(c, SN_EINVAL, "steps not yet run");
+    if (t0 < c->raster_from) return fail(c, SN_EINVAL, "steps older than the raster capacity (record_steps)");
+    if (t1 == t0) return SN_OK;
+    if (!bits) return fail(c, SN_EINVAL, "bits is NULL");
+    const size_t row = (size_t)c->words * 4;
+    // rows are a ring indexed by step % cap: copy the contiguous pieces
+    long long t = t0;
+    while (t < t1) {
+        const long long slot = t % c->cap;
+        const long long len = std::min<long long>(t1 - t, c->cap - slot);
+        uint8_t *dst = (uint8_t *)bits + (size_t)(t - t0) * row;
+        const uint8_t *src = (const uint8_t *)c->raster + (size_t)slot * row;
+        cudaError_t e = cudaMemcpyAsync(dst, src, (size_t)len * row,
+                                        on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "raster copy");
+        t += len;
+    }
+    if (on_device) return SN_OK;
+    SN_CUDA(c, cudaStreamSynchronize(c->stream));
+    return read_status(c);
+}
+
+sn_status sn_get_state(sn_ctx *c, void *v, int32_t *refr, int32_t on_device) {
+    if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
+    sn_status s;
+    if (v && (s = copy_out(c, v, c->V, (size_t)c->n * 4, on_device))) return s;
+    if (refr && (s = copy_out(c, refr, c->r, (size_t)c->n * 4, on_device))) return s;
+    return SN_OK;
+}
+
+sn_status sn_get_trace(sn_ctx *c, float *x, int32_t on_device) {
+    if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
+    if (!x) return fail(c, SN_EINVAL, "trace is NULL");
+    if (!c->trace) return fail(c, SN_ESTATE, "STDP was never enabled");
+    const int buf = c->step > 0 ? (int)((c->step - 1) & 1) : 1;
+    return copy_out(c, x, c->trace + (size_t)buf * c->n, (size_t)c->n * 4, on_device);
+}
+
+sn_status sn_get_weights(sn_ctx *c, float *w, int32_t on_device) {
+    if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
+    if (!w) return fail(c, SN_EINVAL, "w is NULL");
+    if (c->kind == KIND_DENSE) return copy_out(c, w, c->W, (size_t)c->n * c->n * 4, on_device);
+    if (c->kind != KIND_SPARSE) return fail(c, SN_ESTATE, "wrong context kind");
+    if (c->m == 0) return SN_OK;
+    if (c->dtype != SN_F32) return fail(c, SN_EUNSUPPORTED, "weights of SN_I32 networks are never changed");
+    if (!c->perm_inv) {
+        sn_status s = dalloc(c, &c->perm_inv, (size_t)c->m * 8);
+        if (s) return s;
+        SN_CUDA(c, cudaMemcpy(c->perm_inv, c->h_perm_inv.data(), (size_t)c->m * 8, cudaMemcpyHostToDevice));
+    }
+    float *dst = w;
+    float *tmp = nullptr;
+    if (!on_device) {
+        sn_status s = dalloc(c, &tmp, (size_t)c->m * 4);
+        if (s) return s;
+        dst = tmp;
+    }
+    cudaError_t e = launch_gather_weights(c->syn, c->perm_inv, c->m, dst, c->stream);
+    if (e != cudaSuccess) { dfree(c, tmp); return cuda_fail(c, e, "weight gather"); }
+    if (!on_device) {
+        e = cudaMemcpyAsync(w, tmp, (size_t)c->m * 4, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        dfree(c, tmp);
+        if (e != cudaSuccess) return cuda_fail(c, e, "weight copy");
+        return read_status(c);
+    }
+    return SN_OK;
+}
+
+sn_status sn_get_counters(sn_ctx *c, int64_t *steps, int64_t *spikes, int64_t *events) {
+    if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
+    SN_CUDA(c, cudaStreamSynchronize(c->stream));
+    Control h;
+    SN_CUDA(c, cudaMemcpy(&h, c->ctl, sizeof(Control), cudaMemcpyDeviceToHost));
+    if (steps) *steps = c->step;
+    if (spikes) *spikes = (int64_t)h.spikes;
+    if (events) *events = (int64_t)h.events;
+    return read_status(c);
+}
+
+// Checkpoint layout: header, V, r, ring, partial (dense), trace (if any),
+// weights (sparse CSR words or dense W), counters.
+struct SaveHeader {
+    char magic[8];
+    int kind, dtype, n, D1, S, has_trace;
+    long long m, step;
+    unsigned long long spikes, events;
+};
+
+static size_t save_size(const sn_ctx *c) {
+    size_t s = sizeof(SaveHeader) + (size_t)c->n * 8 + c->ring_bytes;
+    if (c->kind == KIND_DENSE) s += (size_t)c->S * c->n * 4 + (size_t)c->n * c->n * 4;
+    else s += (size_t)(c->m > 0 ? c->m : 0) * 8;
+    if (c->trace) s += (size_t)2 * c->n * 4;
+    return s;
+}
+
+sn_status sn_save(sn_ctx *c, void *buf, size_t *size) {
+    if (!c || !size) return fail(c, SN_EINVAL, "NULL argument");
+    if (c->kind != KIND_SPARSE && c->kind != KIND_DENSE) return fail(c, SN_ESTATE, "wrong context kind");
+    const size_t need = save_size(c);
+    if (!buf) { *size = need; return SN_OK; }
+    if (*size < need) return fail(c, SN_EINVAL, "buffer too small");
+    SN_CUDA(c, cudaStreamSynchronize(c->stream));
+    sn_status st = read_status(c);
+    if (st) return st;
+    Control h;
+    SN_CUDA(c, cudaMemcpy(&h, c->ctl, sizeof(Control), cudaMemcpyDeviceToHost));
+    SaveHeader hd;
+    memset(&hd, 0, sizeof(hd));
+    memcpy(hd.magic, "SNCKPT1", 8);
+    hd.kind = c->kind; hd.dtype = c->dtype; hd.n = c->n; hd.D1 = c->D1; hd.S = c->S;
+    hd.has_trace = c->trace != nullptr; hd.m = c->m; hd.step = c->step;
+    hd.spikes = h.spikes; hd.events = h.events;
+    uint8_t *p = (uint8_t *)buf;
+    memcpy(p, &hd, sizeof(hd)); p += sizeof(hd);
+    auto get = [&](const void *src, size_t bytes) -> cudaError_t {
+        cudaError_t e = cudaMemcpy(p, src, bytes, cudaMemcpyDeviceToHost);
+        p += bytes;
+        return e;
+    };
+    cudaError_t e;
+    if ((e = get(c->V, (size_t)c->n * 4)) || (e = get(c->r, (size_t)c->n * 4)) || (e = get(c->ring, c->ring_bytes)))
+        return cuda_fail(c, e, "save");
+    if (c->kind == KIND_DENSE) {
+        if ((e = get(c->partial, (size_t)c->S * c->n * 4)) || (e = get(c->W, (size_t)c->n * c->n * 4)))
+            return cuda_fail(c, e, "save");
+    } else if (c->m > 0 && (e = get(c->syn, (size_t)c->m * 8))) {
+        return cuda_fail(c, e, "save");
+    }
+    if (c->trace && (e = get(c->trace, (size_t)2 * c->n * 4))) return cuda_fail(c, e, "save");
+    *size = need;
+    return SN_OK;
+}
+
+sn_status sn_load(sn_ctx *c, const void *buf, size_t size) {
+    if (!c || !buf) return fail(c, SN_EINVAL, "NULL argument");
+    if (size < sizeof(SaveHeader)) return fail(c, SN_EINVAL, "buffer too small");
+    SaveHeader hd;
+    memcpy(&hd, buf, sizeof(hd));
+    if (memcmp(hd.magic, "SNCKPT1", 8) != 0) return fail(c, SN_EINVAL, "not a checkpoint");
+    if (hd.kind != c->kind || hd.dtype != c->dtype || hd.n != c->n || hd.D1 != c->D1 || hd.m != c->m ||
+        hd.S != c->S)
+        return fail(c, SN_EINVAL, "checkpoint is of a different network");
+    if (hd.has_trace && !c->trace) {
+        sn_status s = dalloc(c, &c->trace, (size_t)2 * c->n * 4);
+        if (s) return s;
+    }
+    if (size < save_size(c)) return fail(c, SN_EINVAL, "checkpoint truncated");
+    SN_CUDA(c, cudaStreamSynchronize(c->stream));
+    const uint8_t *p = (const uint8_t *)buf + sizeof(hd);
+    auto put = [&](void *dst, size_t bytes) -> cudaError_t {
+        cudaError_t e = cudaMemcpy(dst, p, bytes, cudaMemcpyHostToDevice);
+        p += bytes;
+        return e;
+    };
+    cudaError_t e;
+    if ((e = put(c->V, (size_t)c->n * 4)) || (e = put(c->r, (size_t)c->n * 4)) || (e = put(c->ring, c->ring_bytes)))
+        return cuda_fail(c, e, "load");
+    if (c->kind == KIND_DENSE) {
+        if ((e = put(c->partial, (size_t)c->S * c->n * 4)) || (e = put(c->W, (size_t)c->n * c->n * 4)))
+            return cuda_fail(c, e, "load");
+    } else if (c->m > 0 && (e = put(c->syn, (size_t)c->m * 8))) {
+        return cuda_fail(c, e, "load");
+    }
+    if (hd.has_trace && (e = put(c->trace, (size_t)2 * c->n * 4))) return cuda_fail(c, e, "load");
+    Control h;
+    memset(&h, 0, sizeof(h));
+    h.spikes = hd.spikes;
+    h.events = hd.events;
+    SN_CUDA(c, cudaMemcpy(c->ctl, &h, sizeof(h), cudaMemcpyHostToDevice));
+    c->step = hd.step;
+    c->raster_from = hd.step;
+    c->failed = 0;
+    return SN_OK;
+}
+
+void sn_destroy(sn_ctx *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    destroy_all(c);
+    delete c;
+}
+
+}  // extern "C"

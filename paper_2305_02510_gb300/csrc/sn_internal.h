@@ -1,0 +1,86 @@
+// Internal declarations shared by the host API (sn_api.cu) and the kernel
+// translation units.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sn.h"
+
+namespace sn {
+
+enum Kind { KIND_SPARSE = 0, KIND_DENSE = 1, KIND_BATCH = 2, KIND_SHARED_I8 = 3 };
+
+// Grid barrier state (one per context): arrival count and generation.
+struct GridBarrier {
+    unsigned int count;
+    unsigned int gen;
+};
+
+// Device-side control block: latched status word and run counters.
+struct Control {
+    int status;                       // 0 or an sn_status latched by a kernel
+    int pad;
+    unsigned long long spikes;        // total spikes
+    unsigned long long events;        // total synaptic events
+    GridBarrier bar;
+};
+
+// Wall-clock limit of one grid-barrier wait before the kernel gives up and
+// latches SN_ETIMEOUT (nanoseconds of %globaltimer).
+constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;
+
+// Packed synapse of the CSR (pre-major) store: x = post | (delay-1) << 26,
+// y = weight bits (float in SN_F32 mode, int32 in SN_I32 mode).
+constexpr int kPostBits = 26;
+constexpr unsigned kPostMask = (1u << kPostBits) - 1u;
+
+// Arguments of the single-network kernels (sparse push and dense gather).
+struct NetArgs {
+    int n, D1, words, cap;            // neurons, ring slots (D+1), raster words/row, raster rows
+    int t0, steps;                    // first absolute step, steps to run
+    int chunk;                        // neurons owned per block (multiple of 32)
+    // neuron state and parameters (float or int32 according to the mode)
+    void *V;
+    int *r;
+    const void *th, *lk, *rs;
+    const int *R;
+    const unsigned *prate;            // Poisson threshold per neuron (0: no source)
+    const void *pamp;                 // Poisson amplitude per neuron
+    unsigned long long pkey;          // Poisson stream key of the network
+    // explicit events, deduplicated per (step, neuron), sorted by neuron per step
+    const int *ev_off;                // [ev_nsteps + 1] offsets by absolute step
+    int ev_nsteps;
+    const int *ev_neuron;
+    const void *ev_val;
+    // sparse store (CSR by pre)
+    const long long *rowptr;
+    uint2 *syn;                       // weights are rewritten in place by STDP
+    const long long *colptr;          // CSC by post (STDP only)
+    const uint2 *csc;                 // {pre, CSR position}
+    void *ring;                       // [D1][n] pending input (int64 fixed point / int32 / float)
+    // dense store
+    float *W;                         // [n][n]
+    float *partial;                   // [S][n] gather partial sums
+    int S, dense_delay;
+    // spikes
+    unsigned *raster;                 // [cap][words]
+    // STDP
+    int stdp;
+    float decay, a_plus, a_minus, wmin, wmax;
+    float *trace;                     // [2][n], buffer (t & 1) holds x(t)
+    Control *ctl;
+};
+
+// Launchers (kernels live in sn_kernels.cu).  Return a CUDA error code.
+cudaError_t launch_sparse(const NetArgs &a, int dtype, int grid, int block, cudaStream_t s);
+cudaError_t launch_dense(const NetArgs &a, int grid, int block, cudaStream_t s);
+cudaError_t max_grid_sparse(int dtype, int stdp, int block, int *grid);
+cudaError_t max_grid_dense(int block, int *grid, size_t *smem);
+cudaError_t launch_gather_weights(const uint2 *syn, const long long *perm_inv, long long m,
+                                  float *out, cudaStream_t s);
+
+}  // namespace sn

@@ -1,0 +1,298 @@
+"""Thin Python binding of libsn.so: the entry points of include/sn.h under the
+same names, with argument marshalling only.
+
+Host arrays are numpy arrays; device buffers are torch CUDA tensors (their
+data pointers are passed through).  Every call raises SnError when the C call
+returns a status other than SN_OK.  The library is loaded on first use, and
+loading fails loudly if it has not been built: there is no fallback path.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+SN_OK, SN_EINVAL, SN_ENOMEM, SN_ECUDA, SN_ESTATE, SN_ETIMEOUT, SN_EUNSUPPORTED, SN_EOVERFLOW = range(8)
+SN_F32, SN_I32 = 0, 1
+SN_AUTO, SN_EXEC_CTA, SN_EXEC_GRID = 0, 1, 2
+_NAMES = ["SN_OK", "SN_EINVAL", "SN_ENOMEM", "SN_ECUDA", "SN_ESTATE", "SN_ETIMEOUT",
+          "SN_EUNSUPPORTED", "SN_EOVERFLOW"]
+
+
+class SnError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_NAMES[status] if 0 <= status < len(_NAMES) else status}: {msg}")
+        self.status = status
+
+
+class sn_config(C.Structure):
+    _fields_ = [("dtype", C.c_int32), ("max_delay", C.c_int32), ("flags", C.c_uint32),
+                ("record_steps", C.c_int32), ("cuda_stream", C.c_void_p)]
+
+
+class sn_neurons(C.Structure):
+    _fields_ = [("n", C.c_int32), ("threshold", C.c_void_p), ("leak", C.c_void_p),
+                ("reset", C.c_void_p), ("refractory", C.c_void_p)]
+
+
+class sn_synapses(C.Structure):
+    _fields_ = [("m", C.c_int64), ("pre", C.c_void_p), ("post", C.c_void_p),
+                ("weight", C.c_void_p), ("delay", C.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+_P = C.c_void_p
+
+
+def lib():
+    """Load libsn.so (raises if it is missing: build it with build.build())."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError(f"libsn.so not built ({_build.LIB}); run "
+                                   "paper_2305_02510_gb300.build.build() first")
+            L = C.CDLL(_build.LIB)
+            sig = {
+                "sn_create": [C.POINTER(sn_config), C.POINTER(sn_neurons), C.POINTER(sn_synapses),
+                              C.POINTER(_P)],
+                "sn_create_dense": [C.POINTER(sn_config), C.POINTER(sn_neurons), _P, C.c_int32,
+                                    C.POINTER(_P)],
+                "sn_set_input": [_P, C.c_int64, _P, _P, _P],
+                "sn_set_poisson": [_P, C.c_int32, _P, _P, _P, C.c_uint64],
+                "sn_stdp": [_P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int32],
+                "sn_run": [_P, C.c_int32],
+                "sn_sync": [_P],
+                "sn_get_spikes": [_P, C.c_int64, C.c_int64, _P, C.c_int32],
+                "sn_get_state": [_P, _P, _P, C.c_int32],
+                "sn_get_trace": [_P, _P, C.c_int32],
+                "sn_get_weights": [_P, _P, C.c_int32],
+                "sn_get_counters": [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                    C.POINTER(C.c_int64)],
+                "sn_save": [_P, _P, C.POINTER(C.c_size_t)],
+                "sn_load": [_P, _P, C.c_size_t],
+            }
+            for name, args in sig.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = C.c_int
+            L.sn_last_error.argtypes = [_P]
+            L.sn_last_error.restype = C.c_char_p
+            L.sn_destroy.argtypes = [_P]
+            L.sn_destroy.restype = None
+            L.sn_version.argtypes = []
+            L.sn_version.restype = C.c_char_p
+            _lib = L
+    return _lib
+
+
+def _check(st, ctx=None):
+    if st != SN_OK:
+        msg = lib().sn_last_error(ctx.handle if ctx is not None else None)
+        raise SnError(st, msg.decode() if msg else "")
+
+
+def _arr(a, dt):
+    return np.ascontiguousarray(np.asarray(a), dtype=dt)
+
+
+def _ptr(x):
+    """Data pointer of a numpy array or a torch tensor (None for None)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+def _is_dev(x):
+    return hasattr(x, "is_cuda") and x.is_cuda
+
+
+class Ctx:
+    """Owns one sn_ctx handle; n, dtype and kind are kept for output sizing."""
+
+    def __init__(self, handle, n, dtype, words, kind, m):
+        self.handle = handle
+        self.n, self.dtype, self.words, self.kind, self.m = n, dtype, words, kind, m
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.sn_destroy(self.handle)
+            self.handle = None
+
+
+def _config(dtype, max_delay, flags, record_steps, stream):
+    cfg = sn_config()
+    cfg.dtype = SN_I32 if dtype in (SN_I32, "i32") else SN_F32
+    cfg.max_delay = int(max_delay)
+    cfg.flags = int(flags)
+    cfg.record_steps = int(record_steps)
+    cfg.cuda_stream = stream
+    return cfg
+
+
+def _neurons(threshold, leak, reset, refractory, keep):
+    th, lk, rs = _arr(threshold, np.float32), _arr(leak, np.float32), _arr(reset, np.float32)
+    rf = _arr(refractory, np.int32)
+    keep += [th, lk, rs, rf]
+    nr = sn_neurons()
+    nr.n = th.size
+    nr.threshold, nr.leak, nr.reset, nr.refractory = _ptr(th), _ptr(lk), _ptr(rs), _ptr(rf)
+    return nr
+
+
+def sn_create(threshold, leak, reset, refractory, pre, post, weight, delay, *, dtype=SN_F32,
+              max_delay=None, flags=SN_AUTO, record_steps=0, stream=None) -> Ctx:
+    keep = []
+    nr = _neurons(threshold, leak, reset, refractory, keep)
+    pre, post = _arr(pre, np.int32), _arr(post, np.int32)
+    w, d = _arr(weight, np.float32), _arr(delay, np.int32)
+    keep += [pre, post, w, d]
+    sy = sn_synapses()
+    sy.m = pre.size
+    sy.pre, sy.post, sy.weight, sy.delay = _ptr(pre), _ptr(post), _ptr(w), _ptr(d)
+    D = int(max_delay if max_delay is not None else (d.max() if d.size else 1))
+    cfg = _config(dtype, D, flags, record_steps, stream)
+    h = _P()
+    _check(lib().sn_create(C.byref(cfg), C.byref(nr), C.byref(sy), C.byref(h)))
+    return Ctx(h, nr.n, cfg.dtype, (nr.n + 31) // 32, "sparse", pre.size)
+
+
+def sn_create_dense(threshold, leak, reset, refractory, w, delay=1, *, max_delay=None,
+                    flags=SN_AUTO, record_steps=0, stream=None) -> Ctx:
+    keep = []
+    nr = _neurons(threshold, leak, reset, refractory, keep)
+    w = _arr(w, np.float32)
+    keep.append(w)
+    cfg = _config(SN_F32, max_delay if max_delay is not None else delay, flags, record_steps, stream)
+    h = _P()
+    _check(lib().sn_create_dense(C.byref(cfg), C.byref(nr), _ptr(w), int(delay), C.byref(h)))
+    return Ctx(h, nr.n, SN_F32, (nr.n + 31) // 32, "dense", nr.n * nr.n)
+
+
+def sn_set_input(ctx: Ctx, step, neuron, value):
+    s, j, v = _arr(step, np.int32), _arr(neuron, np.int32), _arr(value, np.float32)
+    _check(lib().sn_set_input(ctx.handle, s.size, _ptr(s) if s.size else None,
+                              _ptr(j) if j.size else None, _ptr(v) if v.size else None), ctx)
+
+
+def sn_set_poisson(ctx: Ctx, neuron, rate, amplitude, seed):
+    j, r, a = _arr(neuron, np.int32), _arr(rate, np.float32), _arr(amplitude, np.float32)
+    _check(lib().sn_set_poisson(ctx.handle, j.size, _ptr(j) if j.size else None,
+                                _ptr(r) if r.size else None, _ptr(a) if a.size else None,
+                                int(seed) & (2**64 - 1)), ctx)
+
+
+def sn_stdp(ctx: Ctx, decay, a_plus, a_minus, wmin, wmax, enable=True):
+    _check(lib().sn_stdp(ctx.handle, decay, a_plus, a_minus, wmin, wmax, int(bool(enable))), ctx)
+
+
+def sn_run(ctx: Ctx, steps: int):
+    _check(lib().sn_run(ctx.handle, int(steps)), ctx)
+
+
+def sn_sync(ctx: Ctx):
+    _check(lib().sn_sync(ctx.handle), ctx)
+
+
+def sn_get_spikes(ctx: Ctx, t0: int, t1: int, out=None):
+    """Raster words [(t1 - t0), words] (uint32).  `out` may be a torch CUDA
+    tensor of that shape (int32 or uint32 storage) for a device-side copy."""
+    if out is None:
+        out = np.zeros((t1 - t0, ctx.words), np.uint32)
+    _check(lib().sn_get_spikes(ctx.handle, int(t0), int(t1), _ptr(out), int(_is_dev(out))), ctx)
+    return out
+
+
+def unpack_raster(bits, n):
+    """Raster words -> uint8 [steps, n] (bit j % 32 of word j // 32)."""
+    b = np.asarray(bits, dtype=np.uint32)
+    u8 = b.view(np.uint8).reshape(b.shape[0], -1)
+    return np.unpackbits(u8, axis=1, bitorder="little")[:, :n]
+
+
+def sn_get_state(ctx: Ctx, v=None, refractory=None):
+    vt = np.int32 if ctx.dtype == SN_I32 else np.float32
+    if v is None:
+        v = np.zeros(ctx.n, vt)
+    if refractory is None:
+        refractory = np.zeros(ctx.n, np.int32)
+    dev = _is_dev(v)
+    _check(lib().sn_get_state(ctx.handle, _ptr(v), _ptr(refractory), int(dev)), ctx)
+    return v, refractory
+
+
+def sn_get_trace(ctx: Ctx, out=None):
+    if out is None:
+        out = np.zeros(ctx.n, np.float32)
+    _check(lib().sn_get_trace(ctx.handle, _ptr(out), int(_is_dev(out))), ctx)
+    return out
+
+
+def sn_get_weights(ctx: Ctx, out=None):
+    if out is None:
+        out = np.zeros(ctx.m, np.float32)
+    _check(lib().sn_get_weights(ctx.handle, _ptr(out), int(_is_dev(out))), ctx)
+    return out
+
+
+def sn_get_counters(ctx: Ctx):
+    a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+    _check(lib().sn_get_counters(ctx.handle, C.byref(a), C.byref(b), C.byref(c)), ctx)
+    return a.value, b.value, c.value
+
+
+def sn_save(ctx: Ctx) -> bytes:
+    size = C.c_size_t(0)
+    _check(lib().sn_save(ctx.handle, None, C.byref(size)), ctx)
+    buf = C.create_string_buffer(size.value)
+    _check(lib().sn_save(ctx.handle, buf, C.byref(size)), ctx)
+    return buf.raw[:size.value]
+
+
+def sn_load(ctx: Ctx, blob: bytes):
+    _check(lib().sn_load(ctx.handle, blob, len(blob)), ctx)
+
+
+def sn_version() -> str:
+    return lib().sn_version().decode()
+
+
+def sn_destroy(ctx: Ctx):
+    if ctx.handle:
+        lib().sn_destroy(ctx.handle)
+        ctx.handle = None
+
+
+# ---------------------------------------------------------------------------
+# workload helper (marshalling of a workload dict into the calls above)
+
+def from_workload(wl, *, record_steps=None, flags=SN_AUTO, stream=None) -> Ctx:
+    """Create a context for a workload dict of paper_2305_02510_gb300.workloads
+    and install its inputs (events, Poisson sources, STDP)."""
+    rec = wl["steps"] if record_steps is None else record_steps
+    if "dense_w" in wl:
+        ctx = sn_create_dense(wl["threshold"], wl["leak"], wl["reset"], wl["refractory"],
+                              wl["dense_w"], wl["dense_delay"], max_delay=wl["max_delay"],
+                              flags=flags, record_steps=rec, stream=stream)
+    else:
+        ctx = sn_create(wl["threshold"], wl["leak"], wl["reset"], wl["refractory"], wl["pre"],
+                        wl["post"], wl["weight"], wl["delay"], dtype=wl["dtype"],
+                        max_delay=wl["max_delay"], flags=flags, record_steps=rec, stream=stream)
+    ev = wl["events"]
+    if len(ev["step"]):
+        sn_set_input(ctx, ev["step"], ev["neuron"], ev["value"])
+    po = wl["poisson"]
+    if len(po["neuron"]):
+        sn_set_poisson(ctx, po["neuron"], po["rate"], po["amplitude"], po["seed"])
+    if wl.get("stdp"):
+        sd = wl["stdp"]
+        sn_stdp(ctx, sd["decay"], sd["a_plus"], sd["a_minus"], sd["wmin"], sd["wmax"], True)
+    return ctx

@@ -1,0 +1,94 @@
+"""The C ABI without a GPU: libsn.so loads, exports every entry point that
+include/sn.h declares, and rejects bad arguments with SN_EINVAL before any
+CUDA call is made."""
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def S():
+    from paper_2305_02510_gb300 import build, sn
+    build.build()
+    sn.lib()
+    return sn
+
+
+def declared():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", h)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"^\s*(?:sn_status|const char\s*\*|void|int32_t)\s*\*?\s*(sn_\w+)\s*\(",
+                                txt, re.M)
+    return names
+
+
+def test_exports_every_declared_symbol(S):
+    names = declared()
+    assert "sn_create" in names and "sn_run" in names and len(names) >= 17
+    missing = [n for n in names if not hasattr(S.lib(), n)]
+    assert not missing
+
+
+def _neurons(S, n, keep):
+    th, lk, rs = np.ones(n, np.float32), np.zeros(n, np.float32), np.zeros(n, np.float32)
+    rf = np.zeros(n, np.int32)
+    keep += [th, lk, rs, rf]
+    nr = S.sn_neurons()
+    nr.n = n
+    nr.threshold, nr.leak, nr.reset, nr.refractory = (a.ctypes.data for a in (th, lk, rs, rf))
+    return nr, (th, lk, rs, rf)
+
+
+def _create(S, n=4, pre=(0,), post=(1,), w=(1.0,), d=(1,), dtype=0, D=2, flags=0, leak=None):
+    keep = []
+    nr, arrs = _neurons(S, n, keep)
+    if leak is not None:
+        arrs[1][:] = leak
+    pre, post = np.array(pre, np.int32), np.array(post, np.int32)
+    w, d = np.array(w, np.float32), np.array(d, np.int32)
+    sy = S.sn_synapses()
+    sy.m = pre.size
+    sy.pre, sy.post, sy.weight, sy.delay = pre.ctypes.data, post.ctypes.data, w.ctypes.data, d.ctypes.data
+    cfg = S.sn_config()
+    cfg.dtype, cfg.max_delay, cfg.flags, cfg.record_steps = dtype, D, flags, 0
+    h = C.c_void_p()
+    st = S.lib().sn_create(C.byref(cfg), C.byref(nr), C.byref(sy), C.byref(h))
+    return st, S.lib().sn_last_error(None).decode()
+
+
+@pytest.mark.parametrize("kw,frag", [
+    (dict(d=(3,)), "delay"),
+    (dict(d=(0,)), "delay"),
+    (dict(pre=(4,)), "index"),
+    (dict(post=(-1,)), "index"),
+    (dict(w=(float("nan"),)), "weight"),
+    (dict(w=(0.5,), dtype=1), "integer"),
+    (dict(D=0), "max_delay"),
+    (dict(D=65), "max_delay"),
+    (dict(dtype=7), "dtype"),
+    (dict(flags=3), "exclusive"),
+    (dict(flags=64), "flags"),
+    (dict(leak=-1.0), "leak"),
+    (dict(n=0), "n must"),
+])
+def test_invalid_arguments(S, kw, frag):
+    st, msg = _create(S, **kw)
+    assert st == S.SN_EINVAL
+    assert frag in msg
+
+
+def test_version_and_null_handles(S):
+    L = S.lib()
+    assert b"sm_103a" in L.sn_version()
+    assert L.sn_run(None, 1) == S.SN_EINVAL
+    assert L.sn_sync(None) == S.SN_EINVAL
+    L.sn_destroy(None)
