@@ -1,0 +1,289 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the spiking-network simulator on one GB300.
+
+One benchmark step = one full simulation of the large sparse network
+(N = 100,000 LIF neurons, 100 synapses each = 1e7 synapses, delays 1..16,
+float32 state, Poisson input into 1% of the neurons) for 1000 timesteps, from
+the initial state.  Headline metric: synaptic events per second (one event =
+one spike delivered along one synapse), with timesteps per second beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank simulates its own replica of the network with its own
+input stream (the single network is not sharded: replicas only, weak scaling).
+The reference arm (--impl reference) times the CPU oracle on bounded samples
+of the same workload on this host; only rank 0 runs it.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "synaptic events/s & timesteps/s on 1 GB300 (batched vs plain); BPTT step ms"
+UNIT = "synaptic events/s"
+TIMESTEPS = 1000
+# per-neuron state bytes touched once per timestep by the update phase:
+# V and r read+write (16), threshold/leak/reset/refractory/Poisson rate and
+# amplitude read (24), pending-input slot read and clear (16)
+STATE_BYTES = 56
+# DRAM bytes per launch of the sparse kernel from the last ncu capture of the
+# current kernel (None until one is taken for this kernel version)
+NCU_TRAFFIC_BYTES = None
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        self.rows = []
+        if self.p is None:
+            return
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            out = ""
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) >= 9:
+                self.rows.append(f)
+
+    def summary(self):
+        if not getattr(self, "rows", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def algorithmic_bytes(n, timesteps, spikes, events):
+    """Bytes the sparse path must move per launch: per spike its CSR row
+    bounds (16 B); per event its packed synapse (8 B) and its accumulate into
+    the pending-input ring (8 B); per neuron and timestep the update phase's
+    state traffic and its raster bit."""
+    return spikes * 16 + events * 16 + timesteps * n * STATE_BYTES + timesteps * n / 8
+
+
+def oracle_sample(wl, warm=40, timed=60):
+    """The CPU oracle as it stands, single-threaded, on a bounded sample of the
+    workload: `warm` untimed timesteps from the initial state (past the start-up
+    transient), then `timed` timed timesteps.  Returns (events/s, timesteps/s,
+    sample text)."""
+    from oracle import oracle as O
+    deg = np.bincount(np.asarray(wl["pre"]), minlength=wl["n"]).astype(np.int64)
+    st, _, _ = O.run(wl, O.F32, warm)
+    t0 = time.perf_counter()
+    st, raster, _ = O.run(wl, O.F32, timed, state=st)
+    dt = time.perf_counter() - t0
+    ev = int((raster.astype(np.int64) * deg[None, :]).sum())
+    return ev / dt, timed / dt, f"timesteps {warm}..{warm + timed - 1} of {wl['name']} (N={wl['n']}, " \
+                                f"M={len(wl['pre'])}), single-threaded C oracle, float32 mirror"
+
+
+def run_reference(args, wl, rank):
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    deg = np.bincount(np.asarray(wl["pre"]), minlength=wl["n"]).astype(np.int64)
+    base, _, _ = O.run(wl, O.F32, 40)
+    per = 8
+    times, evs = [], []
+    for k in range(args.warmup + args.steps):
+        st = base.copy()
+        t0 = time.perf_counter()
+        st, raster, _ = O.run(wl, O.F32, per, state=st)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+            evs.append(int((raster.astype(np.int64) * deg[None, :]).sum()))
+    value = sum(evs) / sum(times)
+    sample = f"{per} timesteps (40..{40 + per - 1}) of {wl['name']} per step, single-threaded C oracle"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": "large-sparse", "neurons": wl["n"], "synapses": int(len(wl["pre"])),
+                   "max_delay": 16, "timesteps_per_step": per, "parallelism": "replicas"},
+        "timesteps_per_s": per * len(times) / sum(times),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--timesteps", type=int, default=TIMESTEPS)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+
+    from paper_2305_02510_gb300 import workloads as W
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        run_reference(args, W.large_sparse(integer=False), rank)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__ as G
+    if rank == 0:
+        G.build()
+    if world > 1:
+        dist.barrier()
+    from paper_2305_02510_gb300 import sn as S
+
+    T = args.timesteps
+    wl = W.large_sparse(integer=False, steps=T)
+    wl["poisson"]["seed"] = int(wl["poisson"]["seed"]) + 7919 * rank   # own input per replica
+    stream = torch.cuda.current_stream()
+    ctx = S.from_workload(wl, record_steps=T, stream=stream.cuda_stream)
+    n = wl["n"]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
+
+    def one(record):
+        S.sn_reset(ctx)
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        S.sn_run(ctx, T)
+        b.record(stream)
+        S.sn_sync(ctx)
+        _, spk, ev = S.sn_get_counters(ctx)
+        record.append((a.elapsed_time(b), spk, ev))
+
+    for _ in range(args.warmup):
+        one([])
+    res = []
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        w0 = time.perf_counter()
+        for _ in range(args.steps):
+            one(res)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+    if world > 1:
+        dist.barrier()
+    ms = sum(r[0] for r in res) / len(res)
+    spikes = sum(r[1] for r in res) / len(res)
+    events = sum(r[2] for r in res) / len(res)
+    # end to end through the public API with host buffers: install the input
+    # (host arrays -> device), reset, run, read the raster back into pinned
+    # host memory and the counters
+    raster_host = torch.empty((T, ctx.words), dtype=torch.int32, pin_memory=True)
+    po = wl["poisson"]
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    e_events = 0
+    for _ in range(args.steps):
+        S.sn_set_poisson(ctx, po["neuron"], po["rate"], po["amplitude"], po["seed"])
+        S.sn_reset(ctx)
+        S.sn_run(ctx, T)
+        S.sn_get_spikes(ctx, 0, T, out=raster_host.numpy())
+        e_events += S.sn_get_counters(ctx)[2]
+    e2e_s = time.perf_counter() - e0
+
+    t = torch.tensor([ms, events, e2e_s, e_events], dtype=torch.float64, device="cuda")
+    if world > 1:
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        ms_all, ev_all, e2e_all, e2e_ev_all = float(mx[0]), float(sm[1]), float(mx[2]), float(sm[3])
+    else:
+        ms_all, ev_all, e2e_all, e2e_ev_all = ms, events, e2e_s, e_events
+    value = ev_all / (ms_all / 1e3)
+
+    if rank == 0:
+        peak, src = peaks()
+        abytes = algorithmic_bytes(n, T, spikes, events)
+        achieved = abytes / (ms / 1e3) / 1e9
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "large-sparse", "neurons": n, "synapses": int(len(wl["pre"])),
+                       "max_delay": 16, "timesteps_per_step": T, "input": "Poisson 0.05/step into 1000 neurons",
+                       "l2": "256 MiB buffer written before every timed run (L2 flushed)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "timesteps_per_s": world * T / (ms_all / 1e3),
+            "spikes_per_step": spikes, "events_per_step": events,
+            "wall_ms_per_step": 1e3 * wall / args.steps,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": src,
+                         "traffic": NCU_TRAFFIC_BYTES, "kernel": "sparse_kernel<SN_F32,false>",
+                         "algorithmic_bytes_per_launch": abytes},
+            "e2e": {"value": e2e_ev_all / e2e_all, "unit": UNIT,
+                    "h2d_bytes_per_step": 8 * n,
+                    "d2h_bytes_per_step": T * ctx.words * 4 + 32},
+            "gpu_launches": args.steps,
+            "clocks": clk.summary(),
+        }
+        if not args.no_cpu_baseline:
+            ev_s, ts_s, sample = oracle_sample(wl)
+            line["cpu_baseline"] = {"value": ev_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": sample, "timesteps_per_s": ts_s}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -162,6 +162,12 @@ sn_status sn_stdp(sn_ctx *ctx, float decay, float a_plus, float a_minus,
  * context's stream; a step counter makes repeated calls continue the run. */
 sn_status sn_run(sn_ctx *ctx, int32_t steps);
 
+/* Return the dynamic state to that of a new context: step 0, V = reset,
+ * r = 0, no pending synaptic input, zero STDP traces, zero counters, empty
+ * raster.  Weights and inputs are kept (weights changed by STDP stay
+ * changed).  Queued on the stream; allocates nothing. */
+sn_status sn_reset(sn_ctx *ctx);
+
 /* Wait for queued work; report a latched device status (SN_ETIMEOUT,
  * SN_EOVERFLOW) if any. */
 sn_status sn_sync(sn_ctx *ctx);

@@ -29,7 +29,8 @@
  *            to float gives the correctly rounded float result, so this is
  *            float arithmetic in the canonical order stated below.
  *   ORC_INT: integer values; all operations are exact in double while the
- *            magnitudes stay below 2^53 (checked: |V| must stay below 2^31).
+ *            magnitudes stay below 2^53 (checked: the state compared with
+ *            the threshold must stay below 2^31 in magnitude).
  * Canonical order of the synaptic sum for post-neuron j at step t:
  *   acc = 0; for each incoming synapse in ascending (delay, pre, input index):
  *   if pre spiked at t - delay: acc = acc + w.   Then V = (L(V) + acc) + ext.
@@ -267,6 +268,8 @@ int orc_run(const orc_net *net, int64_t t0, int32_t steps,
             vj = R(vj + acc);
             vj = R(vj + ext[j]);
             if (ctrace) ctrace[(size_t)s * n + j] = vj;
+            /* integer mode: the integrated state must fit int32 */
+            if (net->mode == ORC_INT && fabs(vj) >= 2147483648.0) status = ORC_EOVERFLOW;
             /* threshold (strict), refractory mask, reset */
             int fire = (vj > net->threshold[j]) && (r[j] == 0);
             if (fire) {
@@ -275,7 +278,6 @@ int orc_run(const orc_net *net, int64_t t0, int32_t steps,
             } else if (r[j] > 0) {
                 r[j] -= 1;
             }
-            if (net->mode == ORC_INT && fabs(vj) >= 2147483648.0) status = ORC_EOVERFLOW;
             v[j] = vj;
             cur[j] = (uint8_t)fire;
         }

@@ -526,6 +526,23 @@ sn_status sn_run(sn_ctx *c, int32_t steps) {
     return SN_OK;
 }
 
+sn_status sn_reset(sn_ctx *c) {
+    if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
+    if (c->kind != KIND_SPARSE && c->kind != KIND_DENSE) return fail(c, SN_ESTATE, "wrong context kind");
+    const size_t vb = (size_t)c->n * 4;
+    SN_CUDA(c, cudaMemcpyAsync(c->V, c->rs, vb, cudaMemcpyDeviceToDevice, c->stream));
+    SN_CUDA(c, cudaMemsetAsync(c->r, 0, vb, c->stream));
+    SN_CUDA(c, cudaMemsetAsync(c->ring, 0, c->ring_bytes, c->stream));
+    if (c->partial) SN_CUDA(c, cudaMemsetAsync(c->partial, 0, (size_t)c->S * c->n * 4, c->stream));
+    if (c->trace) SN_CUDA(c, cudaMemsetAsync(c->trace, 0, 2 * vb, c->stream));
+    SN_CUDA(c, cudaMemsetAsync(c->raster, 0, (size_t)c->cap * c->words * 4, c->stream));
+    SN_CUDA(c, cudaMemsetAsync(c->ctl, 0, sizeof(Control), c->stream));
+    c->step = 0;
+    c->raster_from = 0;
+    c->failed = 0;
+    return SN_OK;
+}
+
 sn_status sn_sync(sn_ctx *c) {
     if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
     SN_CUDA(c, cudaStreamSynchronize(c->stream));

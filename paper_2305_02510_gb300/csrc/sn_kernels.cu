@@ -162,10 +162,11 @@ __device__ __forceinline__ bool lif_update_i32(int &v, int &rr, int acc, int ext
     else u = rs;
     u += acc;
     u += ext;
+    // the integrated state must fit int32 before it meets the threshold
+    if (u > 2147483647ll || u < -2147483648ll) overflow = true;
     bool fire = (u > th) && (rr == 0);
     if (fire) { u = rs; rr = R; }
     else if (rr > 0) rr -= 1;
-    if (u > 2147483647ll || u < -2147483648ll) overflow = true;
     v = (int)u;
     return fire;
 }

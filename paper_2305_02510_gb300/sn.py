@@ -68,6 +68,7 @@ def lib():
                 "sn_set_poisson": [_P, C.c_int32, _P, _P, _P, C.c_uint64],
                 "sn_stdp": [_P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int32],
                 "sn_run": [_P, C.c_int32],
+                "sn_reset": [_P],
                 "sn_sync": [_P],
                 "sn_get_spikes": [_P, C.c_int64, C.c_int64, _P, C.c_int32],
                 "sn_get_state": [_P, _P, _P, C.c_int32],
@@ -196,6 +197,10 @@ def sn_stdp(ctx: Ctx, decay, a_plus, a_minus, wmin, wmax, enable=True):
 
 def sn_run(ctx: Ctx, steps: int):
     _check(lib().sn_run(ctx.handle, int(steps)), ctx)
+
+
+def sn_reset(ctx: Ctx):
+    _check(lib().sn_reset(ctx.handle), ctx)
 
 
 def sn_sync(ctx: Ctx):

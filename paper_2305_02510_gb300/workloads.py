@@ -230,7 +230,7 @@ def random_small(seed: int, n: int | None = None, integer: bool = True,
     R = rng.integers(0, 4, size=n).astype(np.int32)
     wl = _base(n, dt, th, lk, rs, R, D, steps)
     wl.update(pre=pre, post=post, weight=w, delay=delay)
-    ne = rng.binomial(steps * n, events_rate / max(n, 1) * 3)
+    ne = rng.binomial(steps * n, min(1.0, events_rate / max(n, 1) * 3))
     st = rng.integers(0, steps, size=ne).astype(np.int32)
     nu = rng.integers(0, n, size=ne).astype(np.int32)
     if integer:
