@@ -213,6 +213,60 @@ const char *sn_last_error(const sn_ctx *ctx);
 /* Free the context and its device memory (NULL is ignored). */
 void sn_destroy(sn_ctx *ctx);
 
+/* ------------------------------------------------------------------------
+ * Dense run without allocation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory, for example
+ * code running while a CUDA stream is being captured into a graph (where
+ * cudaMalloc is not allowed), or a host application whose device memory is
+ * fully reserved by its own pool allocator.
+ *
+ * It simulates `steps` timesteps (steps 0 .. steps-1) of an all-to-all
+ * network exactly as sn_create_dense + sn_run would, on buffers the caller
+ * owns, starting from the caller's state with no synaptic input pending and
+ * no explicit events.  Every pointer below is a device pointer:
+ *   w                  [n*n] row-major weights (row = pre), read only
+ *   threshold, leak, reset [n] float; refractory [n] int32
+ *   poisson_threshold  [n] uint32 = floor(rate * 2^32) per neuron (0: none),
+ *                      poisson_amplitude [n] float; both NULL for no input;
+ *                      the stream key is derived from seed as in
+ *                      sn_set_poisson with net = 0
+ *   v, r               [n] state in/out (start: v = reset, r = 0)
+ *   raster             [steps * ceil(n/32)] uint32 out, row k = step k
+ * The kernel's scratch (partial sums, pending-input ring, control block)
+ * lives in one static device array of SN_NOALLOC_SCRATCH_BYTES, held by
+ * every device that loads the library until the process exits.  A network
+ * whose scratch does not fit is rejected with SN_EINVAL; the need is about
+ * 4 * (1024 * resident blocks + (delay + 2) * n) bytes, so every network up
+ * to the 200,000-neuron dense limit fits while delay + 2 <= 16.  The first call on a device
+ * looks up the array's device address with that device current; make that
+ * first call before any stream capture.  Every call shares the array and
+ * clears it first, so calls whose work overlaps on the GPU (two streams,
+ * two threads) race and must not be issued.  The call waits for its work and
+ * returns the device status (SN_ETIMEOUT if a grid barrier gave up).
+ * ------------------------------------------------------------------------ */
+#define SN_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+typedef struct {
+    int32_t n;
+    int32_t delay;                  /* 1 .. SN_MAX_DELAY                         */
+    int32_t steps;
+    int32_t pad;
+    const float *w;
+    const float *threshold;
+    const float *leak;
+    const float *reset;
+    const int32_t *refractory;
+    const uint32_t *poisson_threshold;
+    const float *poisson_amplitude;
+    uint64_t seed;
+    float *v;
+    int32_t *r;
+    uint32_t *raster;
+    void *cuda_stream;              /* cudaStream_t, NULL = default stream       */
+} sn_dense_noalloc_args;
+
+sn_status sn_run_dense_noalloc(const sn_dense_noalloc_args *args);
+
 /* Library version string. */
 const char *sn_version(void);
 

@@ -1,0 +1,124 @@
+// sn_run_dense_noalloc: the dense simulation for callers that cannot allocate
+// device memory.  It launches the same dense kernel as sn_run on a dense
+// context, but every buffer comes from the caller except the kernel's scratch
+// (partial sums, pending-input ring, zero Poisson table, control block), which
+// lives in one fixed file-scope device array.  No cudaMalloc, cudaFree or
+// allocating library routine is called on this path.
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "sn_internal.h"
+
+namespace {
+
+constexpr size_t kScratchBytes = SN_NOALLOC_SCRATCH_BYTES;
+
+// The shared scratch: every call on a device uses it, and it keeps the last
+// call's contents (cleared below where a call needs zeros).
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+// Device address of g_scratch for each device, looked up once per device with
+// that device current.  In host code `g_scratch` names a host-side shadow,
+// not device memory, so only this address may be handed to a kernel.
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void *g_addr[kMaxDevices];
+
+sn_status scratch_address(int dev, void **out) {
+    if (dev < 0 || dev >= kMaxDevices) return SN_EUNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess || !p) return SN_ECUDA;
+        g_addr[dev] = p;
+    }
+    *out = g_addr[dev];
+    return SN_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" sn_status sn_run_dense_noalloc(const sn_dense_noalloc_args *p) {
+    using namespace sn;
+    if (!p) return SN_EINVAL;
+    const int n = p->n;
+    if (n < 1 || n > 200000 || p->steps < 0 || p->delay < 1 || p->delay > SN_MAX_DELAY) return SN_EINVAL;
+    if (!p->w || !p->threshold || !p->leak || !p->reset || !p->refractory || !p->v || !p->r ||
+        (p->steps > 0 && !p->raster))
+        return SN_EINVAL;
+    if ((p->poisson_threshold == nullptr) != (p->poisson_amplitude == nullptr)) return SN_EINVAL;
+    if (p->steps == 0) return SN_OK;
+    cudaStream_t stream = (cudaStream_t)p->cuda_stream;
+
+    // executor sizing, the same rule as a dense context
+    const int block = 256;
+    const int words = (n + 31) / 32;
+    size_t smem_words = (size_t)words;
+    int gmax = 0;
+    if (max_grid_dense(block, &gmax, &smem_words) != cudaSuccess || gmax < 1) return SN_ECUDA;
+    const int g = std::min(gmax, (n + 31) / 32);
+    const int chunk = ((n + g - 1) / g + 31) / 32 * 32;
+    if (chunk > 2048) return SN_EUNSUPPORTED;
+    const int grid = gmax;
+    const int ntile = (n + 1023) / 1024;
+    const int S = std::max(1, (grid + ntile - 1) / ntile);
+    const int D1 = p->delay + 1;
+
+    // scratch layout: control | partial [S][n] | ring [D1][n] | zero Poisson table [n]
+    const size_t off_part = align256(sizeof(Control));
+    const size_t off_ring = off_part + align256((size_t)S * n * 4);
+    const size_t off_zero = off_ring + align256((size_t)D1 * n * 4);
+    const size_t need = off_zero + align256((size_t)n * 4);
+    if (need > kScratchBytes) return SN_EINVAL;   // beyond the fixed scratch
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return SN_ECUDA;
+    void *base = nullptr;
+    sn_status st = scratch_address(dev, &base);
+    if (st != SN_OK) return st;
+    unsigned char *b = (unsigned char *)base;
+
+    // zero what must start at zero: control block, partial sums, ring, table
+    if (cudaMemsetAsync(b, 0, need, stream) != cudaSuccess) return SN_ECUDA;
+
+    NetArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n = n; a.D1 = D1; a.words = words; a.cap = p->steps;
+    a.t0 = 0; a.steps = p->steps; a.chunk = chunk;
+    a.V = p->v; a.r = p->r;
+    a.th = p->threshold; a.lk = p->leak; a.rs = p->reset; a.R = p->refractory;
+    a.prate = p->poisson_threshold ? p->poisson_threshold : (const unsigned *)(b + off_zero);
+    a.pamp = p->poisson_amplitude ? (const void *)p->poisson_amplitude : (const void *)(b + off_zero);
+    {
+        // the same key derivation as sn_set_poisson for network 0
+        auto sm = [](unsigned long long x) {
+            unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+            z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+            z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+            return z ^ (z >> 31);
+        };
+        a.pkey = sm(p->seed ^ sm(0ull));
+    }
+    a.W = (float *)p->w;
+    a.partial = (float *)(b + off_part);
+    a.S = S;
+    a.dense_delay = p->delay;
+    a.ring = b + off_ring;
+    a.raster = p->raster;
+    a.ctl = (Control *)b;
+    if (launch_dense(a, grid, block, stream) != cudaSuccess) return SN_ECUDA;
+
+    // wait, then read the device status word (no allocation involved)
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return SN_ECUDA;
+    int status = 0;
+    if (cudaMemcpy(&status, b, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SN_ECUDA;
+    return (sn_status)status;
+}

@@ -45,6 +45,15 @@ class sn_synapses(C.Structure):
                 ("weight", C.c_void_p), ("delay", C.c_void_p)]
 
 
+class sn_dense_noalloc_args(C.Structure):
+    _fields_ = [("n", C.c_int32), ("delay", C.c_int32), ("steps", C.c_int32), ("pad", C.c_int32),
+                ("w", C.c_void_p), ("threshold", C.c_void_p), ("leak", C.c_void_p),
+                ("reset", C.c_void_p), ("refractory", C.c_void_p),
+                ("poisson_threshold", C.c_void_p), ("poisson_amplitude", C.c_void_p),
+                ("seed", C.c_uint64), ("v", C.c_void_p), ("r", C.c_void_p),
+                ("raster", C.c_void_p), ("cuda_stream", C.c_void_p)]
+
+
 _lib = None
 _lock = threading.Lock()
 _P = C.c_void_p
@@ -83,6 +92,8 @@ def lib():
                 f = getattr(L, name)
                 f.argtypes = args
                 f.restype = C.c_int
+            L.sn_run_dense_noalloc.argtypes = [C.POINTER(sn_dense_noalloc_args)]
+            L.sn_run_dense_noalloc.restype = C.c_int
             L.sn_last_error.argtypes = [_P]
             L.sn_last_error.restype = C.c_char_p
             L.sn_destroy.argtypes = [_P]
@@ -264,6 +275,23 @@ def sn_save(ctx: Ctx) -> bytes:
 
 def sn_load(ctx: Ctx, blob: bytes):
     _check(lib().sn_load(ctx.handle, blob, len(blob)), ctx)
+
+
+def sn_run_dense_noalloc(n, delay, steps, w, threshold, leak, reset, refractory, v, r, raster,
+                         poisson_threshold=None, poisson_amplitude=None, seed=0, stream=None):
+    """Dense run on caller-owned device tensors (torch CUDA tensors); the
+    library allocates nothing.  Raises SnError on a non-OK status."""
+    a = sn_dense_noalloc_args()
+    a.n, a.delay, a.steps = int(n), int(delay), int(steps)
+    a.w, a.threshold, a.leak, a.reset = _ptr(w), _ptr(threshold), _ptr(leak), _ptr(reset)
+    a.refractory = _ptr(refractory)
+    a.poisson_threshold, a.poisson_amplitude = _ptr(poisson_threshold), _ptr(poisson_amplitude)
+    a.seed = int(seed) & (2**64 - 1)
+    a.v, a.r, a.raster = _ptr(v), _ptr(r), _ptr(raster)
+    a.cuda_stream = stream
+    st = lib().sn_run_dense_noalloc(C.byref(a))
+    if st != SN_OK:
+        raise SnError(st, "sn_run_dense_noalloc failed")
 
 
 def sn_version() -> str:
