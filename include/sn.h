@@ -129,6 +129,34 @@ sn_status sn_create(const sn_config *cfg, const sn_neurons *neurons,
 sn_status sn_create_dense(const sn_config *cfg, const sn_neurons *neurons,
                           const float *w, int32_t delay, sn_ctx **out);
 
+/* Create a batched context: `nets` independent networks (neurons[b],
+ * synapses[b] as for sn_create, indices local to each network) simulated
+ * together, each with its own parameters.  Every network has 1..4096
+ * neurons; cfg->max_delay <= 16.  The context's neuron index space is the
+ * concatenation of the networks (network b's neuron j is global index
+ * offset_b + j); sn_set_input and sn_set_poisson take global indices (the
+ * Poisson stream of network b uses net = b and the local index j);
+ * sn_get_state concatenates the states, and every raster row holds each
+ * network's ceil(n_b/32) words in network order.  sn_run advances all
+ * networks by the same number of steps in one persistent kernel launch,
+ * replayed from a CUDA graph.  STDP, weights and checkpoints are not
+ * available for batched contexts (SN_EUNSUPPORTED / SN_ESTATE). */
+sn_status sn_create_batch(const sn_config *cfg, int32_t nets, const sn_neurons *neurons,
+                          const sn_synapses *synapses, sn_ctx **out);
+
+/* Executor mapping of a batched context: networks with at most warp_max_n
+ * neurons (0..512) run on a single warp, larger ones on a whole block; a
+ * network's pending-input ring is held in shared memory while it runs when
+ * it fits ring_smem_bytes (per block; a warp gets an eighth).  Results do
+ * not depend on the mapping. */
+sn_status sn_batch_config(sn_ctx *ctx, int32_t warp_max_n, int32_t ring_smem_bytes);
+
+/* Time every mapping of a fixed candidate set on `trial_steps` steps of the
+ * context's own networks and inputs, keep the fastest, then reset the
+ * dynamic state (as sn_reset).  *best_ms (may be NULL) receives the time of
+ * the chosen mapping.  Batched contexts only. */
+sn_status sn_autotune(sn_ctx *ctx, int32_t trial_steps, float *best_ms);
+
 /* Replace the explicit external input (Section 2.1, third step of a
  * timestep): event e adds value[e] to neuron[e] at absolute step step[e] >= 0.
  * Events of one (step, neuron) are summed in the order given.  nev = 0 clears
@@ -147,6 +175,13 @@ sn_status sn_set_input(sn_ctx *ctx, int64_t nev, const int32_t *step,
  * [0, 1).  nsrc = 0 clears the sources. */
 sn_status sn_set_poisson(sn_ctx *ctx, int32_t nsrc, const int32_t *neuron,
                          const float *rate, const float *amplitude, uint64_t seed);
+
+/* sn_set_poisson with the stream's network index given explicitly: the
+ * sources of a single network use key = SplitMix64(seed ^ SplitMix64(net)),
+ * so a single context can reproduce network `net` of a batched context.
+ * Single networks only (SN_ESTATE otherwise). */
+sn_status sn_set_poisson_stream(sn_ctx *ctx, int32_t nsrc, const int32_t *neuron, const float *rate,
+                                const float *amplitude, uint64_t seed, uint64_t net);
 
 /* Enable (enable = 1) or disable pair-based STDP (Section 2.1 names STDP but
  * gives no formula; this is the trace form).  Each neuron keeps a trace

@@ -30,9 +30,10 @@ def _theta(wl):
     return np.asarray(np.asarray(wl["threshold"], np.float32), np.float64)
 
 
-def check_int_run(wl, raster, v, r, steps, state=None):
-    """Whole-run equality for integer networks.  Returns the oracle state."""
-    st, want, _ = O.run(wl, O.INT, steps, state=state)
+def check_int_run(wl, raster, v, r, steps, state=None, **run_kw):
+    """Whole-run equality for integer networks.  Returns the oracle state.
+    run_kw (net_index, poisson_seed) go to oracle.run."""
+    st, want, _ = O.run(wl, O.INT, steps, state=state, **run_kw)
     bad = np.nonzero((raster != want).any(axis=1))[0]
     if bad.size:
         t = int(bad[0])
@@ -46,10 +47,10 @@ def check_int_run(wl, raster, v, r, steps, state=None):
     return st
 
 
-def check_float_run(wl, raster, v, r, steps):
+def check_float_run(wl, raster, v, r, steps, **run_kw):
     """Whole-run comparison for float networks.  Returns (first divergence
     step or None, oracle float32 state).  Raises on a violation."""
-    st, want, _ = O.run(wl, O.F32, steps, record_v=True)
+    st, want, _ = O.run(wl, O.F32, steps, record_v=True, **run_kw)
     th = _theta(wl)
     bad = np.nonzero((raster != want).any(axis=1))[0]
     if bad.size == 0:

@@ -15,112 +15,13 @@
 #include <string>
 #include <vector>
 
-#include "sn_internal.h"
+#include "sn_ctx.h"
 
 using namespace sn;
 
-struct sn_ctx {
-    int kind = KIND_SPARSE;
-    int dtype = SN_F32;
-    int n = 0;
-    int D = 1, D1 = 2;
-    unsigned flags = 0;
-    int cap = 1, words = 1;
-    cudaStream_t stream = nullptr;
-    long long step = 0;            // steps run so far (absolute step of the next run)
-    long long raster_from = 0;     // first step whose raster row is valid
-    long long m = 0;
-    bool all_delay_one = true;
-    int dense_delay = 1;
-    // executor
-    int grid = 1, block = 256, chunk = 32, S = 1;
-    // device memory
-    void *V = nullptr;
-    int *r = nullptr;
-    void *th = nullptr, *lk = nullptr, *rs = nullptr;
-    int *R = nullptr;
-    unsigned *prate = nullptr;
-    void *pamp = nullptr;
-    unsigned long long pkey = 0;
-    int *ev_off = nullptr, *ev_neuron = nullptr;
-    void *ev_val = nullptr;
-    int ev_nsteps = 0;
-    long long *rowptr = nullptr;
-    uint2 *syn = nullptr;
-    long long *colptr = nullptr;
-    uint2 *csc = nullptr;
-    long long *perm_inv = nullptr;  // input index -> CSR position (device)
-    void *ring = nullptr;
-    size_t ring_bytes = 0;
-    float *W = nullptr, *partial = nullptr;
-    unsigned *raster = nullptr;
-    float *trace = nullptr;
-    Control *ctl = nullptr;
-    // host copies
-    std::vector<long long> h_perm_inv;
-    // STDP
-    int stdp = 0;
-    float decay = 0, a_plus = 0, a_minus = 0, wmin = 0, wmax = 0;
-    int failed = 0;                // sticky device failure seen
-    std::string err;
-    std::vector<void *> allocs;
-};
-
-static thread_local std::string g_create_err;
+thread_local std::string g_create_err;
 
 namespace {
-
-sn_status fail(sn_ctx *c, sn_status s, const std::string &msg) {
-    if (c) c->err = msg; else g_create_err = msg;
-    return s;
-}
-
-sn_status cuda_fail(sn_ctx *c, cudaError_t e, const char *what) {
-    return fail(c, SN_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
-}
-
-#define SN_CUDA(ctx, call)                                           \
-    do {                                                             \
-        cudaError_t e_ = (call);                                     \
-        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);   \
-    } while (0)
-
-template <typename T>
-sn_status dalloc(sn_ctx *c, T **p, size_t bytes) {
-    void *q = nullptr;
-    if (bytes == 0) bytes = 16;
-    cudaError_t e = cudaMalloc(&q, bytes);
-    if (e != cudaSuccess) {
-        (void)cudaGetLastError();
-        return fail(c, SN_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
-    }
-    c->allocs.push_back(q);
-    *p = (T *)q;
-    return SN_OK;
-}
-
-void dfree(sn_ctx *c, void *p) {
-    if (!p) return;
-    auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
-    if (it != c->allocs.end()) c->allocs.erase(it);
-    cudaFree(p);
-}
-
-bool is_int_valued(float x) { return std::isfinite(x) && std::floor(x) == x && std::fabs(x) < 16777216.0f; }
-
-unsigned long long splitmix64(unsigned long long x) {
-    unsigned long long z = x + 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
-unsigned rate_threshold(float rate) {
-    double r = std::floor((double)rate * 4294967296.0);
-    if (!(r > 0)) return 0u;
-    if (r > 4294967295.0) return 4294967295u;
-    return (unsigned)r;
-}
 
 sn_status check_config(const sn_config *cfg) {
     if (!cfg) return fail(nullptr, SN_EINVAL, "cfg is NULL");
@@ -133,6 +34,32 @@ sn_status check_config(const sn_config *cfg) {
         return fail(nullptr, SN_EINVAL, "SN_EXEC_CTA and SN_EXEC_GRID are exclusive");
     return SN_OK;
 }
+
+sn_status size_sparse_executor(sn_ctx *c) {
+    const int n = c->n;
+    c->block = 256;
+    const bool cta = (c->flags & SN_EXEC_CTA) || (!(c->flags & SN_EXEC_GRID) && n <= 2048);
+    if (cta) {
+        c->grid = 1;
+        c->chunk = (n + 31) / 32 * 32;
+        if (c->chunk > 16384) return fail(nullptr, SN_EINVAL, "SN_EXEC_CTA supports n <= 16384");
+        return SN_OK;
+    }
+    int gmax = 0;
+    cudaError_t e = max_grid_sparse(c->dtype, 1, c->block, &gmax);
+    if (e != cudaSuccess) return fail(nullptr, SN_ECUDA, std::string("occupancy: ") + cudaGetErrorString(e));
+    if (gmax < 1) return fail(nullptr, SN_ECUDA, "no resident blocks possible");
+    int g = std::min(gmax, (n + 31) / 32);
+    int chunk = ((n + g - 1) / g + 31) / 32 * 32;
+    if (chunk > 1024) return fail(nullptr, SN_EUNSUPPORTED, "network too large for the grid executor");
+    c->chunk = chunk;
+    c->grid = (n + chunk - 1) / chunk;
+    return SN_OK;
+}
+
+}  // namespace
+
+namespace sn {
 
 // Neuron parameters to device arrays (float or int32 according to dtype).
 sn_status upload_neurons(sn_ctx *c, const sn_neurons *nr) {
@@ -193,29 +120,7 @@ void destroy_all(sn_ctx *c) {
     c->allocs.clear();
 }
 
-sn_status size_sparse_executor(sn_ctx *c) {
-    const int n = c->n;
-    c->block = 256;
-    const bool cta = (c->flags & SN_EXEC_CTA) || (!(c->flags & SN_EXEC_GRID) && n <= 2048);
-    if (cta) {
-        c->grid = 1;
-        c->chunk = (n + 31) / 32 * 32;
-        if (c->chunk > 16384) return fail(nullptr, SN_EINVAL, "SN_EXEC_CTA supports n <= 16384");
-        return SN_OK;
-    }
-    int gmax = 0;
-    cudaError_t e = max_grid_sparse(c->dtype, 1, c->block, &gmax);
-    if (e != cudaSuccess) return fail(nullptr, SN_ECUDA, std::string("occupancy: ") + cudaGetErrorString(e));
-    if (gmax < 1) return fail(nullptr, SN_ECUDA, "no resident blocks possible");
-    int g = std::min(gmax, (n + 31) / 32);
-    int chunk = ((n + g - 1) / g + 31) / 32 * 32;
-    if (chunk > 1024) return fail(nullptr, SN_EUNSUPPORTED, "network too large for the grid executor");
-    c->chunk = chunk;
-    c->grid = (n + chunk - 1) / chunk;
-    return SN_OK;
-}
-
-}  // namespace
+}  // namespace sn
 
 extern "C" {
 
@@ -355,7 +260,8 @@ sn_status sn_create_dense(const sn_config *cfg, const sn_neurons *nr, const floa
 
 sn_status sn_set_input(sn_ctx *c, int64_t nev, const int32_t *step, const int32_t *neuron, const float *value) {
     if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
-    if (c->kind != KIND_SPARSE && c->kind != KIND_DENSE) return fail(c, SN_ESTATE, "explicit events: single networks only");
+    if (c->kind != KIND_SPARSE && c->kind != KIND_DENSE && c->kind != KIND_BATCH)
+        return fail(c, SN_ESTATE, "wrong context kind");
     if (nev < 0 || (nev > 0 && (!step || !neuron || !value))) return fail(c, SN_EINVAL, "bad event arrays");
     int max_step = -1;
     for (long long e = 0; e < nev; ++e) {
@@ -414,8 +320,10 @@ sn_status sn_set_input(sn_ctx *c, int64_t nev, const int32_t *step, const int32_
 sn_status sn_set_poisson(sn_ctx *c, int32_t nsrc, const int32_t *neuron, const float *rate,
                          const float *amp, uint64_t seed) {
     if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
-    if (c->kind != KIND_SPARSE && c->kind != KIND_DENSE) return fail(c, SN_ESTATE, "wrong context kind");
+    if (c->kind != KIND_SPARSE && c->kind != KIND_DENSE && c->kind != KIND_BATCH)
+        return fail(c, SN_ESTATE, "wrong context kind");
     if (nsrc < 0 || (nsrc > 0 && (!neuron || !rate || !amp))) return fail(c, SN_EINVAL, "bad source arrays");
+    if (c->kind == KIND_BATCH) return batch_set_poisson(c, nsrc, neuron, rate, amp, seed);
     const int n = c->n;
     std::vector<unsigned> thr(n, 0u);
     std::vector<float> af(n, 0.0f);
@@ -436,13 +344,23 @@ sn_status sn_set_poisson(sn_ctx *c, int32_t nsrc, const int32_t *neuron, const f
     SN_CUDA(c, cudaMemcpy(c->prate, thr.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
     SN_CUDA(c, cudaMemcpy(c->pamp, c->dtype == SN_F32 ? (const void *)af.data() : (const void *)ai.data(),
                           (size_t)n * 4, cudaMemcpyHostToDevice));
-    c->pkey = splitmix64(seed ^ splitmix64(0ull));
+    c->pkey = host_splitmix64(seed ^ host_splitmix64(0ull));
+    return SN_OK;
+}
+
+sn_status sn_set_poisson_stream(sn_ctx *c, int32_t nsrc, const int32_t *neuron, const float *rate,
+                                const float *amp, uint64_t seed, uint64_t net) {
+    if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
+    if (c->kind != KIND_SPARSE && c->kind != KIND_DENSE) return fail(c, SN_ESTATE, "single networks only");
+    sn_status s = sn_set_poisson(c, nsrc, neuron, rate, amp, seed);
+    if (s) return s;
+    c->pkey = host_splitmix64(seed ^ host_splitmix64(net));
     return SN_OK;
 }
 
 sn_status sn_stdp(sn_ctx *c, float decay, float a_plus, float a_minus, float wmin, float wmax, int32_t enable) {
     if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
-    if (c->kind != KIND_SPARSE && c->kind != KIND_DENSE) return fail(c, SN_ESTATE, "wrong context kind");
+    if (c->kind != KIND_SPARSE && c->kind != KIND_DENSE) return fail(c, SN_EUNSUPPORTED, "STDP: single networks only");
     if (!enable) { c->stdp = 0; return SN_OK; }
     if (c->dtype != SN_F32) return fail(c, SN_EUNSUPPORTED, "STDP needs an SN_F32 network");
     if (!c->all_delay_one)
@@ -503,6 +421,13 @@ sn_status sn_run(sn_ctx *c, int32_t steps) {
     if (steps < 0) return fail(c, SN_EINVAL, "steps < 0");
     if (steps == 0) return SN_OK;
     if (c->step + steps >= (1ll << 31)) return fail(c, SN_EINVAL, "step counter would exceed 2^31");
+    if (c->kind == KIND_BATCH) {
+        sn_status st = batch_run(c, steps);
+        if (st) return st;
+        c->step += steps;
+        if (c->step - c->raster_from > c->cap) c->raster_from = c->step - c->cap;
+        return SN_OK;
+    }
     if (c->kind != KIND_SPARSE && c->kind != KIND_DENSE) return fail(c, SN_ESTATE, "wrong context kind");
     NetArgs a;
     memset(&a, 0, sizeof(a));
@@ -528,7 +453,8 @@ sn_status sn_run(sn_ctx *c, int32_t steps) {
 
 sn_status sn_reset(sn_ctx *c) {
     if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
-    if (c->kind != KIND_SPARSE && c->kind != KIND_DENSE) return fail(c, SN_ESTATE, "wrong context kind");
+    if (c->kind != KIND_SPARSE && c->kind != KIND_DENSE && c->kind != KIND_BATCH)
+        return fail(c, SN_ESTATE, "wrong context kind");
     const size_t vb = (size_t)c->n * 4;
     SN_CUDA(c, cudaMemcpyAsync(c->V, c->rs, vb, cudaMemcpyDeviceToDevice, c->stream));
     SN_CUDA(c, cudaMemsetAsync(c->r, 0, vb, c->stream));
@@ -741,6 +667,8 @@ sn_status sn_load(sn_ctx *c, const void *buf, size_t size) {
 void sn_destroy(sn_ctx *c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
     destroy_all(c);
     delete c;
 }

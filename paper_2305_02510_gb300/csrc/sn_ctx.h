@@ -1,0 +1,141 @@
+// Host-side context of the C ABI and helpers shared by the host translation
+// units (sn_api.cu, sn_batch_api.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "sn_internal.h"
+
+using namespace sn;
+
+struct sn_ctx {
+    int kind = KIND_SPARSE;
+    int dtype = SN_F32;
+    int n = 0;
+    int D = 1, D1 = 2;
+    unsigned flags = 0;
+    int cap = 1, words = 1;
+    cudaStream_t stream = nullptr;
+    long long step = 0;            // steps run so far (absolute step of the next run)
+    long long raster_from = 0;     // first step whose raster row is valid
+    long long m = 0;
+    bool all_delay_one = true;
+    int dense_delay = 1;
+    // executor
+    int grid = 1, block = 256, chunk = 32, S = 1;
+    // device memory
+    void *V = nullptr;
+    int *r = nullptr;
+    void *th = nullptr, *lk = nullptr, *rs = nullptr;
+    int *R = nullptr;
+    unsigned *prate = nullptr;
+    void *pamp = nullptr;
+    unsigned long long pkey = 0;
+    int *ev_off = nullptr, *ev_neuron = nullptr;
+    void *ev_val = nullptr;
+    int ev_nsteps = 0;
+    long long *rowptr = nullptr;
+    uint2 *syn = nullptr;
+    long long *colptr = nullptr;
+    uint2 *csc = nullptr;
+    long long *perm_inv = nullptr;  // input index -> CSR position (device)
+    void *ring = nullptr;
+    size_t ring_bytes = 0;
+    float *W = nullptr, *partial = nullptr;
+    unsigned *raster = nullptr;
+    float *trace = nullptr;
+    Control *ctl = nullptr;
+    // host copies
+    std::vector<long long> h_perm_inv;
+    // STDP
+    int stdp = 0;
+    float decay = 0, a_plus = 0, a_minus = 0, wmin = 0, wmax = 0;
+    // batched networks
+    int nets = 0;
+    std::vector<int> h_net_n;          // neurons of each network
+    int *net_off = nullptr, *word_off = nullptr, *cta_order = nullptr, *warp_order = nullptr;
+    long long *ring_off = nullptr;
+    unsigned long long *pkeys = nullptr;
+    unsigned short *sidx = nullptr;
+    unsigned *sw = nullptr;
+    int n_cta = 0, n_warp = 0;
+    int warp_max_n = 128, ring_smem = 96 * 1024, batch_grid = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    cudaGraphNode_t graph_kernel = nullptr;
+    int failed = 0;                // sticky device failure seen
+    std::string err;
+    std::vector<void *> allocs;
+};
+
+extern thread_local std::string g_create_err;
+
+namespace sn {
+
+inline sn_status fail(sn_ctx *c, sn_status s, const std::string &msg) {
+    if (c) c->err = msg; else g_create_err = msg;
+    return s;
+}
+
+inline sn_status cuda_fail(sn_ctx *c, cudaError_t e, const char *what) {
+    return fail(c, SN_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define SN_CUDA(ctx, call)                                           \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);   \
+    } while (0)
+
+template <typename T>
+inline sn_status dalloc(sn_ctx *c, T **p, size_t bytes) {
+    void *q = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(c, SN_ENOMEM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+    }
+    c->allocs.push_back(q);
+    *p = (T *)q;
+    return SN_OK;
+}
+
+inline void dfree(sn_ctx *c, void *p) {
+    if (!p) return;
+    auto it = std::find(c->allocs.begin(), c->allocs.end(), p);
+    if (it != c->allocs.end()) c->allocs.erase(it);
+    cudaFree(p);
+}
+
+inline bool is_int_valued(float x) { return std::isfinite(x) && std::floor(x) == x && std::fabs(x) < 16777216.0f; }
+
+inline unsigned long long host_splitmix64(unsigned long long x) {
+    unsigned long long z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+inline unsigned rate_threshold(float rate) {
+    double r = std::floor((double)rate * 4294967296.0);
+    if (!(r > 0)) return 0u;
+    if (r > 4294967295.0) return 4294967295u;
+    return (unsigned)r;
+}
+
+// shared by sn_api.cu and sn_batch_api.cu
+sn_status upload_neurons(sn_ctx *c, const sn_neurons *nr);
+sn_status alloc_common(sn_ctx *c, const sn_config *cfg);
+void destroy_all(sn_ctx *c);
+sn_status batch_run(sn_ctx *c, int steps);
+sn_status batch_set_poisson(sn_ctx *c, int32_t nsrc, const int32_t *neuron, const float *rate,
+                            const float *amp, uint64_t seed);
+
+}  // namespace sn

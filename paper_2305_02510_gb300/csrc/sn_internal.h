@@ -27,6 +27,7 @@ struct Control {
     unsigned long long spikes;        // total spikes
     unsigned long long events;        // total synaptic events
     GridBarrier bar;
+    unsigned queue[2];                // batched work queues: next block item, next warp item
 };
 
 // Wall-clock limit of one grid-barrier wait before the kernel gives up and
@@ -74,6 +75,46 @@ struct NetArgs {
     float *trace;                     // [2][n], buffer (t & 1) holds x(t)
     Control *ctl;
 };
+
+// Arguments of the batched kernel: many independent networks, each run for
+// all steps by one block or one warp.
+struct BatchArgs {
+    int nets, t0, steps, cap, total_words, D1;
+    const int *net_off;               // [nets + 1] first neuron of each network
+    const int *word_off;              // [nets + 1] first raster word of each network
+    const long long *ring_off;        // [nets] first ring element of each network (D1 * n_b)
+    const unsigned long long *pkey;   // [nets] Poisson stream key
+    const int *cta_order;             // networks run by whole blocks, largest first
+    int n_cta;
+    const int *warp_order;            // networks run by single warps
+    int n_warp;
+    void *V;
+    int *r;
+    const void *th, *lk, *rs;
+    const int *R;
+    const unsigned *prate;
+    const void *pamp;
+    const int *ev_off;
+    int ev_nsteps;
+    const int *ev_neuron;
+    const void *ev_val;
+    const long long *rowptr;          // [sum n + 1] over global neuron index
+    const unsigned short *sidx;       // post (12 bits) | (delay-1) << 12
+    const unsigned *sw;               // weight bits
+    void *ring;                       // all networks' pending-input rings
+    unsigned *raster;                 // [cap][total_words]
+    int ring_smem;                    // bytes of shared ring arena per block
+    Control *ctl;
+};
+
+constexpr int kBatchBlock = 256;
+constexpr int kBatchMaxN = 4096;      // largest network of a batched context
+constexpr int kBatchMaxDelay = 16;
+
+cudaError_t launch_batch(const BatchArgs &a, int dtype, int grid, cudaStream_t s);
+cudaError_t batch_kernel_node(int dtype, void **fn);
+cudaError_t max_grid_batch(int dtype, int ring_smem, int *grid);
+size_t batch_smem(int ring_smem);
 
 // Launchers (kernels live in sn_kernels.cu).  Return a CUDA error code.
 cudaError_t launch_sparse(const NetArgs &a, int dtype, int grid, int block, cudaStream_t s);

@@ -73,8 +73,13 @@ def lib():
                               C.POINTER(_P)],
                 "sn_create_dense": [C.POINTER(sn_config), C.POINTER(sn_neurons), _P, C.c_int32,
                                     C.POINTER(_P)],
+                "sn_create_batch": [C.POINTER(sn_config), C.c_int32, C.POINTER(sn_neurons),
+                                    C.POINTER(sn_synapses), C.POINTER(_P)],
+                "sn_batch_config": [_P, C.c_int32, C.c_int32],
+                "sn_autotune": [_P, C.c_int32, C.POINTER(C.c_float)],
                 "sn_set_input": [_P, C.c_int64, _P, _P, _P],
                 "sn_set_poisson": [_P, C.c_int32, _P, _P, _P, C.c_uint64],
+                "sn_set_poisson_stream": [_P, C.c_int32, _P, _P, _P, C.c_uint64, C.c_uint64],
                 "sn_stdp": [_P, C.c_float, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int32],
                 "sn_run": [_P, C.c_int32],
                 "sn_reset": [_P],
@@ -189,6 +194,56 @@ def sn_create_dense(threshold, leak, reset, refractory, w, delay=1, *, max_delay
     return Ctx(h, nr.n, SN_F32, (nr.n + 31) // 32, "dense", nr.n * nr.n)
 
 
+def sn_create_batch(nets, *, dtype=SN_F32, max_delay, record_steps=0, stream=None) -> Ctx:
+    """nets: list of dicts with threshold, leak, reset, refractory, pre, post,
+    weight, delay (local indices)."""
+    keep = []
+    B = len(nets)
+    NR = (sn_neurons * B)()
+    SY = (sn_synapses * B)()
+    total = 0
+    words = 0
+    for b, d in enumerate(nets):
+        nr = _neurons(d["threshold"], d["leak"], d["reset"], d["refractory"], keep)
+        NR[b] = nr
+        pre, post = _arr(d["pre"], np.int32), _arr(d["post"], np.int32)
+        w, dl = _arr(d["weight"], np.float32), _arr(d["delay"], np.int32)
+        keep += [pre, post, w, dl]
+        SY[b].m = pre.size
+        SY[b].pre, SY[b].post = _ptr(pre) if pre.size else None, _ptr(post) if post.size else None
+        SY[b].weight, SY[b].delay = _ptr(w) if w.size else None, _ptr(dl) if dl.size else None
+        total += nr.n
+        words += (nr.n + 31) // 32
+    cfg = _config(dtype, max_delay, 0, record_steps, stream)
+    h = _P()
+    _check(lib().sn_create_batch(C.byref(cfg), B, NR, SY, C.byref(h)))
+    ctx = Ctx(h, total, cfg.dtype, words, "batch", 0)
+    ctx.net_n = [int(np.asarray(d["threshold"]).size) for d in nets]
+    return ctx
+
+
+def sn_batch_config(ctx: Ctx, warp_max_n: int, ring_smem_bytes: int):
+    _check(lib().sn_batch_config(ctx.handle, int(warp_max_n), int(ring_smem_bytes)), ctx)
+
+
+def sn_autotune(ctx: Ctx, trial_steps: int = 20) -> float:
+    ms = C.c_float(0)
+    _check(lib().sn_autotune(ctx.handle, int(trial_steps), C.byref(ms)), ctx)
+    return ms.value
+
+
+def split_batch_raster(bits, net_n):
+    """Raster words of a batched context -> list of per-network uint8
+    rasters [steps, n_b]."""
+    out = []
+    w0 = 0
+    for n in net_n:
+        w = (n + 31) // 32
+        out.append(unpack_raster(np.ascontiguousarray(bits[:, w0:w0 + w]), n))
+        w0 += w
+    return out
+
+
 def sn_set_input(ctx: Ctx, step, neuron, value):
     s, j, v = _arr(step, np.int32), _arr(neuron, np.int32), _arr(value, np.float32)
     _check(lib().sn_set_input(ctx.handle, s.size, _ptr(s) if s.size else None,
@@ -200,6 +255,13 @@ def sn_set_poisson(ctx: Ctx, neuron, rate, amplitude, seed):
     _check(lib().sn_set_poisson(ctx.handle, j.size, _ptr(j) if j.size else None,
                                 _ptr(r) if r.size else None, _ptr(a) if a.size else None,
                                 int(seed) & (2**64 - 1)), ctx)
+
+
+def sn_set_poisson_stream(ctx: Ctx, neuron, rate, amplitude, seed, net):
+    j, r, a = _arr(neuron, np.int32), _arr(rate, np.float32), _arr(amplitude, np.float32)
+    _check(lib().sn_set_poisson_stream(ctx.handle, j.size, _ptr(j) if j.size else None,
+                                       _ptr(r) if r.size else None, _ptr(a) if a.size else None,
+                                       int(seed) & (2**64 - 1), int(net) & (2**64 - 1)), ctx)
 
 
 def sn_stdp(ctx: Ctx, decay, a_plus, a_minus, wmin, wmax, enable=True):
@@ -328,4 +390,24 @@ def from_workload(wl, *, record_steps=None, flags=SN_AUTO, stream=None) -> Ctx:
     if wl.get("stdp"):
         sd = wl["stdp"]
         sn_stdp(ctx, sd["decay"], sd["a_plus"], sd["a_minus"], sd["wmin"], sd["wmax"], True)
+    return ctx
+
+
+def from_batch_workloads(nets, *, record_steps=None, stream=None) -> Ctx:
+    """Batched context for a list of workload dicts (all sparse, same dtype);
+    network b of the list is stream b of the batch's Poisson input, whose
+    seed is taken from the first network."""
+    rec = nets[0]["steps"] if record_steps is None else record_steps
+    D = max(int(w["max_delay"]) for w in nets)
+    ctx = sn_create_batch(nets, dtype=nets[0]["dtype"], max_delay=D, record_steps=rec, stream=stream)
+    off = np.cumsum([0] + [w["n"] for w in nets])
+    nj = [np.asarray(w["poisson"]["neuron"], np.int64) + off[b] for b, w in enumerate(nets)]
+    if sum(x.size for x in nj):
+        sn_set_poisson(ctx, np.concatenate(nj), np.concatenate([w["poisson"]["rate"] for w in nets]),
+                       np.concatenate([w["poisson"]["amplitude"] for w in nets]), nets[0]["poisson"]["seed"])
+    evs = [(np.asarray(w["events"]["step"]), np.asarray(w["events"]["neuron"]) + off[b],
+            np.asarray(w["events"]["value"])) for b, w in enumerate(nets)]
+    if sum(e[0].size for e in evs):
+        sn_set_input(ctx, np.concatenate([e[0] for e in evs]), np.concatenate([e[1] for e in evs]),
+                     np.concatenate([e[2] for e in evs]))
     return ctx

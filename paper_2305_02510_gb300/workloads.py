@@ -242,24 +242,56 @@ def random_small(seed: int, n: int | None = None, integer: bool = True,
     return wl
 
 
+def bernoulli_pairs_skip(rng, n: int, p: float):
+    """Directed pairs (i, j), i != j, each present with probability p, drawn
+    by geometric gaps between successive present pairs in row-major order of
+    the n(n-1) off-diagonal positions (the same Bernoulli process as
+    bernoulli_pairs at O(m) cost).  Sorted by (pre, post)."""
+    total = n * (n - 1)
+    if total == 0 or p <= 0.0:
+        return np.zeros(0, np.int32), np.zeros(0, np.int32)
+    mean = total * p
+    chunks = []
+    last = -1
+    while True:
+        k = int(mean - (last + 1) * p + 6.0 * math.sqrt(mean + 1.0) + 64)
+        gaps = rng.geometric(p, size=max(k, 64))
+        pos = last + np.cumsum(gaps, dtype=np.int64)
+        done = pos[-1] >= total
+        pos = pos[pos < total]
+        chunks.append(pos)
+        if done:
+            break
+        last = int(pos[-1]) if pos.size else last
+    lin = np.concatenate(chunks)
+    i = lin // (n - 1)
+    jj = lin - i * (n - 1)
+    j = jj + (jj >= i)
+    return i.astype(np.int32), j.astype(np.int32)
+
+
 def batched_nets(count: int = 4096, seed: int = SEED_BASE + 4, steps: int = 500,
-                 nmin: int = 64, nmax: int = 4096):
+                 nmin: int = 64, nmax: int = 4096, first: int = 0):
     """Independent nets for the batched simulation: N log-uniform in
     [nmin, nmax], connection probability U(0.01, 0.2), thresholds U(0.5, 1.5),
-    leaks U(0, 0.2), refractory U{0..3}, delays U{1..8}, weights
+    leaks U(0, 0.2), reset 0, refractory U{0..3}, delays U{1..8}, weights
     N(0, 1)/sqrt(p N); Poisson 0.05/step into 10% of each net's neurons with
-    amplitude 2 * max threshold.  Returns a list of workload dicts."""
-    rng = _rng(seed)
+    amplitude 2 * max threshold.  Network b is drawn from its own seed
+    sequence, so any subset [first, first + count) is the same networks as in
+    the full batch.  Weights are float32, indices int32.  Returns a list of
+    workload dicts."""
+    top = np.random.default_rng(np.random.SeedSequence(int(seed)))
+    sizes = np.floor(np.exp(top.uniform(math.log(nmin), math.log(nmax), size=first + count)))
+    probs = top.uniform(0.01, 0.2, size=first + count)
     nets = []
-    for b in range(count):
-        n = int(math.floor(math.exp(rng.uniform(math.log(nmin), math.log(nmax)))))
-        n = max(nmin, min(nmax, n))
-        p = float(rng.uniform(0.01, 0.2))
+    for b in range(first, first + count):
+        n = int(min(nmax, max(nmin, sizes[b])))
+        p = float(probs[b])
         sub = np.random.default_rng(np.random.SeedSequence([int(seed), b]))
-        pre, post = bernoulli_pairs(sub, n, p)
+        pre, post = bernoulli_pairs_skip(sub, n, p)
         m = pre.size
         delay = sub.integers(1, 9, size=m).astype(np.int32)
-        w = sub.normal(0.0, 1.0, size=m) / math.sqrt(p * n)
+        w = (sub.standard_normal(size=m, dtype=np.float32) / np.float32(math.sqrt(p * n)))
         th = sub.uniform(0.5, 1.5, size=n)
         lk = sub.uniform(0.0, 0.2, size=n)
         R = sub.integers(0, 4, size=n).astype(np.int32)
@@ -267,7 +299,7 @@ def batched_nets(count: int = 4096, seed: int = SEED_BASE + 4, steps: int = 500,
         wl.update(pre=pre, post=post, weight=w, delay=delay)
         ni = max(1, n // 10)
         inputs = np.sort(sub.choice(n, size=ni, replace=False)).astype(np.int32)
-        wl["poisson"] = _poisson(inputs, 0.05, 2.0 * float(th.max()), seed * 7 + 4)
+        wl["poisson"] = _poisson(inputs, 0.05, 2.0 * float(np.float32(th).max()), seed * 7 + 4)
         wl["net_index"] = b
         wl["name"] = f"batched-{b}"
         nets.append(wl)
