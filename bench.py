@@ -121,6 +121,90 @@ def oracle_sample(wl, warm=40, timed=60):
                                 f"M={len(wl['pre'])}), single-threaded C oracle, float32 mirror"
 
 
+def timed_runs(S, torch, stream, flush, ctx, steps, reps, warm=1):
+    """Device time of `reps` runs of `steps` timesteps from the initial state,
+    L2 flushed before each; returns (mean ms, spikes, events) per run."""
+    out = []
+    for k in range(warm + reps):
+        S.sn_reset(ctx)
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        S.sn_run(ctx, steps)
+        b.record(stream)
+        S.sn_sync(ctx)
+        _, spk, ev = S.sn_get_counters(ctx)
+        if k >= warm:
+            out.append((a.elapsed_time(b), spk, ev))
+    return (sum(x[0] for x in out) / reps, sum(x[1] for x in out) / reps, sum(x[2] for x in out) / reps)
+
+
+def extras(S, W, torch, stream, flush):
+    """Dense all-to-all network (16384 neurons, 1000 timesteps) without and
+    with STDP; 4096 batched networks (500 timesteps) in one launch against
+    the plain path (one single-network context and launch per network)."""
+    peak, src = peaks()
+    res = {}
+    # dense, delay 1
+    for stdp in (False, True):
+        wl = W.large_dense(stdp=stdp, steps=1000)
+        ctx = S.from_workload(wl, record_steps=1000, stream=stream.cuda_stream)
+        ms, spk, ev = timed_runs(S, torch, stream, flush, ctx, 1000, 2)
+        n = wl["n"]
+        # per spike: its weight row (4n B); per neuron and step: the update's
+        # state traffic
+        abytes = spk * 4 * n + 1000 * n * STATE_BYTES
+        if stdp:
+            # spiking rows written back; spiking columns read+written in every
+            # other row (one 32 B sector per element at this density)
+            abytes += spk * 4 * n + spk * (n - spk / 1000) * 8
+        res["dense_stdp" if stdp else "dense"] = {
+            "workload": wl["name"], "neurons": n, "timesteps": 1000, "ms": ms,
+            "synaptic_events_per_s": ev / (ms / 1e3), "timesteps_per_s": 1000 / (ms / 1e3),
+            "spikes_per_timestep": spk / 1000,
+            "roofline": {"bound": "hbm", "achieved": abytes / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": abytes / (ms / 1e3) / 1e9 / peak, "peak_source": src,
+                         "kernel": "dense_kernel<%s>" % ("true" if stdp else "false")}}
+        del ctx
+    res["dense_stdp"]["stdp_overhead"] = res["dense_stdp"]["ms"] / res["dense"]["ms"]
+    # batched networks against the plain per-network path
+    nets = W.batched_nets(count=4096, steps=500)
+    ctx = S.from_batch_workloads(nets, record_steps=500, stream=stream.cuda_stream)
+    S.sn_autotune(ctx, 10)
+    ms, spk, ev = timed_runs(S, torch, stream, flush, ctx, 500, 3)
+    del ctx
+    plain = []
+    for b, wl in enumerate(nets):
+        c = S.sn_create(wl["threshold"], wl["leak"], wl["reset"], wl["refractory"], wl["pre"], wl["post"],
+                        wl["weight"], wl["delay"], max_delay=8, record_steps=1, stream=stream.cuda_stream)
+        po = wl["poisson"]
+        S.sn_set_poisson_stream(c, po["neuron"], po["rate"], po["amplitude"], po["seed"], b)
+        plain.append(c)
+    for c in plain[:64]:
+        S.sn_run(c, 500)
+    torch.cuda.synchronize()
+    for c in plain:
+        S.sn_reset(c)
+    flush.zero_()
+    a, b2 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for c in plain:
+        S.sn_run(c, 500)
+    b2.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = a.elapsed_time(b2)
+    plain_ev = sum(S.sn_get_counters(c)[2] for c in plain)
+    del plain
+    res["batched"] = {
+        "workload": "4096 networks, N log-uniform [64, 4096], p U(0.01, 0.2), delays 1..8",
+        "networks": len(nets), "neurons": int(sum(w["n"] for w in nets)),
+        "synapses": int(sum(len(w["pre"]) for w in nets)), "timesteps": 500, "ms": ms,
+        "synaptic_events_per_s": ev / (ms / 1e3), "network_timesteps_per_s": len(nets) * 500 / (ms / 1e3),
+        "plain_ms": plain_ms, "plain_synaptic_events_per_s": plain_ev / (plain_ms / 1e3),
+        "speedup_vs_plain": plain_ms / ms, "launches": 1, "plain_launches": len(nets)}
+    return res
+
+
 def run_reference(args, wl, rank):
     if rank != 0:
         return
@@ -161,6 +245,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--timesteps", type=int, default=TIMESTEPS)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the dense, STDP and batched measurements beside the headline")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -275,6 +361,8 @@ def main():
             "gpu_launches": args.steps,
             "clocks": clk.summary(),
         }
+        if not args.no_extras and world == 1:
+            line["extra"] = extras(S, W, torch, stream, flush)
         if not args.no_cpu_baseline:
             ev_s, ts_s, sample = oracle_sample(wl)
             line["cpu_baseline"] = {"value": ev_s, "unit": UNIT, "cores": 1, "kind": "oracle",
