@@ -249,6 +249,54 @@ const char *sn_last_error(const sn_ctx *ctx);
 void sn_destroy(sn_ctx *ctx);
 
 /* ------------------------------------------------------------------------
+ * Feedforward spiking network trained by backpropagation through time.  The
+ * paper names SNN training only as a use (Section 1); the forward pass is the
+ * simulator's timestep (Section 2.1 order and rules) applied layer by layer.
+ *
+ * Layer l = 1..L maps sizes[l-1] inputs to sizes[l] LIF neurons; synapse
+ * i -> j has weight W_l[i][j] (row-major [sizes[l-1]][sizes[l]]) and delay
+ * D_l[i][j] in 1..4, so a spike of layer l-1 at step t reaches layer l at
+ * t + D.  Layer 0 is the input spike train.  The output is the spike count
+ * of each neuron of layer L.  All neurons share the parameters in
+ * sn_ff_params.  Gradients use the fast-sigmoid surrogate
+ * ds/du = 1 / (1 + slope |u - threshold|)^2 (u = state compared with the
+ * threshold), a detached reset, a constant refractory mask and the clamped
+ * leak's derivative [|V - reset| > leak]; delays get no gradient.  The
+ * forward keeps every spike (as bits) and the membrane state every
+ * checkpoint_every steps; the backward recomputes each segment's states from
+ * its checkpoint.  Results do not depend on thread timing.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    float threshold, leak, reset;
+    int32_t refractory;
+    float surrogate_slope;
+    int32_t checkpoint_every;       /* 1, 2, 5, 10 or 20                          */
+} sn_ff_params;
+
+/* delays[l] (host, [sizes[l]][sizes[l+1]] bytes for layer l+1) are copied.
+ * batch >= 1, steps >= 1; every size in 1..65536. */
+sn_status sn_create_ff(const sn_config *cfg, int32_t layers, const int32_t *sizes,
+                       const uint8_t *const *delays, const sn_ff_params *params, int32_t batch,
+                       int32_t steps, sn_ctx **out);
+
+/* Forward pass.  input: device [steps][batch][sizes[0]] bytes (nonzero =
+ * spike); w: host array of `layers` device pointers to the weights (kept
+ * unchanged until the matching sn_backward); counts: device
+ * [batch][sizes[L]] floats out. */
+sn_status sn_ff_forward(sn_ctx *ctx, const uint8_t *input, const float *const *w, float *counts);
+
+/* Backward pass of the last forward: grad_counts = dLoss/dcounts (device
+ * [batch][sizes[L]]); grad_w: host array of `layers` device pointers that
+ * receive dLoss/dW_l.  on_device must be 1. */
+sn_status sn_backward(sn_ctx *ctx, const float *grad_counts, float *const *grad_w, int32_t on_device);
+
+/* Spikes of layer l (0 = input) of the last forward: [steps][batch][ceil(n_l/32)]
+ * words.  Membrane checkpoints of layer l >= 1: [steps/k][batch][n_l] floats,
+ * entry c = state after step (c+1)k - 1. */
+sn_status sn_ff_get_spikes(sn_ctx *ctx, int32_t layer, uint32_t *bits, int32_t on_device);
+sn_status sn_ff_get_checkpoints(sn_ctx *ctx, int32_t layer, float *v, int32_t on_device);
+
+/* ------------------------------------------------------------------------
  * Dense run without allocation.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory, for example
  * code running while a CUDA stream is being captured into a graph (where

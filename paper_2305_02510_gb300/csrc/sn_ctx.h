@@ -69,6 +69,18 @@ struct sn_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     cudaGraphNode_t graph_kernel = nullptr;
+    // feedforward network trained by BPTT
+    int ff_layers = 0, ff_batch = 0, ff_steps = 0, ff_k = 10, ff_splits = 1, ff_refr = 0;
+    float ff_theta = 1, ff_leak = 0, ff_reset = 0, ff_slope = 10;
+    std::vector<int> ff_sizes;
+    std::vector<uint8_t *> ff_D;       // device delays per layer
+    std::vector<void *> ff_DM;         // device delay bit masks per layer
+    std::vector<unsigned *> ff_S;      // device spike bits per layer (0 = input)
+    std::vector<float *> ff_vck;
+    std::vector<int *> ff_rck;
+    float *ff_I = nullptr, *ff_gI = nullptr, *ff_gS = nullptr, *ff_part = nullptr;
+    std::vector<const float *> ff_w;   // weights of the last forward (caller's device memory)
+    bool ff_have_forward = false;
     int failed = 0;                // sticky device failure seen
     std::string err;
     std::vector<void *> allocs;

@@ -1,0 +1,413 @@
+// Feedforward spiking network with per-synapse delays: exact forward
+// simulation and the surrogate-gradient adjoint (backpropagation through
+// time) with membrane checkpoints and recomputation.
+//
+// Layer l (1..L) maps n_in = n_{l-1} inputs to n_out = n_l LIF neurons with
+// weights W[i][j] (row-major, i = pre) and delays D[i][j] in 1..4.  Because
+// every delay is at least one step, the synaptic input of layer l at step t
+// depends only on layer l-1 at steps <= t-1, so each layer is computed for
+// all timesteps at once:
+//   I[t][b][j] = sum_i W[i][j] * s_{l-1}[t - D[i][j]][b][i]      (delay GEMM)
+// followed by the LIF recurrence of every (b, j) over t (Section 2.1 order:
+// leak toward reset, add input, strict threshold, refractory mask, reset).
+//
+// Adjoint (per (b, j), backwards in t; reset detached, refractory mask
+// constant, clamped-leak derivative [|V - reset| > leak]):
+//   gu(t)  = gV(t) (1 - s(t)) + gs(t) m(t) / (1 + slope |u(t) - theta|)^2
+//   gI(t)  = gu(t);   gV(t-1) = gu(t) L'(V(t-1))
+//   gs_{l-1}[t][b][i] = sum_j W[i][j] gI[t + D[i][j]][b][j]
+//   dW[i][j]          = sum_{t,b} gI[t][b][j] s_{l-1}[t - D[i][j]][b][i]
+// u(t) is recomputed from membrane checkpoints stored every k steps.
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sn_internal.h"
+
+namespace sn {
+
+constexpr int kFFDelays = 4;
+
+// ---------------------------------------------------------------------------
+// input spikes (bytes) -> bit rows [T*B][words]
+__global__ void ff_pack_kernel(const uint8_t *in, int rows, int n, int words, unsigned *out) {
+    const int lane = threadIdx.x & 31;
+    const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long total = (long long)rows * words;
+    for (long long w = gw; w < total; w += ((long long)gridDim.x * blockDim.x) >> 5) {
+        const long long r = w / words;
+        const int c = (int)(w - r * words);
+        const int i = c * 32 + lane;
+        const bool bit = i < n && in[r * n + i] != 0;
+        const unsigned word = __ballot_sync(0xffffffffu, bit);
+        if (lane == 0) out[w] = word;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Forward delay GEMM.  Block = 8 warps; a warp owns 32 output columns (one per
+// lane) and kRowsPerWarp rows; the block shares the columns, so the weight
+// chunk [32 inputs][32 columns] is staged once in shared memory.  dm holds,
+// per 32-input chunk c and column j, one bit mask per delay d:
+// bit (i - 32c) of dm[(c * n_out + j) * 4 + d - 1] is set iff D[i][j] == d.
+constexpr int kFwdWarps = 8;
+constexpr int kRowsPerWarp = 8;
+constexpr int kFwdRows = kFwdWarps * kRowsPerWarp;
+
+__global__ void __launch_bounds__(kFwdWarps * 32)
+ff_delay_fwd_kernel(const unsigned *__restrict__ sprev, int words_in, const float *__restrict__ W,
+                    const uint4 *__restrict__ dm, int n_in, int n_out, int B, int row0, int rows,
+                    float *__restrict__ I) {
+    __shared__ float ws[32][33];
+    __shared__ unsigned sw[kFwdRows][kFFDelays];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int col = blockIdx.x * 32 + lane;
+    const int rbase = row0 + blockIdx.y * kFwdRows;
+    float acc[kRowsPerWarp];
+#pragma unroll
+    for (int q = 0; q < kRowsPerWarp; ++q) acc[q] = 0.0f;
+    const int chunks = (n_in + 31) / 32;
+    for (int c = 0; c < chunks; ++c) {
+        __syncthreads();
+        // weights of the chunk: ws[ii][lane] = W[32c + ii][col]
+        for (int ii = warp; ii < 32; ii += kFwdWarps) {
+            const int i = c * 32 + ii;
+            ws[ii][lane] = (i < n_in && col < n_out) ? W[(size_t)i * n_out + col] : 0.0f;
+        }
+        // delayed spike words of the block's rows
+        for (int e = threadIdx.x; e < kFwdRows * kFFDelays; e += blockDim.x) {
+            const int rr = e / kFFDelays, d = e % kFFDelays + 1;
+            const int row = rbase + rr;
+            unsigned v = 0;
+            if (row < row0 + rows) {
+                const int t = row / B, b = row - (row / B) * B;
+                if (t - d >= 0) v = sprev[((size_t)(t - d) * B + b) * words_in + c];
+            }
+            sw[rr][d - 1] = v;
+        }
+        __syncthreads();
+        uint4 m = make_uint4(0, 0, 0, 0);
+        if (col < n_out) m = dm[(size_t)c * n_out + col];
+#pragma unroll
+        for (int q = 0; q < kRowsPerWarp; ++q) {
+            const int rr = warp * kRowsPerWarp + q;
+            const unsigned s1 = sw[rr][0], s2 = sw[rr][1], s3 = sw[rr][2], s4 = sw[rr][3];
+            const unsigned mine = (s1 & m.x) | (s2 & m.y) | (s3 & m.z) | (s4 & m.w);
+            unsigned any = s1 | s2 | s3 | s4;            // same for every lane
+            float a = acc[q];
+            while (any) {
+                const int ii = __ffs(any) - 1;
+                any &= any - 1u;
+                if ((mine >> ii) & 1u) a = __fadd_rn(a, ws[ii][lane]);
+            }
+            acc[q] = a;
+        }
+    }
+    if (col < n_out) {
+#pragma unroll
+        for (int q = 0; q < kRowsPerWarp; ++q) {
+            const int row = rbase + warp * kRowsPerWarp + q;
+            if (row < row0 + rows) I[(size_t)row * n_out + col] = acc[q];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// LIF recurrence of one layer over all steps.  Thread = (b, j); a warp covers
+// 32 consecutive j of one sample, so its ballot is a spike word.
+struct FFNeuron {
+    float theta, leak, reset, slope;
+    int refractory;
+};
+
+__device__ __forceinline__ float ff_leak(float v, float lk, float rs) {
+    if (v > rs) { const float u = __fsub_rn(v, lk); return u > rs ? u : rs; }
+    if (v < rs) { const float u = __fadd_rn(v, lk); return u < rs ? u : rs; }
+    return rs;
+}
+
+__global__ void ff_scan_fwd_kernel(const float *__restrict__ I, int n, int words, int B, int T, int k,
+                                   FFNeuron p, unsigned *__restrict__ S, float *__restrict__ vck,
+                                   int *__restrict__ rck, float *__restrict__ counts) {
+    const int lane = threadIdx.x & 31;
+    const int per_b = words * 32;
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (tid >= (long long)B * per_b) return;          // whole warps exit together
+    const int b = (int)(tid / per_b);
+    const int j = (int)(tid - (long long)b * per_b);
+    const bool live = j < n;
+    float v = p.reset;
+    int r = 0;
+    float cnt = 0.0f;
+    for (int t = 0; t < T; ++t) {
+        bool s = false;
+        if (live) {
+            const float u = __fadd_rn(ff_leak(v, p.leak, p.reset), I[((size_t)t * B + b) * n + j]);
+            s = (u > p.theta) && (r == 0);
+            if (s) { v = p.reset; r = p.refractory; }
+            else { v = u; if (r > 0) r -= 1; }
+            if (s) cnt += 1.0f;
+        }
+        const unsigned word = __ballot_sync(0xffffffffu, s);
+        if (lane == 0) S[((size_t)t * B + b) * words + (j >> 5)] = word;
+        if (live && (t % k) == k - 1) {
+            const size_t q = ((size_t)(t / k) * B + b) * n + j;
+            vck[q] = v;
+            rck[q] = r;
+        }
+    }
+    if (live && counts) counts[(size_t)b * n + j] = cnt;
+}
+
+// Adjoint of the recurrence for one layer: segments of k steps from the last
+// to the first; each is recomputed from its checkpoint (u kept in registers),
+// then walked backwards.  gs = gradient w.r.t. the layer's spikes: per step
+// ([T][B][n]) or, for the output layer, the count gradient gc [B][n] that
+// every step shares.
+template <int K>
+__global__ void ff_scan_bwd_kernel(const float *__restrict__ I, int n, int B, int T, FFNeuron p,
+                                   const float *__restrict__ vck, const int *__restrict__ rck,
+                                   const float *__restrict__ gs, const float *__restrict__ gc,
+                                   float *__restrict__ gI) {
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (tid >= (long long)B * n) return;
+    const int b = (int)(tid / n), j = (int)(tid - (long long)(tid / n) * n);
+    const int segs = (T + K - 1) / K;
+    const float gcount = gc ? gc[(size_t)b * n + j] : 0.0f;
+    float gv = 0.0f;
+    for (int sg = segs - 1; sg >= 0; --sg) {
+        const int t0 = sg * K;
+        float v = p.reset;
+        int r = 0;
+        if (sg > 0) {
+            const size_t q = ((size_t)(sg - 1) * B + b) * n + j;
+            v = vck[q];
+            r = rck[q];
+        }
+        float u[K], vprev[K];
+        bool sp[K], mk[K];
+#pragma unroll
+        for (int q = 0; q < K; ++q) {
+            const int t = t0 + q;
+            vprev[q] = v;
+            if (t < T) {
+                u[q] = __fadd_rn(ff_leak(v, p.leak, p.reset), I[((size_t)t * B + b) * n + j]);
+                mk[q] = (r == 0);
+                sp[q] = (u[q] > p.theta) && mk[q];
+                if (sp[q]) { v = p.reset; r = p.refractory; }
+                else { v = u[q]; if (r > 0) r -= 1; }
+            } else {
+                u[q] = 0.0f; mk[q] = false; sp[q] = false;
+            }
+        }
+#pragma unroll
+        for (int q = K - 1; q >= 0; --q) {
+            const int t = t0 + q;
+            if (t >= T) continue;
+            const float g_s = gc ? gcount : gs[((size_t)t * B + b) * n + j];
+            const float x = fabsf(u[q] - p.theta);
+            const float den = 1.0f + p.slope * x;
+            const float sur = mk[q] ? 1.0f / (den * den) : 0.0f;
+            const float gu = (sp[q] ? 0.0f : gv) + g_s * sur;
+            gI[((size_t)t * B + b) * n + j] = gu;
+            const float dv = vprev[q] - p.reset;
+            gv = (fabsf(dv) > p.leak) ? gu : 0.0f;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Gradient w.r.t. the previous layer's spikes:
+//   gsp[t][b][i] = sum_j W[i][j] * gI[t + D[i][j]][b][j]   (0 beyond T-1)
+// Block = 8 warps over 32 inputs (one per lane) x 64 rows (8 per warp); the
+// reduction over j runs in chunks of 32 staged in shared memory.
+constexpr int kBdRows = 64;
+
+__global__ void __launch_bounds__(256)
+ff_bwd_data_kernel(const float *__restrict__ gI, const float *__restrict__ W, const uint8_t *__restrict__ D,
+                   int n_in, int n_out, int B, int T, float *__restrict__ gsp) {
+    __shared__ float wt[32][33];            // wt[jj][ii] = W[i][j]
+    __shared__ uint8_t dt[32][33];          // dt[jj][ii] = D[i][j] - 1
+    __shared__ float gs[kBdRows][kFFDelays][33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + lane;
+    const int rbase = blockIdx.y * kBdRows;
+    const int rows = T * B;
+    float acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0.0f;
+    for (int j0 = 0; j0 < n_out; j0 += 32) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+            const int ii = e / 32, jj = e % 32;        // coalesced over j
+            const int ig = blockIdx.x * 32 + ii, jg = j0 + jj;
+            const bool ok = ig < n_in && jg < n_out;
+            wt[jj][ii] = ok ? W[(size_t)ig * n_out + jg] : 0.0f;
+            dt[jj][ii] = ok ? (uint8_t)(D[(size_t)ig * n_out + jg] - 1) : (uint8_t)0;
+        }
+        for (int e = threadIdx.x; e < kBdRows * kFFDelays * 32; e += blockDim.x) {
+            const int jj = e % 32, d = (e / 32) % kFFDelays + 1, rr = e / (32 * kFFDelays);
+            const int row = rbase + rr;
+            float g = 0.0f;
+            if (row < rows && j0 + jj < n_out) {
+                const int t = row / B, b = row - (row / B) * B;
+                if (t + d < T) g = gI[((size_t)(t + d) * B + b) * n_out + j0 + jj];
+            }
+            gs[rr][d - 1][jj] = g;
+        }
+        __syncthreads();
+        const int jn = min(32, n_out - j0);
+        for (int jj = 0; jj < jn; ++jj) {
+            const float w = wt[jj][lane];
+            const int d = dt[jj][lane];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) acc[q] = fmaf(w, gs[warp * 8 + q][d][jj], acc[q]);
+        }
+    }
+    if (i < n_in) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int row = rbase + warp * 8 + q;
+            if (row < rows) gsp[(size_t)row * n_in + i] = acc[q];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Weight gradient, split over the rows (t, b) for parallelism:
+//   part[sp][i][j] = sum_{rows of split sp} gI[row][j] * s_{l-1}[t - D[i][j]][b][i]
+// Block = 8 warps: the block owns 32 inputs (i) x 256 outputs (j, one per
+// thread); each thread keeps 32 accumulators, one per input.
+__global__ void __launch_bounds__(256)
+ff_dw_kernel(const float *__restrict__ gI, const unsigned *__restrict__ sprev, int words_in,
+             const uint8_t *__restrict__ D, int n_in, int n_out, int B, int T, int splits,
+             float *__restrict__ part) {
+    const int j = blockIdx.x * 256 + threadIdx.x;
+    const int c = blockIdx.y;                       // 32-input chunk
+    const int sp = blockIdx.z;
+    const int rows = T * B;
+    const int r0 = (int)((long long)sp * rows / splits), r1 = (int)((long long)(sp + 1) * rows / splits);
+    __shared__ unsigned sw[64][kFFDelays];
+    int dsh[32];                                    // per input: delay - 1 (or -1 if absent)
+#pragma unroll
+    for (int ii = 0; ii < 32; ++ii) {
+        const int i = c * 32 + ii;
+        dsh[ii] = (i < n_in && j < n_out) ? (int)D[(size_t)i * n_out + j] - 1 : -1;
+    }
+    float acc[32];
+#pragma unroll
+    for (int ii = 0; ii < 32; ++ii) acc[ii] = 0.0f;
+    for (int rb = r0; rb < r1; rb += 64) {
+        __syncthreads();
+        {
+            const int e = threadIdx.x;              // 64 rows x 4 delays = 256 entries
+            const int rr = e / kFFDelays, d = e % kFFDelays + 1;
+            const int row = rb + rr;
+            unsigned v = 0;
+            if (row < r1) {
+                const int t = row / B, b = row - (row / B) * B;
+                if (t - d >= 0) v = sprev[((size_t)(t - d) * B + b) * words_in + c];
+            }
+            sw[rr][d - 1] = v;
+        }
+        __syncthreads();
+        const int rn = min(64, r1 - rb);
+        for (int rr = 0; rr < rn; ++rr) {
+            const unsigned s1 = sw[rr][0], s2 = sw[rr][1], s3 = sw[rr][2], s4 = sw[rr][3];
+            if ((s1 | s2 | s3 | s4) == 0u) continue;        // uniform over the block
+            const float g = j < n_out ? gI[(size_t)(rb + rr) * n_out + j] : 0.0f;
+#pragma unroll
+            for (int ii = 0; ii < 32; ++ii) {
+                const int d = dsh[ii];
+                const unsigned w = d == 0 ? s1 : d == 1 ? s2 : d == 2 ? s3 : s4;
+                if (d >= 0 && ((w >> ii) & 1u)) acc[ii] = __fadd_rn(acc[ii], g);
+            }
+        }
+    }
+    if (j < n_out) {
+#pragma unroll
+        for (int ii = 0; ii < 32; ++ii) {
+            const int i = c * 32 + ii;
+            if (i < n_in) part[((size_t)sp * n_in + i) * n_out + j] = acc[ii];
+        }
+    }
+}
+
+__global__ void ff_dw_reduce_kernel(const float *__restrict__ part, int splits, long long count,
+                                    float *__restrict__ dW) {
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < count;
+         q += (long long)gridDim.x * blockDim.x) {
+        float s = 0.0f;
+        for (int sp = 0; sp < splits; ++sp) s = __fadd_rn(s, part[(size_t)sp * count + q]);
+        dW[q] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+
+static int blocks_for(long long work, int per) {
+    long long b = (work + per - 1) / per;
+    if (b > 65535LL * 16) b = 65535LL * 16;
+    return (int)(b < 1 ? 1 : b);
+}
+
+cudaError_t ff_pack(const uint8_t *in, int rows, int n, int words, unsigned *out, cudaStream_t s) {
+    const long long warps = (long long)rows * words;
+    ff_pack_kernel<<<blocks_for(warps * 32, 256), 256, 0, s>>>(in, rows, n, words, out);
+    return cudaGetLastError();
+}
+
+cudaError_t ff_delay_fwd(const unsigned *sprev, int words_in, const float *W, const void *dm, int n_in,
+                         int n_out, int B, int row0, int rows, float *I, cudaStream_t s) {
+    dim3 grid((n_out + 31) / 32, (rows + kFwdRows - 1) / kFwdRows);
+    ff_delay_fwd_kernel<<<grid, kFwdWarps * 32, 0, s>>>(sprev, words_in, W, (const uint4 *)dm, n_in, n_out, B,
+                                                       row0, rows, I);
+    return cudaGetLastError();
+}
+
+cudaError_t ff_scan_fwd(const float *I, int n, int B, int T, int k, float theta, float leak, float reset,
+                        int refractory, unsigned *S, float *vck, int *rck, float *counts, cudaStream_t s) {
+    FFNeuron p{theta, leak, reset, 0.0f, refractory};
+    const int words = (n + 31) / 32;
+    const long long threads = (long long)B * words * 32;
+    ff_scan_fwd_kernel<<<blocks_for(threads, 256), 256, 0, s>>>(I, n, words, B, T, k, p, S, vck, rck, counts);
+    return cudaGetLastError();
+}
+
+cudaError_t ff_scan_bwd(const float *I, int n, int B, int T, int k, float theta, float leak, float reset,
+                        int refractory, float slope, const float *vck, const int *rck, const float *gs,
+                        const float *gc, float *gI, cudaStream_t s) {
+    FFNeuron p{theta, leak, reset, slope, refractory};
+    const long long threads = (long long)B * n;
+    const int nb = blocks_for(threads, 128);
+    switch (k) {
+        case 1: ff_scan_bwd_kernel<1><<<nb, 128, 0, s>>>(I, n, B, T, p, vck, rck, gs, gc, gI); break;
+        case 2: ff_scan_bwd_kernel<2><<<nb, 128, 0, s>>>(I, n, B, T, p, vck, rck, gs, gc, gI); break;
+        case 5: ff_scan_bwd_kernel<5><<<nb, 128, 0, s>>>(I, n, B, T, p, vck, rck, gs, gc, gI); break;
+        case 10: ff_scan_bwd_kernel<10><<<nb, 128, 0, s>>>(I, n, B, T, p, vck, rck, gs, gc, gI); break;
+        case 20: ff_scan_bwd_kernel<20><<<nb, 128, 0, s>>>(I, n, B, T, p, vck, rck, gs, gc, gI); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t ff_bwd_data(const float *gI, const float *W, const uint8_t *D, int n_in, int n_out, int B, int T,
+                        float *gsp, cudaStream_t s) {
+    dim3 grid((n_in + 31) / 32, (T * B + kBdRows - 1) / kBdRows);
+    ff_bwd_data_kernel<<<grid, 256, 0, s>>>(gI, W, D, n_in, n_out, B, T, gsp);
+    return cudaGetLastError();
+}
+
+cudaError_t ff_dw(const float *gI, const unsigned *sprev, int words_in, const uint8_t *D, int n_in, int n_out,
+                  int B, int T, int splits, float *part, float *dW, cudaStream_t s) {
+    dim3 grid((n_out + 255) / 256, (n_in + 31) / 32, splits);
+    ff_dw_kernel<<<grid, 256, 0, s>>>(gI, sprev, words_in, D, n_in, n_out, B, T, splits, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long long count = (long long)n_in * n_out;
+    ff_dw_reduce_kernel<<<blocks_for(count, 256), 256, 0, s>>>(part, splits, count, dW);
+    return cudaGetLastError();
+}
+
+}  // namespace sn

@@ -12,7 +12,7 @@
 
 namespace sn {
 
-enum Kind { KIND_SPARSE = 0, KIND_DENSE = 1, KIND_BATCH = 2, KIND_SHARED_I8 = 3 };
+enum Kind { KIND_SPARSE = 0, KIND_DENSE = 1, KIND_BATCH = 2, KIND_SHARED_I8 = 3, KIND_FF = 4 };
 
 // Grid barrier state (one per context): arrival count and generation.
 struct GridBarrier {
@@ -115,6 +115,20 @@ cudaError_t launch_batch(const BatchArgs &a, int dtype, int grid, cudaStream_t s
 cudaError_t batch_kernel_node(int dtype, void **fn);
 cudaError_t max_grid_batch(int dtype, int ring_smem, int *grid);
 size_t batch_smem(int ring_smem);
+
+// Feedforward (BPTT) kernels, sn_ff.cu
+cudaError_t ff_pack(const uint8_t *in, int rows, int n, int words, unsigned *out, cudaStream_t s);
+cudaError_t ff_delay_fwd(const unsigned *sprev, int words_in, const float *W, const void *dm, int n_in,
+                         int n_out, int B, int row0, int rows, float *I, cudaStream_t s);
+cudaError_t ff_scan_fwd(const float *I, int n, int B, int T, int k, float theta, float leak, float reset,
+                        int refractory, unsigned *S, float *vck, int *rck, float *counts, cudaStream_t s);
+cudaError_t ff_scan_bwd(const float *I, int n, int B, int T, int k, float theta, float leak, float reset,
+                        int refractory, float slope, const float *vck, const int *rck, const float *gs,
+                        const float *gc, float *gI, cudaStream_t s);
+cudaError_t ff_bwd_data(const float *gI, const float *W, const uint8_t *D, int n_in, int n_out, int B, int T,
+                        float *gsp, cudaStream_t s);
+cudaError_t ff_dw(const float *gI, const unsigned *sprev, int words_in, const uint8_t *D, int n_in, int n_out,
+                  int B, int T, int splits, float *part, float *dW, cudaStream_t s);
 
 // Launchers (kernels live in sn_kernels.cu).  Return a CUDA error code.
 cudaError_t launch_sparse(const NetArgs &a, int dtype, int grid, int block, cudaStream_t s);

@@ -54,6 +54,11 @@ class sn_dense_noalloc_args(C.Structure):
                 ("raster", C.c_void_p), ("cuda_stream", C.c_void_p)]
 
 
+class sn_ff_params(C.Structure):
+    _fields_ = [("threshold", C.c_float), ("leak", C.c_float), ("reset", C.c_float),
+                ("refractory", C.c_int32), ("surrogate_slope", C.c_float), ("checkpoint_every", C.c_int32)]
+
+
 _lib = None
 _lock = threading.Lock()
 _P = C.c_void_p
@@ -77,6 +82,12 @@ def lib():
                                     C.POINTER(sn_synapses), C.POINTER(_P)],
                 "sn_batch_config": [_P, C.c_int32, C.c_int32],
                 "sn_autotune": [_P, C.c_int32, C.POINTER(C.c_float)],
+                "sn_create_ff": [C.POINTER(sn_config), C.c_int32, _P, _P, C.POINTER(sn_ff_params), C.c_int32,
+                                 C.c_int32, C.POINTER(_P)],
+                "sn_ff_forward": [_P, _P, _P, _P],
+                "sn_backward": [_P, _P, _P, C.c_int32],
+                "sn_ff_get_spikes": [_P, C.c_int32, _P, C.c_int32],
+                "sn_ff_get_checkpoints": [_P, C.c_int32, _P, C.c_int32],
                 "sn_set_input": [_P, C.c_int64, _P, _P, _P],
                 "sn_set_poisson": [_P, C.c_int32, _P, _P, _P, C.c_uint64],
                 "sn_set_poisson_stream": [_P, C.c_int32, _P, _P, _P, C.c_uint64, C.c_uint64],
@@ -354,6 +365,50 @@ def sn_run_dense_noalloc(n, delay, steps, w, threshold, leak, reset, refractory,
     st = lib().sn_run_dense_noalloc(C.byref(a))
     if st != SN_OK:
         raise SnError(st, "sn_run_dense_noalloc failed")
+
+
+def sn_create_ff(sizes, delays, *, threshold, leak, reset, refractory, slope, checkpoint_every,
+                 batch, steps, stream=None) -> Ctx:
+    """Feedforward context; delays: list of uint8 arrays [n_in, n_out] (host)."""
+    sz = np.ascontiguousarray(sizes, np.int32)
+    ds = [np.ascontiguousarray(d, np.uint8) for d in delays]
+    ptrs = (C.c_void_p * len(ds))(*[_ptr(d) for d in ds])
+    p = sn_ff_params(float(threshold), float(leak), float(reset), int(refractory), float(slope),
+                     int(checkpoint_every))
+    cfg = _config(SN_F32, 1, 0, 0, stream)
+    h = _P()
+    _check(lib().sn_create_ff(C.byref(cfg), len(ds), _ptr(sz), ptrs, C.byref(p), int(batch), int(steps),
+                              C.byref(h)))
+    ctx = Ctx(h, int(sz[-1]), SN_F32, 0, "ff", 0)
+    ctx.sizes, ctx.batch, ctx.steps, ctx.k = [int(x) for x in sz], int(batch), int(steps), int(checkpoint_every)
+    return ctx
+
+
+def sn_ff_forward(ctx: Ctx, input_spikes, weights, counts):
+    """input_spikes: CUDA uint8 [steps, batch, n0]; weights: CUDA float32
+    tensors [n_in, n_out]; counts: CUDA float32 [batch, n_out] (written)."""
+    ptrs = (C.c_void_p * len(weights))(*[_ptr(w) for w in weights])
+    _check(lib().sn_ff_forward(ctx.handle, _ptr(input_spikes), ptrs, _ptr(counts)), ctx)
+
+
+def sn_backward(ctx: Ctx, grad_counts, grad_weights):
+    ptrs = (C.c_void_p * len(grad_weights))(*[_ptr(g) for g in grad_weights])
+    _check(lib().sn_backward(ctx.handle, _ptr(grad_counts), ptrs, 1), ctx)
+
+
+def sn_ff_get_spikes(ctx: Ctx, layer: int):
+    n = ctx.sizes[layer]
+    out = np.zeros((ctx.steps, ctx.batch, (n + 31) // 32), np.uint32)
+    _check(lib().sn_ff_get_spikes(ctx.handle, int(layer), _ptr(out), 0), ctx)
+    b = out.reshape(ctx.steps * ctx.batch, -1)
+    return unpack_raster(b, n).reshape(ctx.steps, ctx.batch, n)
+
+
+def sn_ff_get_checkpoints(ctx: Ctx, layer: int):
+    n = ctx.sizes[layer]
+    out = np.zeros((ctx.steps // ctx.k, ctx.batch, n), np.float32)
+    _check(lib().sn_ff_get_checkpoints(ctx.handle, int(layer), _ptr(out), 0), ctx)
+    return out
 
 
 def sn_version() -> str:

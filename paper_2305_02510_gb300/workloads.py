@@ -329,3 +329,29 @@ def to_dense(wl):
     w = np.zeros((n, n))
     np.add.at(w, (wl["pre"], wl["post"]), wl["weight"])
     return w
+
+
+def bptt_task(batch: int = 128, sizes=(700, 1024, 1024, 20), steps: int = 100,
+              max_delay: int = 4, seed: int = SEED_BASE + 7, classes: int | None = None):
+    """Feedforward spiking network trained by backpropagation through time:
+    LIF layers sizes[1..] fed by sizes[0] input channels; weights
+    Kaiming-normal N(0, 2/fan_in) (float32), per-synapse delays U{1..max_delay};
+    threshold 1, leak 0.05, reset 0, refractory 0; fast-sigmoid surrogate with
+    slope 10; membrane checkpoints every 10 steps.  Inputs are Poisson spike
+    trains with a rate U(0, 0.2) per (sample, channel); labels uniform over the
+    output classes.  Returns a dict with input [steps, batch, n0] uint8,
+    labels [batch] int64, w (list of float32 [n_in, n_out]) and delay (list of
+    uint8 [n_in, n_out])."""
+    rng = _rng(seed)
+    sizes = tuple(int(x) for x in sizes)
+    rates = rng.uniform(0.0, 0.2, size=(batch, sizes[0]))
+    x = (rng.random((steps, batch, sizes[0])) < rates[None]).astype(np.uint8)
+    ncls = classes if classes is not None else sizes[-1]
+    labels = rng.integers(0, ncls, size=batch).astype(np.int64)
+    ws, ds = [], []
+    for a, b in zip(sizes[:-1], sizes[1:]):
+        ws.append((rng.standard_normal((a, b)) * math.sqrt(2.0 / a)).astype(np.float32))
+        ds.append(rng.integers(1, max_delay + 1, size=(a, b)).astype(np.uint8))
+    return dict(sizes=sizes, batch=int(batch), steps=int(steps), max_delay=int(max_delay),
+                input=x, labels=labels, w=ws, delay=ds, threshold=1.0, leak=0.05, reset=0.0,
+                refractory=0, slope=10.0, checkpoint_every=10, name="bptt")
