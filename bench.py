@@ -195,6 +195,7 @@ def extras(S, W, torch, stream, flush):
     plain_ms = a.elapsed_time(b2)
     plain_ev = sum(S.sn_get_counters(c)[2] for c in plain)
     del plain
+    res["bptt"] = bptt_extra(S, W, torch, stream)
     res["batched"] = {
         "workload": "4096 networks, N log-uniform [64, 4096], p U(0.01, 0.2), delays 1..8",
         "networks": len(nets), "neurons": int(sum(w["n"] for w in nets)),
@@ -203,6 +204,103 @@ def extras(S, W, torch, stream, flush):
         "plain_ms": plain_ms, "plain_synaptic_events_per_s": plain_ev / (plain_ms / 1e3),
         "speedup_vs_plain": plain_ms / ms, "launches": 1, "plain_launches": len(nets)}
     return res
+
+
+class _Spike:
+    """Surrogate spike for the plain-torch comparison path of the BPTT
+    measurement (fast sigmoid, slope 10)."""
+
+    @staticmethod
+    def make(torch):
+        class F(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, x, slope):
+                ctx.save_for_backward(x)
+                ctx.slope = slope
+                return (x > 0).to(x.dtype)
+
+            @staticmethod
+            def backward(ctx, g):
+                (x,) = ctx.saved_tensors
+                return g / (1.0 + ctx.slope * x.abs()) ** 2, None
+        return F
+
+
+def plain_torch_bptt_step(torch, task, x, ws, masks, labels, spike):
+    """The same training step written as plain torch on the GPU: unrolled over
+    the steps, one masked matmul per delay and layer, autograd backward."""
+    T, B = task["steps"], task["batch"]
+    th, lk, rs = task["threshold"], task["leak"], task["reset"]
+    sizes = task["sizes"]
+    V = [torch.full((B, n), rs, device=x.device) for n in sizes[1:]]
+    hist = [[x[t].float() for t in range(T)]] + [[None] * T for _ in sizes[1:]]
+    counts = torch.zeros((B, sizes[-1]), device=x.device)
+    wd = [[w * m for m in ms] for w, ms in zip(ws, masks)]
+    for t in range(T):
+        for l in range(len(ws)):
+            I = torch.zeros((B, sizes[l + 1]), device=x.device)
+            for d in range(1, len(masks[l]) + 1):
+                if t - d >= 0:
+                    I = I + hist[l][t - d] @ wd[l][d - 1]
+            dv = V[l] - rs
+            far = dv.abs().detach() > lk
+            u = torch.where(far, V[l] - lk * torch.sign(dv.detach()), torch.full_like(V[l], rs)) + I
+            sp = spike.apply(u - th, task["slope"])
+            V[l] = u * (1 - sp.detach()) + rs * sp.detach()
+            hist[l + 1][t] = sp
+        counts = counts + hist[-1][t]
+    loss = torch.nn.functional.cross_entropy(counts, labels)
+    loss.backward()
+    return loss
+
+
+def bptt_extra(S, W, torch, stream):
+    """Training step (forward + backward) of the 700-1024-1024-20 network,
+    batch 128, 100 steps, through SNNFunction, against the same step in plain
+    torch on the same GPU."""
+    from paper_2305_02510_gb300 import bptt
+    task = W.bptt_task()
+    dev = torch.device("cuda")
+    net = bptt.FFNet.from_task(task)
+    x = torch.tensor(task["input"], device=dev)
+    labels = torch.tensor(task["labels"], device=dev)
+    ws = [torch.tensor(w, device=dev, requires_grad=True) for w in task["w"]]
+
+    def ours():
+        for w in ws:
+            w.grad = None
+        counts = bptt.SNNFunction.apply(net, x, *ws)
+        torch.nn.functional.cross_entropy(counts, labels).backward()
+
+    def timed(fn, warm, reps):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    ms = timed(ours, 3, 10)
+    masks = [[torch.tensor(task["delay"][l] == d, device=dev, dtype=torch.float32) for d in range(1, 5)]
+             for l in range(len(ws))]
+    spike = _Spike.make(torch)
+    wp = [torch.tensor(w, device=dev, requires_grad=True) for w in task["w"]]
+
+    def plain():
+        for w in wp:
+            w.grad = None
+        plain_torch_bptt_step(torch, task, x, wp, masks, labels, spike)
+
+    plain_ms = timed(plain, 1, 3)
+    sizes = task["sizes"]
+    syn = sum(a * b for a, b in zip(sizes[:-1], sizes[1:]))
+    return {"workload": "700-1024-1024-20 LIF, per-synapse delays 1..4, batch 128, 100 steps, "
+                        "checkpoint every 10", "synapses": syn, "ms_per_training_step": ms,
+            "plain_torch_ms_per_training_step": plain_ms, "speedup_vs_plain_torch": plain_ms / ms}
 
 
 def run_reference(args, wl, rank):
