@@ -144,6 +144,21 @@ sn_status sn_create_dense(const sn_config *cfg, const sn_neurons *neurons,
 sn_status sn_create_batch(const sn_config *cfg, int32_t nets, const sn_neurons *neurons,
                           const sn_synapses *synapses, sn_ctx **out);
 
+/* Create one shared dense integer network driven by `trains` independent
+ * input trains: every train has its own state, spikes and Poisson stream
+ * (net = train index), and all share the weights w (row-major n x n int8,
+ * w[i*n + j] = weight of i -> j, values -8..8; the diagonal acts like any
+ * entry) and the neuron parameters (integers).  cfg->dtype must be SN_I32,
+ * cfg->max_delay 1; n and trains multiples of 128.  Each step's synaptic
+ * input of all trains is one tensor-core GEMM of the previous spikes with w
+ * (Section 2.1: previous spike vector times the weight matrix), exact in
+ * integers.  State (sn_get_state) is [trains][n]; every raster row holds
+ * each train's n/32 words in train order; sn_set_poisson takes neuron
+ * indices 0..n-1 and drives that neuron in every train.  Explicit events,
+ * STDP and checkpoints are not available. */
+sn_status sn_create_shared_dense_i8(const sn_config *cfg, const sn_neurons *neurons, const int8_t *w,
+                                    int32_t trains, sn_ctx **out);
+
 /* Executor mapping of a batched context: networks with at most warp_max_n
  * neurons (0..512) run on a single warp, larger ones on a whole block; a
  * network's pending-input ring is held in shared memory while it runs when

@@ -320,10 +320,11 @@ sn_status sn_set_input(sn_ctx *c, int64_t nev, const int32_t *step, const int32_
 sn_status sn_set_poisson(sn_ctx *c, int32_t nsrc, const int32_t *neuron, const float *rate,
                          const float *amp, uint64_t seed) {
     if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
-    if (c->kind != KIND_SPARSE && c->kind != KIND_DENSE && c->kind != KIND_BATCH)
+    if (c->kind != KIND_SPARSE && c->kind != KIND_DENSE && c->kind != KIND_BATCH && c->kind != KIND_SHARED_I8)
         return fail(c, SN_ESTATE, "wrong context kind");
     if (nsrc < 0 || (nsrc > 0 && (!neuron || !rate || !amp))) return fail(c, SN_EINVAL, "bad source arrays");
     if (c->kind == KIND_BATCH) return batch_set_poisson(c, nsrc, neuron, rate, amp, seed);
+    if (c->kind == KIND_SHARED_I8) return shared_set_poisson(c, nsrc, neuron, rate, amp, seed);
     const int n = c->n;
     std::vector<unsigned> thr(n, 0u);
     std::vector<float> af(n, 0.0f);
@@ -421,8 +422,8 @@ sn_status sn_run(sn_ctx *c, int32_t steps) {
     if (steps < 0) return fail(c, SN_EINVAL, "steps < 0");
     if (steps == 0) return SN_OK;
     if (c->step + steps >= (1ll << 31)) return fail(c, SN_EINVAL, "step counter would exceed 2^31");
-    if (c->kind == KIND_BATCH) {
-        sn_status st = batch_run(c, steps);
+    if (c->kind == KIND_BATCH || c->kind == KIND_SHARED_I8) {
+        sn_status st = c->kind == KIND_BATCH ? batch_run(c, steps) : shared_run(c, steps);
         if (st) return st;
         c->step += steps;
         if (c->step - c->raster_from > c->cap) c->raster_from = c->step - c->cap;
@@ -453,6 +454,19 @@ sn_status sn_run(sn_ctx *c, int32_t steps) {
 
 sn_status sn_reset(sn_ctx *c) {
     if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
+    if (c->kind == KIND_SHARED_I8) {
+        const size_t bn = (size_t)c->sh_B * c->n;
+        SN_CUDA(c, cudaMemcpyAsync(c->V, c->sh_V0, bn * 4, cudaMemcpyDeviceToDevice, c->stream));
+        SN_CUDA(c, cudaMemsetAsync(c->r, 0, bn * 4, c->stream));
+        SN_CUDA(c, cudaMemsetAsync(c->sh_A0, 0, bn, c->stream));
+        SN_CUDA(c, cudaMemsetAsync(c->sh_A1, 0, bn, c->stream));
+        SN_CUDA(c, cudaMemsetAsync(c->raster, 0, (size_t)c->cap * c->words * 4, c->stream));
+        SN_CUDA(c, cudaMemsetAsync(c->ctl, 0, sizeof(Control), c->stream));
+        c->step = 0;
+        c->raster_from = 0;
+        c->failed = 0;
+        return SN_OK;
+    }
     if (c->kind != KIND_SPARSE && c->kind != KIND_DENSE && c->kind != KIND_BATCH)
         return fail(c, SN_ESTATE, "wrong context kind");
     const size_t vb = (size_t)c->n * 4;
@@ -512,8 +526,10 @@ sn_status sn_get_spikes(sn_ctx *c, int64_t t0, int64_t t1, uint32_t *bits, int32
 sn_status sn_get_state(sn_ctx *c, void *v, int32_t *refr, int32_t on_device) {
     if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
     sn_status s;
-    if (v && (s = copy_out(c, v, c->V, (size_t)c->n * 4, on_device))) return s;
-    if (refr && (s = copy_out(c, refr, c->r, (size_t)c->n * 4, on_device))) return s;
+    if (c->kind == KIND_FF) return fail(c, SN_ESTATE, "feedforward contexts: use sn_ff_get_checkpoints");
+    const size_t bytes = (size_t)state_elems(c) * 4;
+    if (v && (s = copy_out(c, v, c->V, bytes, on_device))) return s;
+    if (refr && (s = copy_out(c, refr, c->r, bytes, on_device))) return s;
     return SN_OK;
 }
 

@@ -81,6 +81,11 @@ struct sn_ctx {
     float *ff_I = nullptr, *ff_gI = nullptr, *ff_gS = nullptr, *ff_part = nullptr;
     std::vector<const float *> ff_w;   // weights of the last forward (caller's device memory)
     bool ff_have_forward = false;
+    // shared dense network driven by many trains (tensor cores)
+    int sh_B = 0, sh_grid = 0;
+    unsigned char *sh_A0 = nullptr, *sh_A1 = nullptr, *sh_WT = nullptr;
+    int *sh_V0 = nullptr;
+    alignas(64) unsigned char sh_tmaps[3 * 128];
     int failed = 0;                // sticky device failure seen
     std::string err;
     std::vector<void *> allocs;
@@ -147,6 +152,10 @@ sn_status upload_neurons(sn_ctx *c, const sn_neurons *nr);
 sn_status alloc_common(sn_ctx *c, const sn_config *cfg);
 void destroy_all(sn_ctx *c);
 sn_status batch_run(sn_ctx *c, int steps);
+sn_status shared_run(sn_ctx *c, int steps);
+sn_status shared_set_poisson(sn_ctx *c, int32_t nsrc, const int32_t *neuron, const float *rate,
+                             const float *amp, uint64_t seed);
+inline long long state_elems(const sn_ctx *c) { return c->kind == KIND_SHARED_I8 ? (long long)c->sh_B * c->n : c->n; }
 sn_status batch_set_poisson(sn_ctx *c, int32_t nsrc, const int32_t *neuron, const float *rate,
                             const float *amp, uint64_t seed);
 

@@ -116,6 +116,22 @@ cudaError_t batch_kernel_node(int dtype, void **fn);
 cudaError_t max_grid_batch(int dtype, int ring_smem, int *grid);
 size_t batch_smem(int ring_smem);
 
+// Shared dense network on tensor cores, sn_shared.cu
+struct SharedHostArgs {
+    int n, B, t0, steps, cap;
+    unsigned char *A0, *A1;
+    int *V, *r;
+    const int *th, *lk, *rs, *R;
+    const unsigned *prate;
+    const int *pamp;
+    const unsigned long long *pkey;
+    unsigned *raster;
+    Control *ctl;
+};
+cudaError_t launch_shared(const void *tmaps, const SharedHostArgs &h, int grid, cudaStream_t s);
+cudaError_t max_grid_shared(int *grid);
+size_t shared_smem_bytes();
+
 // Feedforward (BPTT) kernels, sn_ff.cu
 cudaError_t ff_pack(const uint8_t *in, int rows, int n, int words, unsigned *out, cudaStream_t s);
 cudaError_t ff_delay_fwd(const unsigned *sprev, int words_in, const float *W, const void *dm, int n_in,

@@ -1,0 +1,326 @@
+// One shared dense integer network driven by B independent input trains,
+// propagated on the 5th-generation tensor cores (tcgen05).
+//
+// Per timestep t the synaptic input of all trains is one GEMM
+//   Acc[B][n] = S(t-1)[B][n] . W[n][n]
+// with S the 0/1 spikes of the previous step (Section 2.1: "the vector of
+// spikes from the previous time step is multiplied by the weight matrix").
+// Spikes and integer weights in [-8, 8] are exact in FP8 E4M3, and every sum
+// (at most n * 8 in magnitude, n <= 2^21) is an integer below 2^24, exact in
+// the FP32 accumulator: the GEMM runs as tcgen05.mma kind::f8f6f4 and is
+// bit-exact integer arithmetic.  (kind::i8 does not exist on sm_103a.)
+//
+// Tile = 128 trains x 128 post-neurons, accumulated in TMEM over the K = n
+// pre-neurons in 128-byte stages loaded by TMA (128B swizzle, 4 stages).
+// Warp 0 lane 0 issues TMA, warp 1 lane 0 issues the MMAs; afterwards the four
+// warps read the accumulator rows (tcgen05.ld) and apply the integer LIF rule
+// (Section 2.1 order), write the spike bytes that are the next step's A
+// operand, the raster bits and the state.  A persistent cooperative launch
+// runs all steps; a grid barrier separates them.  Every wait is bounded: on
+// expiry the kernel latches SN_ETIMEOUT, drains its own copies and MMAs,
+// frees its TMEM and returns.
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sn_device.cuh"
+#include "sn_internal.h"
+
+namespace sn {
+
+constexpr int kTM = 128;                       // trains per tile (MMA M)
+constexpr int kTN = 128;                       // post-neurons per tile (MMA N)
+constexpr int kTK = 128;                       // bytes of K per stage (one 128B swizzle row)
+constexpr int kStages = 4;
+constexpr int kStageA = kTM * kTK;             // 16 KiB
+constexpr int kStageBytes = (kTM + kTN) * kTK; // 32 KiB
+constexpr int kShThreads = 128;
+constexpr unsigned kTmemCols = 128;
+constexpr unsigned long long kWaitNs = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for the phase of `parity`; false (status latched) on expiry or
+// when another block has latched a status.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, Control *ctl) {
+    unsigned long long t0 = 0;
+    for (unsigned it = 0;; ++it) {
+        if (mbar_try(bar, parity)) return true;
+        if ((it & 255u) == 255u) {
+            const unsigned long long now = global_timer_ns();
+            if (t0 == 0) t0 = now;
+            else if (now - t0 > kWaitNs) { atomicCAS(&ctl->status, 0, (int)SN_ETIMEOUT); return false; }
+            if (ld_status(ctl) != 0) return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n"
+        :: "r"(dst), "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar) : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile with 128-byte swizzle:
+// 8-row atoms of 128 B stacked every 1024 B (stride byte offset), start
+// address in 16-byte units, descriptor version 1, layout SWIZZLE_128B (2).
+__device__ __forceinline__ uint64_t umma_desc_sw128(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)(16u >> 4) << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+// Instruction descriptor of kind::f8f6f4: FP32 accumulator, A and B E4M3,
+// both K-major, N = 128, M = 128.
+__host__ __device__ constexpr uint32_t idesc_e4m3_f32(int m, int n) {
+    return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f8(uint32_t tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int acc) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n"
+        :: "r"(tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n"
+                 :: "r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+          "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+          "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+          "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+}
+
+struct SharedArgs {
+    int n, B, t0, steps, cap, words;
+    int tiles_m, tiles;
+    unsigned char *A0, *A1;        // spike operands [B][n] bytes, A_(t & 1) holds step t
+    int *V, *r;                    // [B][n]
+    const int *th, *lk, *rs, *R;   // [n]
+    const unsigned *prate;         // [n]
+    const int *pamp;               // [n]
+    const unsigned long long *pkey;// [B]
+    unsigned *raster;              // [cap][B][words]
+    Control *ctl;
+};
+
+__global__ void __launch_bounds__(kShThreads, 1)
+shared_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
+              const __grid_constant__ CUtensorMap tmW, SharedArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full[kStages], empty[kStages], accbar;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t sbase = smem_addr(smem);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(smem_addr(&full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(smem_addr(&empty[s])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(smem_addr(&accbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        s_abort = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
+                     :: "r"(smem_addr(&s_tmem)), "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    const int kblocks = a.n / kTK;
+    constexpr uint32_t idesc = idesc_e4m3_f32(kTM, kTN);
+    unsigned g_prod = 0, g_mma = 0, tiles_done = 0;
+    unsigned long long my_spikes = 0;
+    bool overflow = false;
+
+    for (int s = 0; s < a.steps && !s_abort; ++s) {
+        const int t = a.t0 + s;
+        const CUtensorMap *tmA = ((t + 1) & 1) ? &tmA1 : &tmA0;   // holds step t-1
+        unsigned char *Aout = (t & 1) ? a.A1 : a.A0;
+        for (int tile = blockIdx.x; tile < a.tiles; tile += gridDim.x) {
+            const int m0 = (tile % a.tiles_m) * kTM, n0 = (tile / a.tiles_m) * kTN;
+            if (warp == 0 && lane == 0) {
+                // TMA producer
+                for (int kb = 0; kb < kblocks; ++kb, ++g_prod) {
+                    const int st = g_prod % kStages;
+                    const unsigned round = g_prod / kStages;
+                    if (round > 0 && !mbar_wait(smem_addr(&empty[st]), (round - 1) & 1u, a.ctl)) {
+                        s_abort = 1;
+                        break;
+                    }
+                    const uint32_t fb = smem_addr(&full[st]);
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
+                                 :: "r"(fb), "r"(kStageBytes) : "memory");
+                    const uint32_t dA = sbase + st * kStageBytes;
+                    tma_load_2d(dA, tmA, kb * kTK, m0, fb);
+                    tma_load_2d(dA + kStageA, &tmW, kb * kTK, n0, fb);
+                }
+            } else if (warp == 1 && lane == 0) {
+                // MMA issuer
+                for (int kb = 0; kb < kblocks; ++kb, ++g_mma) {
+                    const int st = g_mma % kStages;
+                    const unsigned round = g_mma / kStages;
+                    if (!mbar_wait(smem_addr(&full[st]), round & 1u, a.ctl)) { s_abort = 1; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    const uint32_t dA = sbase + st * kStageBytes;
+#pragma unroll
+                    for (int kk = 0; kk < kTK / 32; ++kk)
+                        mma_f8(tmem, umma_desc_sw128(dA + kk * 32), umma_desc_sw128(dA + kStageA + kk * 32), idesc,
+                               (kb | kk) != 0);
+                    mma_commit(smem_addr(&empty[st]));
+                }
+                mma_commit(smem_addr(&accbar));
+            }
+            __syncwarp();
+            // epilogue: warp w owns TMEM lanes (tile rows) 32w .. 32w+31
+            const bool ok = mbar_wait(smem_addr(&accbar), tiles_done & 1u, a.ctl);
+            ++tiles_done;
+            if (!ok) s_abort = 1;
+            __syncwarp();
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const int b = m0 + warp * 32 + lane;
+            const unsigned long long key = a.pkey[b];
+            unsigned *rrow = a.raster + ((size_t)(t % a.cap) * a.B + b) * a.words;
+            for (int c = 0; c < kTN / 32; ++c) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
+                if (!ok) continue;
+                const int j0 = n0 + c * 32;
+                int4 *Vp = (int4 *)(a.V + (size_t)b * a.n + j0);
+                int4 *rp = (int4 *)(a.r + (size_t)b * a.n + j0);
+                unsigned bits = 0;
+                uint32_t outw[8];
+#pragma unroll
+                for (int q4 = 0; q4 < 8; ++q4) {
+                    const int4 vv = Vp[q4], rr4 = rp[q4];
+                    const int4 th4 = __ldg((const int4 *)(a.th + j0) + q4), lk4 = __ldg((const int4 *)(a.lk + j0) + q4);
+                    const int4 rs4 = __ldg((const int4 *)(a.rs + j0) + q4), R4 = __ldg((const int4 *)(a.R + j0) + q4);
+                    int vin[4] = {vv.x, vv.y, vv.z, vv.w}, rin[4] = {rr4.x, rr4.y, rr4.z, rr4.w};
+                    const int thv[4] = {th4.x, th4.y, th4.z, th4.w}, lkv[4] = {lk4.x, lk4.y, lk4.z, lk4.w};
+                    const int rsv[4] = {rs4.x, rs4.y, rs4.z, rs4.w}, Rv[4] = {R4.x, R4.y, R4.z, R4.w};
+                    uint32_t bytes = 0;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const int q = q4 * 4 + e, j = j0 + q;
+                        const int acc = __float2int_rn(__uint_as_float(v[q]));
+                        int ext = 0;
+                        const unsigned thr = __ldg(a.prate + j);
+                        if (thr && poisson_fires(key, (unsigned)t, (unsigned)j, thr)) ext = __ldg(a.pamp + j);
+                        const bool fire = lif_update_i32(vin[e], rin[e], acc, ext, thv[e], lkv[e], rsv[e], Rv[e], overflow);
+                        bits |= (unsigned)fire << q;
+                        bytes |= (fire ? 0x38u : 0u) << (8 * e);      // E4M3 1.0
+                    }
+                    Vp[q4] = make_int4(vin[0], vin[1], vin[2], vin[3]);
+                    rp[q4] = make_int4(rin[0], rin[1], rin[2], rin[3]);
+                    outw[q4] = bytes;
+                }
+                uint4 *dst = (uint4 *)(Aout + (size_t)b * a.n + j0);
+                dst[0] = make_uint4(outw[0], outw[1], outw[2], outw[3]);
+                dst[1] = make_uint4(outw[4], outw[5], outw[6], outw[7]);
+                rrow[j0 >> 5] = bits;
+                my_spikes += (unsigned long long)__popc(bits);
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            __syncthreads();
+            if (s_abort) break;
+        }
+        // the spike bytes written this step are read by TMA (async proxy) next step
+        asm volatile("fence.proxy.async.global;\n" ::: "memory");
+        __syncthreads();
+        if (s_abort) break;
+        if (!grid_barrier(a.ctl)) { s_abort = 1; break; }
+        asm volatile("fence.proxy.async.global;\n" ::: "memory");
+    }
+
+    // drain: TMA loads issued and MMAs committed by this block complete before
+    // its shared memory and TMEM go away (bounded waits; no-ops when all
+    // phases have already completed)
+    if (warp == 0 && lane == 0) {
+        for (unsigned i = g_prod > kStages ? g_prod - kStages : 0; i < g_prod; ++i)
+            mbar_wait(smem_addr(&full[i % kStages]), (i / kStages) & 1u, a.ctl);
+    }
+    if (warp == 1 && lane == 0) {
+        for (unsigned i = g_mma > kStages ? g_mma - kStages : 0; i < g_mma; ++i)
+            mbar_wait(smem_addr(&empty[i % kStages]), (i / kStages) & 1u, a.ctl);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(tmem), "r"(kTmemCols));
+    if (overflow) atomicCAS(&a.ctl->status, 0, (int)SN_EOVERFLOW);
+    if (my_spikes) {
+        atomicAdd(&a.ctl->spikes, my_spikes);
+        atomicAdd(&a.ctl->events, my_spikes * (unsigned long long)a.n);
+    }
+}
+
+size_t shared_smem_bytes() { return (size_t)kStages * kStageBytes + 1024; }
+
+cudaError_t max_grid_shared(int *grid) {
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute((const void *)shared_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)shared_smem_bytes());
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void *)shared_kernel, kShThreads,
+                                                      shared_smem_bytes());
+    if (e != cudaSuccess) return e;
+    // one block per SM: TMEM columns and the 128 KiB pipeline are per block
+    *grid = (per > 0 ? 1 : 0) * sms;
+    return cudaSuccess;
+}
+
+cudaError_t launch_shared(const void *tmaps, const SharedHostArgs &h, int grid, cudaStream_t s) {
+    SharedArgs a;
+    a.n = h.n; a.B = h.B; a.t0 = h.t0; a.steps = h.steps; a.cap = h.cap; a.words = h.n / 32;
+    a.tiles_m = h.B / kTM;
+    a.tiles = a.tiles_m * (h.n / kTN);
+    a.A0 = h.A0; a.A1 = h.A1; a.V = h.V; a.r = h.r;
+    a.th = h.th; a.lk = h.lk; a.rs = h.rs; a.R = h.R;
+    a.prate = h.prate; a.pamp = h.pamp; a.pkey = h.pkey; a.raster = h.raster; a.ctl = h.ctl;
+    const CUtensorMap *tm = (const CUtensorMap *)tmaps;
+    const int g = grid < a.tiles ? grid : a.tiles;
+    void *args[] = {(void *)&tm[0], (void *)&tm[1], (void *)&tm[2], (void *)&a};
+    return cudaLaunchCooperativeKernel((const void *)shared_kernel, dim3(g), dim3(kShThreads), args,
+                                       shared_smem_bytes(), s);
+}
+
+}  // namespace sn

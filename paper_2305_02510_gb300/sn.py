@@ -82,6 +82,8 @@ def lib():
                                     C.POINTER(sn_synapses), C.POINTER(_P)],
                 "sn_batch_config": [_P, C.c_int32, C.c_int32],
                 "sn_autotune": [_P, C.c_int32, C.POINTER(C.c_float)],
+                "sn_create_shared_dense_i8": [C.POINTER(sn_config), C.POINTER(sn_neurons), _P, C.c_int32,
+                                              C.POINTER(_P)],
                 "sn_create_ff": [C.POINTER(sn_config), C.c_int32, _P, _P, C.POINTER(sn_ff_params), C.c_int32,
                                  C.c_int32, C.POINTER(_P)],
                 "sn_ff_forward": [_P, _P, _P, _P],
@@ -230,6 +232,31 @@ def sn_create_batch(nets, *, dtype=SN_F32, max_delay, record_steps=0, stream=Non
     _check(lib().sn_create_batch(C.byref(cfg), B, NR, SY, C.byref(h)))
     ctx = Ctx(h, total, cfg.dtype, words, "batch", 0)
     ctx.net_n = [int(np.asarray(d["threshold"]).size) for d in nets]
+    return ctx
+
+
+def sn_create_shared_dense_i8(threshold, leak, reset, refractory, w, trains, *, record_steps=0,
+                              stream=None) -> Ctx:
+    """Shared dense integer network (weights int8 [n, n], -8..8) driven by
+    `trains` input trains."""
+    keep = []
+    nr = _neurons(threshold, leak, reset, refractory, keep)
+    w8 = np.ascontiguousarray(w, np.int8)
+    cfg = _config(SN_I32, 1, 0, record_steps, stream)
+    h = _P()
+    _check(lib().sn_create_shared_dense_i8(C.byref(cfg), C.byref(nr), _ptr(w8), int(trains), C.byref(h)))
+    ctx = Ctx(h, nr.n * int(trains), SN_I32, nr.n * int(trains) // 32, "shared", nr.n * nr.n)
+    ctx.net_n = [nr.n] * int(trains)
+    return ctx
+
+
+def from_shared_workload(wl, *, record_steps=None, stream=None) -> Ctx:
+    rec = wl["steps"] if record_steps is None else record_steps
+    ctx = sn_create_shared_dense_i8(wl["threshold"], wl["leak"], wl["reset"], wl["refractory"],
+                                    wl["dense_w_i8"], wl["batch"], record_steps=rec, stream=stream)
+    po = wl["poisson"]
+    if len(po["neuron"]):
+        sn_set_poisson(ctx, po["neuron"], po["rate"], po["amplitude"], po["seed"])
     return ctx
 
 
