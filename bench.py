@@ -196,6 +196,7 @@ def extras(S, W, torch, stream, flush):
     plain_ev = sum(S.sn_get_counters(c)[2] for c in plain)
     del plain
     res["bptt"] = bptt_extra(S, W, torch, stream)
+    res["shared_dense"] = shared_extra(S, W, torch, stream, flush)
     res["batched"] = {
         "workload": "4096 networks, N log-uniform [64, 4096], p U(0.01, 0.2), delays 1..8",
         "networks": len(nets), "neurons": int(sum(w["n"] for w in nets)),
@@ -301,6 +302,49 @@ def bptt_extra(S, W, torch, stream):
     return {"workload": "700-1024-1024-20 LIF, per-synapse delays 1..4, batch 128, 100 steps, "
                         "checkpoint every 10", "synapses": syn, "ms_per_training_step": ms,
             "plain_torch_ms_per_training_step": plain_ms, "speedup_vs_plain_torch": plain_ms / ms}
+
+
+def shared_extra(S, W, torch, stream, flush):
+    """8192-neuron integer network shared by 256 Poisson input trains, 500
+    steps: one persistent launch whose per-step propagation is an exact FP8
+    tcgen05 GEMM, against the plain path (the single-network dense simulator
+    run once per train, same network, same input streams)."""
+    wl = W.shared_dense_i8()
+    n, B, T = wl["n"], wl["batch"], 500
+    ctx = S.from_shared_workload(wl, record_steps=T, stream=stream.cuda_stream)
+    ms, spk, ev = timed_runs(S, torch, stream, flush, ctx, T, 3)
+    del ctx
+    ops = 2.0 * B * n * n * T
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16 = float(json.load(f)["bf16_tflops"])
+        peak, src = 2.0 * bf16, "measured bf16 burst x 2 (nominal fp8/bf16 ratio)"
+    except Exception:
+        peak, src = 2.0 * 1900.0, "fallback bf16 x 2"
+    po = wl["poisson"]
+    plain = S.sn_create_dense(wl["threshold"], wl["leak"], wl["reset"], wl["refractory"],
+                              wl["dense_w_i8"].astype(np.float32), 1, record_steps=1, stream=stream.cuda_stream)
+    S.sn_set_poisson_stream(plain, po["neuron"], po["rate"], po["amplitude"], po["seed"], 0)
+    S.sn_run(plain, T)
+    torch.cuda.synchronize()
+    total, pev = 0.0, 0
+    for b in range(B):
+        S.sn_set_poisson_stream(plain, po["neuron"], po["rate"], po["amplitude"], po["seed"], b)
+        S.sn_reset(plain)
+        a, c = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        S.sn_run(plain, T)
+        c.record(stream)
+        S.sn_sync(plain)
+        total += a.elapsed_time(c)
+        pev += S.sn_get_counters(plain)[2]
+    return {"workload": "8192-neuron int8-weight network (-8..8), 256 Poisson trains, 500 steps",
+            "ms": ms, "synaptic_events_per_s": ev / (ms / 1e3), "spikes_per_train_step": spk / (B * T),
+            "roofline": {"bound": "tensor", "achieved": ops / (ms / 1e3) / 1e12, "peak": peak,
+                         "unit": "TFLOP/s", "frac": ops / (ms / 1e3) / 1e12 / peak, "peak_source": src,
+                         "kernel": "shared_kernel (tcgen05.mma kind::f8f6f4)"},
+            "plain_ms": total, "plain_synaptic_events_per_s": pev / (total / 1e3),
+            "speedup_vs_plain": total / ms, "launches": 1, "plain_launches": B}
 
 
 def run_reference(args, wl, rank):

@@ -39,6 +39,20 @@ sn_status size_sparse_executor(sn_ctx *c) {
     const int n = c->n;
     c->block = 256;
     const bool cta = (c->flags & SN_EXEC_CTA) || (!(c->flags & SN_EXEC_GRID) && n <= 2048);
+    // register-resident executor (used without STDP): at most one neuron per
+    // thread of a 512-thread block
+    {
+        int gr = 0;
+        cudaError_t e = max_grid_sparse_reg(&gr);
+        if (e != cudaSuccess) return fail(nullptr, SN_ECUDA, std::string("occupancy: ") + cudaGetErrorString(e));
+        if (cta) {
+            if (n <= kSparseRegBlock) { c->reg_grid = 1; c->reg_chunk = (n + 31) / 32 * 32; }
+        } else if (gr >= 1 && (long long)gr * kSparseRegBlock >= n) {
+            const int g = std::min(gr, (n + 31) / 32);
+            c->reg_chunk = ((n + g - 1) / g + 31) / 32 * 32;
+            c->reg_grid = (n + c->reg_chunk - 1) / c->reg_chunk;
+        }
+    }
     if (cta) {
         c->grid = 1;
         c->chunk = (n + 31) / 32 * 32;
@@ -444,8 +458,14 @@ sn_status sn_run(sn_ctx *c, int32_t steps) {
     a.stdp = c->stdp; a.decay = c->decay; a.a_plus = c->a_plus; a.a_minus = c->a_minus;
     a.wmin = c->wmin; a.wmax = c->wmax; a.trace = c->trace;
     a.ctl = c->ctl;
-    cudaError_t e = c->kind == KIND_SPARSE ? launch_sparse(a, c->dtype, c->grid, c->block, c->stream)
-                                           : launch_dense(a, c->grid, c->block, c->stream);
+    cudaError_t e;
+    if (c->kind == KIND_SPARSE && !c->stdp && c->reg_grid > 0) {
+        a.chunk = c->reg_chunk;
+        e = launch_sparse_reg(a, c->dtype, c->reg_grid, c->stream);
+    } else {
+        e = c->kind == KIND_SPARSE ? launch_sparse(a, c->dtype, c->grid, c->block, c->stream)
+                                   : launch_dense(a, c->grid, c->block, c->stream);
+    }
     if (e != cudaSuccess) return cuda_fail(c, e, "simulation launch");
     c->step += steps;
     if (c->step - c->raster_from > c->cap) c->raster_from = c->step - c->cap;

@@ -29,6 +29,7 @@ struct sn_ctx {
     int dense_delay = 1;
     // executor
     int grid = 1, block = 256, chunk = 32, S = 1;
+    int reg_grid = 0, reg_chunk = 0;   // register-resident sparse executor (0: not usable)
     // device memory
     void *V = nullptr;
     int *r = nullptr;

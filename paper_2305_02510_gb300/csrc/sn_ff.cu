@@ -333,6 +333,71 @@ ff_dw_kernel(const float *__restrict__ gI, const unsigned *__restrict__ sprev, i
     }
 }
 
+// Weight gradient from the spike lists (sparse form): input i's spikes are
+// few, so
+//   dW[i][j] = sum over spikes (t', b) of input i of gI[t' + D[i][j]][b][j]
+// with t' + D < T.  One block per input (and per 2048-column slice): it
+// compacts the rows (t', b) where the input spiked, in ascending order, into
+// shared memory, then each thread accumulates its columns over that list.
+constexpr int kDwJ = 8;                          // columns per thread
+constexpr int kDwCols = 256 * kDwJ;              // columns per block
+
+__global__ void __launch_bounds__(256)
+ff_dw_sparse_kernel(const float *__restrict__ gI, const unsigned *__restrict__ sprev, int words_in,
+                    const uint8_t *__restrict__ D, int n_in, int n_out, int B, int T, float *__restrict__ dW) {
+    extern __shared__ int s_rows[];             // [T * B] spike rows of input i
+    __shared__ int s_warp[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int i = blockIdx.x;
+    const int jb = blockIdx.y * kDwCols;
+    const int rows = T * B;
+    const int c = i >> 5;
+    const unsigned bit = 1u << (i & 31);
+    int count = 0;
+    for (int r0 = 0; r0 < rows; r0 += 256) {
+        const int r = r0 + threadIdx.x;
+        const bool sp = r < rows && (sprev[(size_t)r * words_in + c] & bit);
+        const unsigned ball = __ballot_sync(0xffffffffu, sp);
+        if (lane == 0) s_warp[warp] = __popc(ball);
+        __syncthreads();
+        int before = 0, total = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            const int v = s_warp[w];
+            before += w < warp ? v : 0;
+            total += v;
+        }
+        if (sp) s_rows[count + before + __popc(ball & ((1u << lane) - 1u))] = r;
+        count += total;
+        __syncthreads();
+    }
+    int dj[kDwJ];
+    float acc[kDwJ];
+#pragma unroll
+    for (int q = 0; q < kDwJ; ++q) {
+        const int j = jb + threadIdx.x + 256 * q;
+        dj[q] = j < n_out ? (int)D[(size_t)i * n_out + j] : 0;
+        acc[q] = 0.0f;
+    }
+    for (int k = 0; k < count; ++k) {
+        const int r = s_rows[k];
+        const int t = r / B, b = r - (r / B) * B;
+#pragma unroll
+        for (int q = 0; q < kDwJ; ++q) {
+            const int tt = t + dj[q];
+            if (dj[q] > 0 && tt < T)
+                acc[q] = __fadd_rn(acc[q], __ldg(gI + ((size_t)tt * B + b) * n_out + jb + threadIdx.x + 256 * q));
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kDwJ; ++q) {
+        const int j = jb + threadIdx.x + 256 * q;
+        if (j < n_out) dW[(size_t)i * n_out + j] = acc[q];
+    }
+}
+
+constexpr int kDwSparseMaxRows = 49152;          // spike-list capacity (192 KiB of shared memory)
+
 __global__ void ff_dw_reduce_kernel(const float *__restrict__ part, int splits, long long count,
                                     float *__restrict__ dW) {
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < count;
@@ -401,6 +466,15 @@ cudaError_t ff_bwd_data(const float *gI, const float *W, const uint8_t *D, int n
 
 cudaError_t ff_dw(const float *gI, const unsigned *sprev, int words_in, const uint8_t *D, int n_in, int n_out,
                   int B, int T, int splits, float *part, float *dW, cudaStream_t s) {
+    if (T * B <= kDwSparseMaxRows) {
+        const size_t smem = (size_t)T * B * sizeof(int);
+        cudaError_t e = cudaFuncSetAttribute((const void *)ff_dw_sparse_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        dim3 g(n_in, (n_out + kDwCols - 1) / kDwCols);
+        ff_dw_sparse_kernel<<<g, 256, smem, s>>>(gI, sprev, words_in, D, n_in, n_out, B, T, dW);
+        return cudaGetLastError();
+    }
     dim3 grid((n_out + 255) / 256, (n_in + 31) / 32, splits);
     ff_dw_kernel<<<grid, 256, 0, s>>>(gI, sprev, words_in, D, n_in, n_out, B, T, splits, part);
     cudaError_t e = cudaGetLastError();

@@ -150,6 +150,9 @@ cudaError_t ff_dw(const float *gI, const unsigned *sprev, int words_in, const ui
 cudaError_t launch_sparse(const NetArgs &a, int dtype, int grid, int block, cudaStream_t s);
 cudaError_t launch_dense(const NetArgs &a, int grid, int block, cudaStream_t s);
 cudaError_t max_grid_sparse(int dtype, int stdp, int block, int *grid);
+cudaError_t max_grid_sparse_reg(int *grid);
+cudaError_t launch_sparse_reg(const NetArgs &a, int dtype, int grid, cudaStream_t s);
+constexpr int kSparseRegBlock = 512;
 cudaError_t max_grid_dense(int block, int *grid, size_t *smem);
 cudaError_t launch_gather_weights(const uint2 *syn, const long long *perm_inv, long long m,
                                   float *out, cudaStream_t s);

@@ -90,12 +90,14 @@ __global__ void __launch_bounds__(kBlock) sparse_kernel(NetArgs a) {
     A *ring = (A *)a.ring;
     unsigned long long my_spikes = 0, my_events = 0;
 
+    __shared__ int s_stop;
     for (int s = 0; s < a.steps; ++s) {
-        if (ld_status(a.ctl) != 0) break;
+        // thread 0 reads the status for the whole block (a uniform exit)
+        if (threadIdx.x == 0) { s_cnt = 0; s_stop = ld_status(a.ctl); }
+        __syncthreads();
+        if (s_stop) break;
         const int t = a.t0 + s;
         const int cur = t % a.D1;
-        if (threadIdx.x == 0) s_cnt = 0;
-        __syncthreads();
         A *slot = ring + (size_t)cur * a.n;
         phase_update<MODE, STDP>(a, t, j0, j1, s_list, &s_cnt, [&](int j) -> V {
             A v = slot[j];
@@ -177,6 +179,179 @@ __global__ void __launch_bounds__(kBlock) sparse_kernel(NetArgs a) {
     // run counters: one atomic per thread that counted anything
     if (my_spikes) atomicAdd(&a.ctl->spikes, my_spikes);
     if (my_events) atomicAdd(&a.ctl->events, my_events);
+}
+
+// ---------------------------------------------------------------------------
+// Sparse push, register-resident variant (no STDP).  Block = 512 threads and
+// every thread owns at most one neuron, so the neuron's state, parameters,
+// Poisson source and CSR row bounds live in registers for the whole launch
+// (V and r are written back at the end).  The spikers of a step are compacted
+// with their row bounds; an exclusive scan of the row lengths flattens the
+// block's synapse work, and every thread keeps eight independent synapse
+// loads in flight before issuing their fixed-point atomics.
+
+constexpr int kRegBlock = 512;
+constexpr int kRegUnroll = 8;
+
+template <int MODE>
+__global__ void __launch_bounds__(kRegBlock) sparse_reg_kernel(NetArgs a) {
+    using A = typename Tr<MODE>::A;
+    using V = typename Tr<MODE>::V;
+    __shared__ int s_j[kRegBlock];
+    __shared__ long long s_beg[kRegBlock];
+    __shared__ int s_off[kRegBlock + 1];
+    __shared__ int s_wsum[kRegBlock / 32];
+    __shared__ int s_cnt, s_stop;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int j0 = blockIdx.x * a.chunk;
+    const int j1 = min(a.n, j0 + a.chunk);
+    const int j = j0 + threadIdx.x;
+    const bool mine = j < j1;
+    V v = 0, th = 0, lk = 0, rs = 0, amp = 0;
+    int rr = 0, R = 0, len = 0;
+    unsigned thr = 0;
+    long long beg = 0;
+    if (mine) {
+        v = ((const V *)a.V)[j];
+        rr = a.r[j];
+        th = ((const V *)a.th)[j];
+        lk = ((const V *)a.lk)[j];
+        rs = ((const V *)a.rs)[j];
+        R = a.R[j];
+        thr = a.prate[j];
+        amp = ((const V *)a.pamp)[j];
+        beg = a.rowptr[j];
+        len = (int)(a.rowptr[j + 1] - beg);
+    }
+    A *ring = (A *)a.ring;
+    unsigned long long my_spikes = 0, my_events = 0;
+    bool overflow = false;
+    for (int s = 0; s < a.steps; ++s) {
+        if (threadIdx.x == 0) { s_cnt = 0; s_stop = ld_status(a.ctl); }
+        __syncthreads();
+        if (s_stop) break;
+        const int t = a.t0 + s;
+        const int cur = t % a.D1;
+        bool fire = false;
+        if (mine) {
+            A *slot = ring + (size_t)cur * a.n;
+            const V acc = Tr<MODE>::from_acc(slot[j]);
+            slot[j] = 0;
+            V ext = 0;
+            if (t < a.ev_nsteps) {
+                int lo = a.ev_off[t], hi = a.ev_off[t + 1];
+                const int end = hi;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (a.ev_neuron[mid] < j) lo = mid + 1; else hi = mid;
+                }
+                if (lo < end && a.ev_neuron[lo] == j) ext = ((const V *)a.ev_val)[lo];
+            }
+            if (thr && poisson_fires(a.pkey, (unsigned)t, (unsigned)j, thr)) {
+                if (MODE == SN_F32) ext = __fadd_rn(ext, amp); else ext = ext + amp;
+            }
+            if constexpr (MODE == SN_F32) fire = lif_update_f32(v, rr, acc, ext, th, lk, rs, R);
+            else fire = lif_update_i32(v, rr, acc, ext, th, lk, rs, R, overflow);
+        }
+        const unsigned ball = __ballot_sync(0xffffffffu, fire);
+        const int wbase = j0 + warp * 32;
+        if (lane == 0 && wbase < j1) a.raster[(size_t)(t % a.cap) * a.words + (wbase >> 5)] = ball;
+        if (ball) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&s_cnt, __popc(ball));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (fire) {
+                const int q = base + __popc(ball & ((1u << lane) - 1u));
+                s_j[q] = j;
+                s_beg[q] = beg;
+                s_off[q] = len;
+            }
+        }
+        __syncthreads();
+        const int k = s_cnt;
+        // exclusive scan of the spikers' row lengths
+        const int x = threadIdx.x < k ? s_off[threadIdx.x] : 0;
+        int incl = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int w = lane < kRegBlock / 32 ? s_wsum[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += y;
+            }
+            if (lane < kRegBlock / 32) s_wsum[lane] = w;
+        }
+        __syncthreads();
+        const int total = s_wsum[kRegBlock / 32 - 1];
+        if (threadIdx.x < k) s_off[threadIdx.x] = (warp ? s_wsum[warp - 1] : 0) + incl - x;
+        if (threadIdx.x == 0) s_off[k] = total;
+        __syncthreads();
+        if (threadIdx.x == 0) { my_spikes += (unsigned long long)k; my_events += (unsigned long long)total; }
+        // flattened push: item e = synapse (e - s_off[q]) of spiker q
+        int q = 0;
+        for (int e0 = 0; e0 < total; e0 += kRegBlock * kRegUnroll) {
+            uint2 sy[kRegUnroll];
+            bool ok[kRegUnroll];
+#pragma unroll
+            for (int u = 0; u < kRegUnroll; ++u) {
+                const int e = e0 + u * kRegBlock + threadIdx.x;
+                ok[u] = e < total;
+                if (ok[u]) {
+                    while (s_off[q + 1] <= e) ++q;
+                    sy[u] = __ldg(a.syn + s_beg[q] + (e - s_off[q]));
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kRegUnroll; ++u) {
+                if (!ok[u]) continue;
+                const int post = (int)(sy[u].x & kPostMask);
+                int sl = cur + (int)(sy[u].x >> kPostBits) + 1;
+                if (sl >= a.D1) sl -= a.D1;
+                atomicAdd(ring + (size_t)sl * a.n + post, Tr<MODE>::to_acc(sy[u].y));
+            }
+        }
+        if (!grid_barrier(a.ctl)) break;
+    }
+    if (mine) {
+        ((V *)a.V)[j] = v;
+        a.r[j] = rr;
+    }
+    if (MODE == SN_I32 && overflow) atomicCAS(&a.ctl->status, 0, (int)SN_EOVERFLOW);
+    if (my_spikes) atomicAdd(&a.ctl->spikes, my_spikes);
+    if (my_events) atomicAdd(&a.ctl->events, my_events);
+}
+
+static const void *sparse_reg_fn(int dtype) {
+    return dtype == SN_F32 ? (const void *)sparse_reg_kernel<SN_F32> : (const void *)sparse_reg_kernel<SN_I32>;
+}
+
+cudaError_t max_grid_sparse_reg(int *grid) {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    int per = 1 << 30;
+    for (int dt : {(int)SN_F32, (int)SN_I32}) {
+        int p = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, sparse_reg_fn(dt), kRegBlock, 0);
+        if (e != cudaSuccess) return e;
+        per = p < per ? p : per;
+    }
+    *grid = per * sms;
+    return cudaSuccess;
+}
+
+cudaError_t launch_sparse_reg(const NetArgs &a, int dtype, int grid, cudaStream_t s) {
+    void *args[] = {(void *)&a};
+    return cudaLaunchCooperativeKernel(sparse_reg_fn(dtype), dim3(grid), dim3(kRegBlock), args, 0, s);
 }
 
 cudaError_t launch_sparse(const NetArgs &a, int dtype, int grid, int block, cudaStream_t s) {
@@ -265,12 +440,13 @@ __global__ void __launch_bounds__(kBlock) dense_kernel(NetArgs a) {
     float *ring = (float *)a.ring;
     unsigned long long my_spikes = 0;
 
+    __shared__ int s_stop;
     for (int s = 0; s < a.steps; ++s) {
-        if (ld_status(a.ctl) != 0) break;
+        if (threadIdx.x == 0) { s_cnt = 0; s_stop = ld_status(a.ctl); }
+        __syncthreads();
+        if (s_stop) break;
         const int t = a.t0 + s;
         const int cur = t % a.D1;
-        if (threadIdx.x == 0) s_cnt = 0;
-        __syncthreads();
         // U: fold the partials of step t-1 into the arrival slot, then update
         int arr = (t - 1 + a.dense_delay) % a.D1;
         phase_update<SN_F32, STDP>(a, t, j0, j1, list, &s_cnt, [&](int j) -> float {

@@ -11,9 +11,10 @@
 // bit-exact integer arithmetic.  (kind::i8 does not exist on sm_103a.)
 //
 // Tile = 128 trains x 128 post-neurons, accumulated in TMEM over the K = n
-// pre-neurons in 128-byte stages loaded by TMA (128B swizzle, 4 stages).
-// Warp 0 lane 0 issues TMA, warp 1 lane 0 issues the MMAs; afterwards the four
-// warps read the accumulator rows (tcgen05.ld) and apply the integer LIF rule
+// pre-neurons in 128-byte stages loaded by TMA (128B swizzle, 6 stages).
+// Warp 0 lane 0 issues TMA, warp 1 lane 0 issues the MMAs; afterwards the eight
+// warps read the accumulator rows (tcgen05.ld: warps w and w+4 share TMEM lane
+// quarter w, each taking half of the columns) and apply the integer LIF rule
 // (Section 2.1 order), write the spike bytes that are the next step's A
 // operand, the raster bits and the state.  A persistent cooperative launch
 // runs all steps; a grid barrier separates them.  Every wait is bounded: on
@@ -32,10 +33,10 @@ namespace sn {
 constexpr int kTM = 128;                       // trains per tile (MMA M)
 constexpr int kTN = 128;                       // post-neurons per tile (MMA N)
 constexpr int kTK = 128;                       // bytes of K per stage (one 128B swizzle row)
-constexpr int kStages = 4;
+constexpr int kStages = 6;
 constexpr int kStageA = kTM * kTK;             // 16 KiB
 constexpr int kStageBytes = (kTM + kTN) * kTK; // 32 KiB
-constexpr int kShThreads = 128;
+constexpr int kShThreads = 256;
 constexpr unsigned kTmemCols = 128;
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
@@ -207,18 +208,20 @@ shared_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ 
                 mma_commit(smem_addr(&accbar));
             }
             __syncwarp();
-            // epilogue: warp w owns TMEM lanes (tile rows) 32w .. 32w+31
+            // epilogue: warps w and w+4 own TMEM lanes (tile rows) 32(w%4) ..,
+            // each taking half of the 128 columns
             const bool ok = mbar_wait(smem_addr(&accbar), tiles_done & 1u, a.ctl);
             ++tiles_done;
             if (!ok) s_abort = 1;
             __syncwarp();
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const int b = m0 + warp * 32 + lane;
+            const int quarter = warp & 3, half = warp >> 2;
+            const int b = m0 + quarter * 32 + lane;
             const unsigned long long key = a.pkey[b];
             unsigned *rrow = a.raster + ((size_t)(t % a.cap) * a.B + b) * a.words;
-            for (int c = 0; c < kTN / 32; ++c) {
+            for (int c = half * (kTN / 64); c < (half + 1) * (kTN / 64); ++c) {
                 uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), v);
+                tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(c * 32), v);
                 if (!ok) continue;
                 const int j0 = n0 + c * 32;
                 int4 *Vp = (int4 *)(a.V + (size_t)b * a.n + j0);
