@@ -42,6 +42,26 @@ STATE_BYTES = 56
 NCU_TRAFFIC_BYTES = None
 
 
+def replica_seed(seed, rank):
+    """Poisson seed of replica `rank`: every rank simulates its own copy of the
+    network with its own input stream."""
+    return int(seed) + 7919 * int(rank)
+
+
+def combine_ranks(ms, events, e2e_s, e2e_events, world, device):
+    """Whole-job figures over the ranks: the slowest rank's time (max) and the
+    total work (sum).  With world == 1 the local figures."""
+    if world <= 1:
+        return ms, events, e2e_s, e2e_events
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms, events, e2e_s, e2e_events], dtype=torch.float64, device=device)
+    mx, sm = t.clone(), t.clone()
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[1]), float(mx[2]), float(sm[3])
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -417,7 +437,7 @@ def main():
 
     T = args.timesteps
     wl = W.large_sparse(integer=False, steps=T)
-    wl["poisson"]["seed"] = int(wl["poisson"]["seed"]) + 7919 * rank   # own input per replica
+    wl["poisson"]["seed"] = replica_seed(wl["poisson"]["seed"], rank)   # own input per replica
     stream = torch.cuda.current_stream()
     ctx = S.from_workload(wl, record_steps=T, stream=stream.cuda_stream)
     n = wl["n"]
@@ -467,15 +487,8 @@ def main():
         e_events += S.sn_get_counters(ctx)[2]
     e2e_s = time.perf_counter() - e0
 
-    t = torch.tensor([ms, events, e2e_s, e_events], dtype=torch.float64, device="cuda")
-    if world > 1:
-        mx = t.clone()
-        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
-        sm = t.clone()
-        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
-        ms_all, ev_all, e2e_all, e2e_ev_all = float(mx[0]), float(sm[1]), float(mx[2]), float(sm[3])
-    else:
-        ms_all, ev_all, e2e_all, e2e_ev_all = ms, events, e2e_s, e_events
+    ms_all, ev_all, e2e_all, e2e_ev_all = combine_ranks(ms, events, e2e_s, e_events, world,
+                                                         torch.device("cuda"))
     value = ev_all / (ms_all / 1e3)
 
     if rank == 0:
