@@ -330,12 +330,13 @@ sn_status sn_ff_get_checkpoints(sn_ctx *ctx, int32_t layer, float *v, int32_t on
  *                      sn_set_poisson with net = 0
  *   v, r               [n] state in/out (start: v = reset, r = 0)
  *   raster             [steps * ceil(n/32)] uint32 out, row k = step k
- * The kernel's scratch (partial sums, pending-input ring, control block)
- * lives in one static device array of SN_NOALLOC_SCRATCH_BYTES, held by
- * every device that loads the library until the process exits.  A network
- * whose scratch does not fit is rejected with SN_EINVAL; the need is about
- * 4 * (1024 * resident blocks + (delay + 2) * n) bytes, so every network up
- * to the 200,000-neuron dense limit fits while delay + 2 <= 16.  The first call on a device
+ * The kernel's scratch (spike bits of the last two steps, pending-input
+ * ring, control block) lives in one static device array of
+ * SN_NOALLOC_SCRATCH_BYTES, held by every device that loads the library until
+ * the process exits.  A network whose scratch does not fit is rejected with
+ * SN_EINVAL; the need is about 4 * (delay + 2) * n bytes, so every network up
+ * to the 200,000-neuron dense limit fits while delay <= 18.  The first call
+ * on a device
  * looks up the array's device address with that device current; make that
  * first call before any stream capture.  Every call shares the array and
  * clears it first, so calls whose work overlaps on the GPU (two streams,

@@ -244,27 +244,21 @@ sn_status sn_create_dense(const sn_config *cfg, const sn_neurons *nr, const floa
                                     destroy_all(c); delete c; g_create_err = msg; return st; };
     if ((s = upload_neurons(c, nr))) return bail(s);
     if ((s = alloc_common(c, cfg))) return bail(s);
-    // executor: one block per 32-aligned neuron chunk for the update, work
-    // items (column tile x spike chunk) for the gather
+    // executor: column slabs of 32 * cpl columns, one block each, co-resident
     c->block = 256;
-    size_t smem_words = (size_t)c->words;
-    int gmax = 0;
-    cudaError_t e = max_grid_dense(c->block, &gmax, &smem_words);
-    if (e != cudaSuccess) { c->err = std::string("occupancy: ") + cudaGetErrorString(e); return bail(SN_ECUDA); }
-    if (gmax < 1) { c->err = "dense executor: no resident blocks"; return bail(SN_EUNSUPPORTED); }
-    const bool cta = (cfg->flags & SN_EXEC_CTA) != 0;
-    int g = cta ? 1 : std::min(gmax, (n + 31) / 32);
-    c->chunk = ((n + g - 1) / g + 31) / 32 * 32;
-    if (c->chunk > 2048) { c->err = "dense executor: chunk too large"; return bail(SN_EUNSUPPORTED); }
-    c->grid = cta ? 1 : gmax;          // every resident block takes gather items
-    const int ntile = (n + 1023) / 1024;
-    c->S = std::max(1, (c->grid + ntile - 1) / ntile);
+    int grid = 0, chunk = 0;
+    cudaError_t e = plan_dense(n, &grid, &chunk);
+    if (e != cudaSuccess) { c->err = std::string("dense executor: ") + cudaGetErrorString(e); return bail(SN_ECUDA); }
+    if (grid < 1) { c->err = "dense network too large for a co-resident grid"; return bail(SN_EUNSUPPORTED); }
+    c->grid = grid;
+    c->chunk = chunk;
+    c->S = 1;
     c->ring_bytes = (size_t)c->D1 * n * 4;
-    if ((s = dalloc(c, &c->W, nn * 4)) || (s = dalloc(c, &c->partial, (size_t)c->S * n * 4)) ||
+    if ((s = dalloc(c, &c->W, nn * 4)) || (s = dalloc(c, &c->spk, (size_t)2 * c->words * 4)) ||
         (s = dalloc(c, &c->ring, c->ring_bytes)))
         return bail(s);
     if ((e = cudaMemcpy(c->W, w, nn * 4, cudaMemcpyHostToDevice)) ||
-        (e = cudaMemset(c->partial, 0, (size_t)c->S * n * 4)) || (e = cudaMemset(c->ring, 0, c->ring_bytes))) {
+        (e = cudaMemset(c->spk, 0, (size_t)2 * c->words * 4)) || (e = cudaMemset(c->ring, 0, c->ring_bytes))) {
         c->err = std::string("upload: ") + cudaGetErrorString(e);
         return bail(SN_ECUDA);
     }
@@ -384,9 +378,9 @@ sn_status sn_stdp(sn_ctx *c, float decay, float a_plus, float a_minus, float wmi
           std::isfinite(wmax) && wmin <= wmax))
         return fail(c, SN_EINVAL, "bad STDP parameters");
     if (!c->trace) {
-        sn_status s = dalloc(c, &c->trace, (size_t)2 * c->n * 4);
+        sn_status s = dalloc(c, &c->trace, (size_t)3 * c->n * 4);
         if (s) return s;
-        SN_CUDA(c, cudaMemset(c->trace, 0, (size_t)2 * c->n * 4));
+        SN_CUDA(c, cudaMemset(c->trace, 0, (size_t)3 * c->n * 4));
     }
     if (c->kind == KIND_SPARSE && !c->csc) {
         // CSC by post: {pre, CSR position}
@@ -453,7 +447,7 @@ sn_status sn_run(sn_ctx *c, int32_t steps) {
     a.ev_off = c->ev_off; a.ev_nsteps = c->ev_nsteps; a.ev_neuron = c->ev_neuron; a.ev_val = c->ev_val;
     a.rowptr = c->rowptr; a.syn = c->syn; a.colptr = c->colptr; a.csc = c->csc;
     a.ring = c->ring;
-    a.W = c->W; a.partial = c->partial; a.S = c->S; a.dense_delay = c->dense_delay;
+    a.W = c->W; a.partial = c->partial; a.S = c->S; a.dense_delay = c->dense_delay; a.spk = c->spk;
     a.raster = c->raster;
     a.stdp = c->stdp; a.decay = c->decay; a.a_plus = c->a_plus; a.a_minus = c->a_minus;
     a.wmin = c->wmin; a.wmax = c->wmax; a.trace = c->trace;
@@ -493,8 +487,8 @@ sn_status sn_reset(sn_ctx *c) {
     SN_CUDA(c, cudaMemcpyAsync(c->V, c->rs, vb, cudaMemcpyDeviceToDevice, c->stream));
     SN_CUDA(c, cudaMemsetAsync(c->r, 0, vb, c->stream));
     SN_CUDA(c, cudaMemsetAsync(c->ring, 0, c->ring_bytes, c->stream));
-    if (c->partial) SN_CUDA(c, cudaMemsetAsync(c->partial, 0, (size_t)c->S * c->n * 4, c->stream));
-    if (c->trace) SN_CUDA(c, cudaMemsetAsync(c->trace, 0, 2 * vb, c->stream));
+    if (c->spk) SN_CUDA(c, cudaMemsetAsync(c->spk, 0, (size_t)2 * c->words * 4, c->stream));
+    if (c->trace) SN_CUDA(c, cudaMemsetAsync(c->trace, 0, 3 * vb, c->stream));
     SN_CUDA(c, cudaMemsetAsync(c->raster, 0, (size_t)c->cap * c->words * 4, c->stream));
     SN_CUDA(c, cudaMemsetAsync(c->ctl, 0, sizeof(Control), c->stream));
     c->step = 0;
@@ -557,7 +551,8 @@ sn_status sn_get_trace(sn_ctx *c, float *x, int32_t on_device) {
     if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
     if (!x) return fail(c, SN_EINVAL, "trace is NULL");
     if (!c->trace) return fail(c, SN_ESTATE, "STDP was never enabled");
-    const int buf = c->step > 0 ? (int)((c->step - 1) & 1) : 1;
+    const int buf = c->kind == KIND_DENSE ? (int)((c->step + 2) % 3)
+                                          : (c->step > 0 ? (int)((c->step - 1) & 1) : 1);
     return copy_out(c, x, c->trace + (size_t)buf * c->n, (size_t)c->n * 4, on_device);
 }
 
@@ -603,7 +598,7 @@ sn_status sn_get_counters(sn_ctx *c, int64_t *steps, int64_t *spikes, int64_t *e
     return read_status(c);
 }
 
-// Checkpoint layout: header, V, r, ring, partial (dense), trace (if any),
+// Checkpoint layout: header, V, r, ring, spike bits (dense), trace (if any),
 // weights (sparse CSR words or dense W), counters.
 struct SaveHeader {
     char magic[8];
@@ -614,9 +609,9 @@ struct SaveHeader {
 
 static size_t save_size(const sn_ctx *c) {
     size_t s = sizeof(SaveHeader) + (size_t)c->n * 8 + c->ring_bytes;
-    if (c->kind == KIND_DENSE) s += (size_t)c->S * c->n * 4 + (size_t)c->n * c->n * 4;
+    if (c->kind == KIND_DENSE) s += (size_t)2 * c->words * 4 + (size_t)c->n * c->n * 4;
     else s += (size_t)(c->m > 0 ? c->m : 0) * 8;
-    if (c->trace) s += (size_t)2 * c->n * 4;
+    if (c->trace) s += (size_t)3 * c->n * 4;
     return s;
 }
 
@@ -648,12 +643,12 @@ sn_status sn_save(sn_ctx *c, void *buf, size_t *size) {
     if ((e = get(c->V, (size_t)c->n * 4)) || (e = get(c->r, (size_t)c->n * 4)) || (e = get(c->ring, c->ring_bytes)))
         return cuda_fail(c, e, "save");
     if (c->kind == KIND_DENSE) {
-        if ((e = get(c->partial, (size_t)c->S * c->n * 4)) || (e = get(c->W, (size_t)c->n * c->n * 4)))
+        if ((e = get(c->spk, (size_t)2 * c->words * 4)) || (e = get(c->W, (size_t)c->n * c->n * 4)))
             return cuda_fail(c, e, "save");
     } else if (c->m > 0 && (e = get(c->syn, (size_t)c->m * 8))) {
         return cuda_fail(c, e, "save");
     }
-    if (c->trace && (e = get(c->trace, (size_t)2 * c->n * 4))) return cuda_fail(c, e, "save");
+    if (c->trace && (e = get(c->trace, (size_t)3 * c->n * 4))) return cuda_fail(c, e, "save");
     *size = need;
     return SN_OK;
 }
@@ -668,7 +663,7 @@ sn_status sn_load(sn_ctx *c, const void *buf, size_t size) {
         hd.S != c->S)
         return fail(c, SN_EINVAL, "checkpoint is of a different network");
     if (hd.has_trace && !c->trace) {
-        sn_status s = dalloc(c, &c->trace, (size_t)2 * c->n * 4);
+        sn_status s = dalloc(c, &c->trace, (size_t)3 * c->n * 4);
         if (s) return s;
     }
     if (size < save_size(c)) return fail(c, SN_EINVAL, "checkpoint truncated");
@@ -683,12 +678,12 @@ sn_status sn_load(sn_ctx *c, const void *buf, size_t size) {
     if ((e = put(c->V, (size_t)c->n * 4)) || (e = put(c->r, (size_t)c->n * 4)) || (e = put(c->ring, c->ring_bytes)))
         return cuda_fail(c, e, "load");
     if (c->kind == KIND_DENSE) {
-        if ((e = put(c->partial, (size_t)c->S * c->n * 4)) || (e = put(c->W, (size_t)c->n * c->n * 4)))
+        if ((e = put(c->spk, (size_t)2 * c->words * 4)) || (e = put(c->W, (size_t)c->n * c->n * 4)))
             return cuda_fail(c, e, "load");
     } else if (c->m > 0 && (e = put(c->syn, (size_t)c->m * 8))) {
         return cuda_fail(c, e, "load");
     }
-    if (hd.has_trace && (e = put(c->trace, (size_t)2 * c->n * 4))) return cuda_fail(c, e, "load");
+    if (hd.has_trace && (e = put(c->trace, (size_t)3 * c->n * 4))) return cuda_fail(c, e, "load");
     Control h;
     memset(&h, 0, sizeof(h));
     h.spikes = hd.spikes;

@@ -49,6 +49,7 @@ struct sn_ctx {
     void *ring = nullptr;
     size_t ring_bytes = 0;
     float *W = nullptr, *partial = nullptr;
+    unsigned *spk = nullptr;          // dense: spike bits of the last two steps [2][words]
     unsigned *raster = nullptr;
     float *trace = nullptr;
     Control *ctl = nullptr;

@@ -69,10 +69,11 @@ struct NetArgs {
     int S, dense_delay;
     // spikes
     unsigned *raster;                 // [cap][words]
+    unsigned *spk;                    // [2][words] spike bits of the last two steps (dense)
     // STDP
     int stdp;
     float decay, a_plus, a_minus, wmin, wmax;
-    float *trace;                     // [2][n], buffer (t & 1) holds x(t)
+    float *trace;                     // [3][n]: sparse kernels use buffer t & 1, dense t % 3
     Control *ctl;
 };
 
@@ -153,7 +154,7 @@ cudaError_t max_grid_sparse(int dtype, int stdp, int block, int *grid);
 cudaError_t max_grid_sparse_reg(int *grid);
 cudaError_t launch_sparse_reg(const NetArgs &a, int dtype, int grid, cudaStream_t s);
 constexpr int kSparseRegBlock = 512;
-cudaError_t max_grid_dense(int block, int *grid, size_t *smem);
+cudaError_t plan_dense(int n, int *grid, int *chunk);
 cudaError_t launch_gather_weights(const uint2 *syn, const long long *perm_inv, long long m,
                                   float *out, cudaStream_t s);
 

@@ -392,24 +392,31 @@ cudaError_t max_grid_sparse(int dtype, int stdp, int block, int *grid) {
 }
 
 // ---------------------------------------------------------------------------
-// Dense network: W[n][n] row-major (row = pre).  After every block's update
-// of step t (barrier), work items (column tile, spike chunk) gather the rows of
-// the spikers of step t, in ascending pre order within a chunk, into
-// partial[chunk][column].  The next update sums the S partials of its neurons
-// in chunk order into the ring slot of the arrival step, so the result does
-// not depend on timing.
+// Dense network: W[n][n] row-major (row = pre), one grid barrier per step.
+// Block c owns the column slab [c * cw, c * cw + cw), cw = 32 * CPL, and the
+// neurons with the same indices.  Step t:
+//   update(t):  own neurons (state in registers), input from the block's own
+//               ring slot t; spikes -> spike bits of t (double buffer), raster;
+//   grid barrier;
+//   gather(t):  every block walks the spikers of step t in ascending order,
+//               each warp taking every eighth row, and sums W[i][own columns];
+//               the eight warp partials are folded in warp order and stored as
+//               the input arriving at t + delay.  With STDP the block also
+//               updates its columns of the spiking rows (LTD, and LTP where the
+//               column spiked) before using them, and its spiking columns in
+//               the other rows (LTP), from the traces of step t-1.
+// Every write to W[:, slab] and to the slab's ring comes from the owning
+// block, so no other synchronisation is needed; the result does not depend on
+// thread timing.
 
-constexpr int kDenseCols = 4;                      // columns per thread per tile
-constexpr int kTile = kBlock * kDenseCols;         // columns per tile
-constexpr int kListMax = 2048;                     // spikers held in shared memory
+constexpr int kDListMax = 2048;                    // spikers held in shared memory
 
-// Spikers of step t with rank in [lo, hi) (ascending neuron order) into list.
+// Spikers of a spike-bit row with rank in [lo, hi) (ascending neuron order).
 __device__ void extract_ranks(const unsigned *rrow, const int *wpre, int words, int lo, int hi,
                               int *list) {
-    // first word whose prefix count exceeds lo
     int a = 0, b = words;
     while (a < b) {
-        int mid = (a + b) >> 1;
+        const int mid = (a + b) >> 1;
         if (wpre[mid + 1] <= lo) a = mid + 1; else b = mid;
     }
     for (int w = a + threadIdx.x; w < words && wpre[w] < hi; w += blockDim.x) {
@@ -424,205 +431,259 @@ __device__ void extract_ranks(const unsigned *rrow, const int *wpre, int words, 
     }
 }
 
-template <bool STDP>
+// Block-wide exclusive prefix of the popcounts of a spike-bit row into wpre
+// (words + 1 entries; wpre[words] = total).
+__device__ void popcount_prefix(const unsigned *row, int words, int *wpre, int *s_scan) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    int run = 0;
+    for (int w0 = 0; w0 < words; w0 += blockDim.x) {
+        const int w = w0 + threadIdx.x;
+        const int c = w < words ? __popc(row[w]) : 0;
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) s_scan[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            int v = lane < nw ? s_scan[lane] : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= o) v += y;
+            }
+            if (lane < nw) s_scan[lane] = v;
+        }
+        __syncthreads();
+        if (w < words) wpre[w] = run + (warp ? s_scan[warp - 1] : 0) + incl - c;
+        run += s_scan[nw - 1];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) wpre[words] = run;
+    __syncthreads();
+}
+
+template <int CPL, bool STDP>
 __global__ void __launch_bounds__(kBlock) dense_kernel(NetArgs a) {
     extern __shared__ int smem[];
-    int *wpre = smem;                           // [words + 1] prefix popcounts
-    int *list = smem + a.words + 1;             // [kListMax]
-    __shared__ int s_cnt;
+    constexpr int cw = 32 * CPL;
+    constexpr int nwarp = kBlock / 32;
+    int *wpre = smem;                                  // [words + 1]
+    int *list = smem + a.words + 1;                    // [kDListMax]
+    float *wpart = (float *)(list + kDListMax);        // [nwarp][cw]
     __shared__ int s_scan[kBlock / 32];
+    __shared__ int s_stop;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int j0 = blockIdx.x * a.chunk;
-    const int j1 = min(a.n, j0 + a.chunk);
     const int n = a.n;
-    const int ntile = (n + kTile - 1) / kTile;
-    const int items = ntile * a.S;
+    const int c0 = blockIdx.x * cw;
+    const int j = c0 + threadIdx.x;
+    const bool mine = threadIdx.x < cw && j < n;
     float *ring = (float *)a.ring;
+    float v = 0, th = 0, lk = 0, rs = 0, amp = 0;
+    int rr = 0, R = 0;
+    unsigned thr = 0;
+    if (mine) {
+        v = ((const float *)a.V)[j];
+        rr = a.r[j];
+        th = ((const float *)a.th)[j];
+        lk = ((const float *)a.lk)[j];
+        rs = ((const float *)a.rs)[j];
+        R = a.R[j];
+        thr = a.prate[j];
+        amp = ((const float *)a.pamp)[j];
+    }
     unsigned long long my_spikes = 0;
 
-    __shared__ int s_stop;
     for (int s = 0; s < a.steps; ++s) {
-        if (threadIdx.x == 0) { s_cnt = 0; s_stop = ld_status(a.ctl); }
+        if (threadIdx.x == 0) s_stop = ld_status(a.ctl);
         __syncthreads();
         if (s_stop) break;
         const int t = a.t0 + s;
         const int cur = t % a.D1;
-        // U: fold the partials of step t-1 into the arrival slot, then update
-        int arr = (t - 1 + a.dense_delay) % a.D1;
-        phase_update<SN_F32, STDP>(a, t, j0, j1, list, &s_cnt, [&](int j) -> float {
-            float sum = 0.0f;
-            for (int c = 0; c < a.S; ++c) sum = __fadd_rn(sum, a.partial[(size_t)c * n + j]);
-            ring[(size_t)arr * n + j] = sum;
-            return ring[(size_t)cur * n + j];
-        });
-        __syncthreads();
-        if (threadIdx.x == 0) my_spikes += (unsigned long long)s_cnt;
+        // ---- update(t)
+        bool fire = false;
+        if (mine) {
+            const float acc = ring[(size_t)cur * n + j];
+            float ext = 0.0f;
+            if (t < a.ev_nsteps) {
+                int lo = a.ev_off[t], hi = a.ev_off[t + 1];
+                const int end = hi;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (a.ev_neuron[mid] < j) lo = mid + 1; else hi = mid;
+                }
+                if (lo < end && a.ev_neuron[lo] == j) ext = ((const float *)a.ev_val)[lo];
+            }
+            if (thr && poisson_fires(a.pkey, (unsigned)t, (unsigned)j, thr)) ext = __fadd_rn(ext, amp);
+            fire = lif_update_f32(v, rr, acc, ext, th, lk, rs, R);
+            if constexpr (STDP) {
+                const float xo = a.trace[(size_t)((t + 2) % 3) * n + j];
+                a.trace[(size_t)(t % 3) * n + j] = __fadd_rn(__fmul_rn(a.decay, xo), fire ? 1.0f : 0.0f);
+            }
+        }
+        if (threadIdx.x < cw) {
+            const unsigned ball = __ballot_sync(0xffffffffu, fire);
+            if (lane == 0 && c0 + warp * 32 < n) {
+                const int word = (c0 >> 5) + warp;
+                a.spk[(size_t)(t & 1) * a.words + word] = ball;
+                a.raster[(size_t)(t % a.cap) * a.words + word] = ball;
+                my_spikes += (unsigned long long)__popc(ball);
+            }
+        }
         if (!grid_barrier(a.ctl)) break;
 
-        // G: prefix popcounts of the raster row of step t
-        const unsigned *rrow = a.raster + (size_t)(t % a.cap) * a.words;
-        {
-            int run = 0;
-            for (int w0 = 0; w0 < a.words; w0 += blockDim.x) {
-                const int w = w0 + threadIdx.x;
-                int c = w < a.words ? __popc(rrow[w]) : 0;
-                int incl = c;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    int y = __shfl_up_sync(0xffffffffu, incl, o);
-                    if (lane >= o) incl += y;
-                }
-                if (lane == 31) s_scan[warp] = incl;
-                __syncthreads();
-                if (warp == 0) {
-                    int v = lane < (int)(blockDim.x >> 5) ? s_scan[lane] : 0;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        int y = __shfl_up_sync(0xffffffffu, v, o);
-                        if (lane >= o) v += y;
-                    }
-                    if (lane < (int)(blockDim.x >> 5)) s_scan[lane] = v;
-                }
-                __syncthreads();
-                const int wexcl = warp ? s_scan[warp - 1] : 0;
-                if (w < a.words) wpre[w] = run + wexcl + incl - c;
-                const int tot = s_scan[(blockDim.x >> 5) - 1];
-                __syncthreads();
-                run += tot;
-            }
-            if (threadIdx.x == 0) wpre[a.words] = run;
-            __syncthreads();
-        }
+        // ---- gather(t): input of t + delay (and STDP of step t)
+        const unsigned *row_bits = a.spk + (size_t)(t & 1) * a.words;
+        popcount_prefix(row_bits, a.words, wpre, s_scan);
         const int k = wpre[a.words];
-        const float *xo = STDP ? a.trace + (size_t)((t & 1) ^ 1) * n : nullptr;
-
-        for (int item = blockIdx.x; item < items; item += gridDim.x) {
-            const int tile = item % ntile, chunk = item / ntile;
-            const int lo = (int)((long long)chunk * k / a.S);
-            const int hi = (int)((long long)(chunk + 1) * k / a.S);
-            const int c0 = tile * kTile + threadIdx.x;
-            float acc[kDenseCols];
-            float xc[kDenseCols];
-            bool sc[kDenseCols];
+        const float *xo = STDP ? a.trace + (size_t)((t + 2) % 3) * n : nullptr;   // x(t-1)
+        float acc[CPL];
+        bool sc[CPL];
+        float xc[CPL];
 #pragma unroll
-            for (int u = 0; u < kDenseCols; ++u) {
-                acc[u] = 0.0f;
-                const int c = c0 + u * kBlock;
-                if (STDP && c < n) { xc[u] = xo[c]; sc[u] = spiked(rrow, c); }
-                else { xc[u] = 0.0f; sc[u] = false; }
-            }
-            for (int base = lo; base < hi; base += kListMax) {
-                const int cnt = min(kListMax, hi - base);
-                __syncthreads();
-                extract_ranks(rrow, wpre, a.words, base, base + cnt, list);
-                __syncthreads();
-                int q = 0;
-                if constexpr (!STDP) {
-                    for (; q + 4 <= cnt; q += 4) {
-                        float v[4][kDenseCols];
-#pragma unroll
-                        for (int r = 0; r < 4; ++r) {
-                            const float *row = a.W + (size_t)list[q + r] * n;
-#pragma unroll
-                            for (int u = 0; u < kDenseCols; ++u) {
-                                const int c = c0 + u * kBlock;
-                                v[r][u] = c < n ? __ldg(row + c) : 0.0f;
-                            }
-                        }
-#pragma unroll
-                        for (int r = 0; r < 4; ++r)
-#pragma unroll
-                            for (int u = 0; u < kDenseCols; ++u) acc[u] = __fadd_rn(acc[u], v[r][u]);
-                    }
-                }
-                for (; q < cnt; ++q) {
-                    const int i = list[q];
-                    float *row = a.W + (size_t)i * n;
-                    const float xi = STDP ? xo[i] : 0.0f;
-#pragma unroll
-                    for (int u = 0; u < kDenseCols; ++u) {
-                        const int c = c0 + u * kBlock;
-                        if (c >= n) continue;
-                        float w = row[c];
-                        if (STDP && c != i) {
-                            float dw = sc[u] ? __fmul_rn(a.a_plus, xi) : 0.0f;
-                            dw = __fsub_rn(dw, __fmul_rn(a.a_minus, xc[u]));
-                            w = clampf(__fadd_rn(w, dw), a.wmin, a.wmax);
-                            row[c] = w;
-                        }
-                        acc[u] = __fadd_rn(acc[u], w);
-                    }
-                }
-            }
-            float *part = a.partial + (size_t)chunk * n;
-#pragma unroll
-            for (int u = 0; u < kDenseCols; ++u) {
-                const int c = c0 + u * kBlock;
-                if (c < n) part[c] = acc[u];
-            }
+        for (int q = 0; q < CPL; ++q) {
+            acc[q] = 0.0f;
+            const int col = c0 + lane + 32 * q;
+            sc[q] = false;
+            xc[q] = 0.0f;
+            if (STDP && col < n) { sc[q] = spiked(row_bits, col); xc[q] = xo[col]; }
         }
-
-        if constexpr (STDP) {
-            // LTP on columns of spiking post-neurons, rows of non-spiking
-            // pre-neurons (spiking rows were updated in full above).
-            const int nwarp_grid = gridDim.x * (blockDim.x >> 5);
-            const int gw = blockIdx.x * (blockDim.x >> 5) + warp;
-            for (int base = 0; base < k; base += kListMax) {
-                const int cnt = min(kListMax, k - base);
-                __syncthreads();
-                extract_ranks(rrow, wpre, a.words, base, base + cnt, list);
-                __syncthreads();
-                for (int i = gw; i < n; i += nwarp_grid) {
-                    if (spiked(rrow, i)) continue;
+        for (int base = 0; base < k; base += kDListMax) {
+            const int cnt = min(kDListMax, k - base);
+            __syncthreads();
+            extract_ranks(row_bits, wpre, a.words, base, base + cnt, list);
+            __syncthreads();
+            int r = warp;
+            if constexpr (!STDP) {
+                // sixteen rows per warp in flight
+                for (; r + 15 * nwarp < cnt; r += 16 * nwarp) {
+                    float w16[16][CPL];
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const float *row = a.W + (size_t)list[r + u * nwarp] * n;
+#pragma unroll
+                        for (int q = 0; q < CPL; ++q) {
+                            const int col = c0 + lane + 32 * q;
+                            w16[u][q] = col < n ? __ldg(row + col) : 0.0f;
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < 16; ++u)
+#pragma unroll
+                        for (int q = 0; q < CPL; ++q) acc[q] = __fadd_rn(acc[q], w16[u][q]);
+                }
+            }
+            for (; r < cnt; r += nwarp) {
+                const int i = list[r];
+                float *row = a.W + (size_t)i * n;
+                const float xi = STDP ? xo[i] : 0.0f;
+#pragma unroll
+                for (int q = 0; q < CPL; ++q) {
+                    const int col = c0 + lane + 32 * q;
+                    if (col >= n) continue;
+                    float w = row[col];
+                    if (STDP && col != i) {
+                        float dw = sc[q] ? __fmul_rn(a.a_plus, xi) : 0.0f;
+                        dw = __fsub_rn(dw, __fmul_rn(a.a_minus, xc[q]));
+                        w = clampf(__fadd_rn(w, dw), a.wmin, a.wmax);
+                        row[col] = w;
+                    }
+                    acc[q] = __fadd_rn(acc[q], w);
+                }
+            }
+            if constexpr (STDP) {
+                // LTP in the spiking columns of this list chunk, rows that did not
+                // spike; the rows are shared out over every warp of the grid (no
+                // block writes a row the gather touches: those rows spiked)
+                const int gwarps = gridDim.x * nwarp;
+                for (int i = blockIdx.x * nwarp + warp; i < n; i += gwarps) {
+                    if (spiked(row_bits, i)) continue;
                     const float dw = __fmul_rn(a.a_plus, xo[i]);
                     float *row = a.W + (size_t)i * n;
                     for (int q = lane; q < cnt; q += 32) {
-                        const int j = list[q];
-                        row[j] = clampf(__fadd_rn(row[j], dw), a.wmin, a.wmax);
+                        const int jj = list[q];
+                        row[jj] = clampf(__fadd_rn(row[jj], dw), a.wmin, a.wmax);
                     }
                 }
             }
         }
-        if (!grid_barrier(a.ctl)) break;
+        // fold the warp partials in warp order; the input of t + delay
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) wpart[warp * cw + lane + 32 * q] = acc[q];
+        __syncthreads();
+        if (mine) {
+            float sum = 0.0f;
+#pragma unroll
+            for (int w = 0; w < nwarp; ++w) sum = __fadd_rn(sum, wpart[w * cw + threadIdx.x]);
+            ring[(size_t)((t + a.dense_delay) % a.D1) * n + j] = sum;
+        }
+        __syncthreads();
     }
-    if (threadIdx.x == 0 && my_spikes) {
+    if (mine) {
+        ((float *)a.V)[j] = v;
+        a.r[j] = rr;
+    }
+    if (my_spikes) {
         atomicAdd(&a.ctl->spikes, my_spikes);
         atomicAdd(&a.ctl->events, my_spikes * (unsigned long long)n);
     }
 }
 
-static size_t dense_smem(int words) { return (size_t)(words + 1 + kListMax) * sizeof(int); }
-
-cudaError_t launch_dense(const NetArgs &a, int grid, int block, cudaStream_t s) {
-    void *args[] = {(void *)&a};
-    const size_t smem = dense_smem(a.words);
-    const void *fn = a.stdp ? (const void *)dense_kernel<true> : (const void *)dense_kernel<false>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(block), args, smem, s);
+static size_t dense_smem(int words, int cpl) {
+    return (size_t)(words + 1 + kDListMax) * sizeof(int) + (size_t)(kBlock / 32) * 32 * cpl * sizeof(float);
 }
 
-cudaError_t max_grid_dense(int block, int *grid, size_t *smem_for_words) {
-    int dev = 0, sms = 0, per = 0;
+static const void *dense_fn(int cpl, bool stdp) {
+    switch (cpl) {
+        case 1: return stdp ? (const void *)dense_kernel<1, true> : (const void *)dense_kernel<1, false>;
+        case 2: return stdp ? (const void *)dense_kernel<2, true> : (const void *)dense_kernel<2, false>;
+        case 4: return stdp ? (const void *)dense_kernel<4, true> : (const void *)dense_kernel<4, false>;
+        default: return stdp ? (const void *)dense_kernel<8, true> : (const void *)dense_kernel<8, false>;
+    }
+}
+
+cudaError_t launch_dense(const NetArgs &a, int grid, int block, cudaStream_t s) {
+    (void)block;
+    void *args[] = {(void *)&a};
+    const size_t smem = dense_smem(a.words, a.chunk / 32);
+    const void *fn = dense_fn(a.chunk / 32, a.stdp != 0);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), args, smem, s);
+}
+
+// Executor plan of a dense network: the smallest columns-per-lane (1, 2, 4,
+// 8) whose grid of ceil(n / (32 * cpl)) blocks is co-resident.
+cudaError_t plan_dense(int n, int *grid, int *chunk) {
+    int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    const int words = (int)(*smem_for_words);
-    const size_t smem = dense_smem(words);
-    for (const void *fn : {(const void *)dense_kernel<true>, (const void *)dense_kernel<false>}) {
-        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
+    const int words = (n + 31) / 32;
+    for (int cpl : {1, 2, 4, 8}) {
+        const size_t smem = dense_smem(words, cpl);
+        int per = 1 << 30;
+        for (bool st : {false, true}) {
+            const void *fn = dense_fn(cpl, st);
+            e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            int p = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, fn, kBlock, smem);
+            if (e != cudaSuccess) return e;
+            per = p < per ? p : per;
+        }
+        const int g = (n + 32 * cpl - 1) / (32 * cpl);
+        if (per > 0 && g <= per * sms) {
+            *grid = g;
+            *chunk = 32 * cpl;
+            return cudaSuccess;
+        }
     }
-    per = 1 << 30;
-    for (const void *fn : {(const void *)dense_kernel<true>, (const void *)dense_kernel<false>}) {
-        int p = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, fn, block, smem);
-        if (e != cudaSuccess) return e;
-        per = p < per ? p : per;
-    }
-    *grid = per * sms;
-    *smem_for_words = smem;
+    *grid = 0;
+    *chunk = 0;
     return cudaSuccess;
 }
 

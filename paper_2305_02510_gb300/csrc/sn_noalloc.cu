@@ -1,8 +1,8 @@
 // sn_run_dense_noalloc: the dense simulation for callers that cannot allocate
 // device memory.  It launches the same dense kernel as sn_run on a dense
 // context, but every buffer comes from the caller except the kernel's scratch
-// (partial sums, pending-input ring, zero Poisson table, control block), which
-// lives in one fixed file-scope device array.  No cudaMalloc, cudaFree or
+// (spike bits of the last two steps, pending-input ring, zero Poisson table,
+// control block), which lives in one fixed file-scope device array.  No cudaMalloc, cudaFree or
 // allocating library routine is called on this path.
 
 #include <cuda_runtime.h>
@@ -59,22 +59,15 @@ extern "C" sn_status sn_run_dense_noalloc(const sn_dense_noalloc_args *p) {
     cudaStream_t stream = (cudaStream_t)p->cuda_stream;
 
     // executor sizing, the same rule as a dense context
-    const int block = 256;
     const int words = (n + 31) / 32;
-    size_t smem_words = (size_t)words;
-    int gmax = 0;
-    if (max_grid_dense(block, &gmax, &smem_words) != cudaSuccess || gmax < 1) return SN_ECUDA;
-    const int g = std::min(gmax, (n + 31) / 32);
-    const int chunk = ((n + g - 1) / g + 31) / 32 * 32;
-    if (chunk > 2048) return SN_EUNSUPPORTED;
-    const int grid = gmax;
-    const int ntile = (n + 1023) / 1024;
-    const int S = std::max(1, (grid + ntile - 1) / ntile);
+    int grid = 0, chunk = 0;
+    if (plan_dense(n, &grid, &chunk) != cudaSuccess) return SN_ECUDA;
+    if (grid < 1) return SN_EUNSUPPORTED;
     const int D1 = p->delay + 1;
 
-    // scratch layout: control | partial [S][n] | ring [D1][n] | zero Poisson table [n]
-    const size_t off_part = align256(sizeof(Control));
-    const size_t off_ring = off_part + align256((size_t)S * n * 4);
+    // scratch layout: control | spike bits [2][words] | ring [D1][n] | zero Poisson table [n]
+    const size_t off_spk = align256(sizeof(Control));
+    const size_t off_ring = off_spk + align256((size_t)2 * words * 4);
     const size_t off_zero = off_ring + align256((size_t)D1 * n * 4);
     const size_t need = off_zero + align256((size_t)n * 4);
     if (need > kScratchBytes) return SN_EINVAL;   // beyond the fixed scratch
@@ -86,7 +79,7 @@ extern "C" sn_status sn_run_dense_noalloc(const sn_dense_noalloc_args *p) {
     if (st != SN_OK) return st;
     unsigned char *b = (unsigned char *)base;
 
-    // zero what must start at zero: control block, partial sums, ring, table
+    // zero what must start at zero: control block, spike bits, ring, table
     if (cudaMemsetAsync(b, 0, need, stream) != cudaSuccess) return SN_ECUDA;
 
     NetArgs a;
@@ -108,13 +101,13 @@ extern "C" sn_status sn_run_dense_noalloc(const sn_dense_noalloc_args *p) {
         a.pkey = sm(p->seed ^ sm(0ull));
     }
     a.W = (float *)p->w;
-    a.partial = (float *)(b + off_part);
-    a.S = S;
+    a.spk = (unsigned *)(b + off_spk);
+    a.S = 1;
     a.dense_delay = p->delay;
     a.ring = b + off_ring;
     a.raster = p->raster;
     a.ctl = (Control *)b;
-    if (launch_dense(a, grid, block, stream) != cudaSuccess) return SN_ECUDA;
+    if (launch_dense(a, grid, 256, stream) != cudaSuccess) return SN_ECUDA;
 
     // wait, then read the device status word (no allocation involved)
     if (cudaStreamSynchronize(stream) != cudaSuccess) return SN_ECUDA;
