@@ -184,7 +184,7 @@ def extras(S, W, torch, stream, flush):
             "spikes_per_timestep": spk / 1000,
             "roofline": {"bound": "hbm", "achieved": abytes / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": abytes / (ms / 1e3) / 1e9 / peak, "peak_source": src,
-                         "kernel": "dense_kernel<%s>" % ("true" if stdp else "false")}}
+                         "kernel": "dense_kernel<CPL,%s>" % ("true" if stdp else "false")}}
         del ctx
     res["dense_stdp"]["stdp_overhead"] = res["dense_stdp"]["ms"] / res["dense"]["ms"]
     # batched networks against the plain per-network path
@@ -508,7 +508,7 @@ def main():
             "wall_ms_per_step": 1e3 * wall / args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": src,
-                         "traffic": NCU_TRAFFIC_BYTES, "kernel": "sparse_kernel<SN_F32,false>",
+                         "traffic": NCU_TRAFFIC_BYTES, "kernel": "sparse_reg_kernel<SN_F32>",
                          "algorithmic_bytes_per_launch": abytes},
             "e2e": {"value": e2e_ev_all / e2e_all, "unit": UNIT,
                     "h2d_bytes_per_step": 8 * n,
