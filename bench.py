@@ -125,6 +125,15 @@ def algorithmic_bytes(n, timesteps, spikes, events):
     return spikes * 16 + events * 16 + timesteps * n * STATE_BYTES + timesteps * n / 8
 
 
+def algorithmic_bytes_pull(n, m, timesteps):
+    """Bytes pull propagation must move per launch: every timestep each
+    neuron's incoming synapses (8 B each, packed pre | delay and weight) and
+    the update phase's state traffic and raster bit.  The spike-history rows
+    each block copies into shared memory are not counted (L2 reads of a few
+    MB per step)."""
+    return timesteps * (m * 8 + n * STATE_BYTES + n / 8)
+
+
 def oracle_sample(wl, warm=40, timed=60):
     """The CPU oracle as it stands, single-threaded, on a bounded sample of the
     workload: `warm` untimed timesteps from the initial state (past the start-up
@@ -441,7 +450,12 @@ def main():
     stream = torch.cuda.current_stream()
     ctx = S.from_workload(wl, record_steps=T, stream=stream.cuda_stream)
     n = wl["n"]
+    m = int(len(wl["pre"]))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")   # > 129 MB L2
+    # the public autotuner times push and pull propagation on this network's
+    # own input over a whole run and keeps the faster
+    S.sn_autotune(ctx, T)
+    pull = S.sn_get_propagation(ctx) == S.SN_PULL
 
     def one(record):
         S.sn_reset(ctx)
@@ -493,14 +507,15 @@ def main():
 
     if rank == 0:
         peak, src = peaks()
-        abytes = algorithmic_bytes(n, T, spikes, events)
+        abytes = algorithmic_bytes_pull(n, m, T) if pull else algorithmic_bytes(n, T, spikes, events)
         achieved = abytes / (ms / 1e3) / 1e9
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "large-sparse", "neurons": n, "synapses": int(len(wl["pre"])),
+            "config": {"workload": "large-sparse", "neurons": n, "synapses": m,
                        "max_delay": 16, "timesteps_per_step": T, "input": "Poisson 0.05/step into 1000 neurons",
+                       "propagation": "pull" if pull else "push",
                        "l2": "256 MiB buffer written before every timed run (L2 flushed)",
                        "parallelism": "replicas" if world > 1 else "single"},
             "timesteps_per_s": world * T / (ms_all / 1e3),
@@ -508,7 +523,8 @@ def main():
             "wall_ms_per_step": 1e3 * wall / args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": src,
-                         "traffic": NCU_TRAFFIC_BYTES, "kernel": "sparse_reg_kernel<SN_F32>",
+                         "traffic": NCU_TRAFFIC_BYTES,
+                         "kernel": "sparse_pull_kernel<SN_F32>" if pull else "sparse_reg_kernel<SN_F32>",
                          "algorithmic_bytes_per_launch": abytes},
             "e2e": {"value": e2e_ev_all / e2e_all, "unit": UNIT,
                     "h2d_bytes_per_step": 8 * n,
@@ -517,7 +533,19 @@ def main():
             "clocks": clk.summary(),
         }
         if not args.no_extras and world == 1:
-            line["extra"] = extras(S, W, torch, stream, flush)
+            other = S.SN_PUSH if pull else S.SN_PULL
+            try:
+                S.sn_set_propagation(ctx, other)
+                o_ms, o_spk, o_ev = timed_runs(S, torch, stream, flush, ctx, T, 3)
+                o_bytes = algorithmic_bytes(n, T, o_spk, o_ev) if pull else algorithmic_bytes_pull(n, m, T)
+                alt = {"propagation": "push" if pull else "pull", "ms_per_step": o_ms,
+                       "value": o_ev / (o_ms / 1e3), "unit": UNIT,
+                       "kernel": "sparse_reg_kernel<SN_F32>" if pull else "sparse_pull_kernel<SN_F32>",
+                       "roofline_frac": o_bytes / (o_ms / 1e3) / 1e9 / peak}
+            except S.SnError as e:
+                alt = {"unavailable": str(e)}
+            line["extra"] = {"large_sparse_other_propagation": alt}
+            line["extra"].update(extras(S, W, torch, stream, flush))
         if not args.no_cpu_baseline:
             ev_s, ts_s, sample = oracle_sample(wl)
             line["cpu_baseline"] = {"value": ev_s, "unit": UNIT, "cores": 1, "kind": "oracle",

@@ -65,9 +65,11 @@ typedef enum {
 
 /* Arithmetic of the membrane state. */
 typedef enum {
-    SN_F32 = 0,  /* float state; synaptic sums are exact fixed-point (2^-32)
-                    accumulations rounded once to float, so results do not
-                    depend on thread timing                                  */
+    SN_F32 = 0,  /* float state.  Push propagation sums the synaptic input
+                    exactly in fixed point (2^-32) and rounds it once to
+                    float; pull propagation adds the weights in float in
+                    ascending (delay, pre, input index) order.  Neither
+                    depends on thread timing.                                */
     SN_I32 = 1   /* exact integer state; parameters and weights must be
                     integral (checked)                                       */
 } sn_dtype;
@@ -76,13 +78,17 @@ typedef enum {
 #define SN_AUTO 0u          /* the library picks the executor                      */
 #define SN_EXEC_CTA 1u      /* force the one-block executor (small networks)       */
 #define SN_EXEC_GRID 2u     /* force the grid-wide persistent executor             */
+#define SN_PROP_PULL 4u     /* sn_create only: start with pull propagation (see
+                               sn_set_propagation); SN_EUNSUPPORTED if the
+                               network does not fit it                             */
 
 #define SN_MAX_DELAY 64     /* largest supported synaptic delay                    */
 
 typedef struct {
     int32_t dtype;          /* sn_dtype                                            */
     int32_t max_delay;      /* D: every synaptic delay lies in 1..D, D <= 64       */
-    uint32_t flags;         /* SN_AUTO or one SN_EXEC_* value                      */
+    uint32_t flags;         /* SN_AUTO or one SN_EXEC_* value, optionally with
+                               SN_PROP_PULL                                        */
     int32_t record_steps;   /* spike-raster capacity in steps (a ring); sn_get_spikes
                                can return any of the last record_steps steps; 0
                                means 1                                              */
@@ -169,7 +175,9 @@ sn_status sn_batch_config(sn_ctx *ctx, int32_t warp_max_n, int32_t ring_smem_byt
 /* Time every mapping of a fixed candidate set on `trial_steps` steps of the
  * context's own networks and inputs, keep the fastest, then reset the
  * dynamic state (as sn_reset).  *best_ms (may be NULL) receives the time of
- * the chosen mapping.  Batched contexts only. */
+ * the chosen mapping.  Batched contexts: the warp/block split and the
+ * shared-memory ring size.  Sparse contexts (sn_create): push or pull
+ * propagation (pull only where it fits, never with STDP on). */
 sn_status sn_autotune(sn_ctx *ctx, int32_t trial_steps, float *best_ms);
 
 /* Replace the explicit external input (Section 2.1, third step of a
@@ -207,6 +215,24 @@ sn_status sn_set_poisson_stream(sn_ctx *ctx, int32_t nsrc, const int32_t *neuron
  * used from step t + 1.  Supported for SN_F32 networks (sparse and dense). */
 sn_status sn_stdp(sn_ctx *ctx, float decay, float a_plus, float a_minus,
                   float wmin, float wmax, int32_t enable);
+
+/* Propagation of a sparse network (sn_create), SN_PUSH or SN_PULL.
+ *   push: each spike of step t adds its weights to the pending input of its
+ *     targets for steps t + d (event-driven; work grows with the spike count).
+ *   pull: each neuron sums, over its incoming synapses in ascending (delay,
+ *     pre, input index) order, the weights whose pre-neuron spiked at t - d
+ *     (Section 2.1's "spikes of the previous step times the weights", with
+ *     delays); work is the synapse count every step, independent of activity.
+ *     In SN_F32 mode this is exactly the FP32 mirror's order of additions.
+ *     It needs max_delay * ceil(n/32) * 4 bytes of spike history in one
+ *     block's shared memory (about 220 KiB) and n <= 1024 per SM; otherwise,
+ *     or with STDP on, SN_EUNSUPPORTED.
+ * The mode may change between any two sn_run calls: input already pending is
+ * carried over exactly.  Enabling STDP selects push. */
+#define SN_PUSH 0
+#define SN_PULL 1
+sn_status sn_set_propagation(sn_ctx *ctx, int32_t mode);
+sn_status sn_get_propagation(const sn_ctx *ctx, int32_t *mode);
 
 /* Advance `steps` timesteps (steps >= 0) from the current step.  Queued on the
  * context's stream; a step counter makes repeated calls continue the run. */
@@ -249,7 +275,8 @@ sn_status sn_get_counters(sn_ctx *ctx, int64_t *steps, int64_t *spikes, int64_t 
 
 /* Checkpoint: sn_save with buf == NULL stores the needed size in *size;
  * otherwise it writes the full dynamic state (step counter, V, refractory
- * countdowns, pending synaptic input, STDP traces, weights, counters) into
+ * countdowns, pending synaptic input and the recent spikes whose deliveries
+ * are due, STDP traces, weights, counters) into
  * buf.  sn_load restores it into a context created with the same network.
  * A run of T steps equals a run of T1 steps, save, load into a fresh
  * context, and a run of T - T1 steps. */

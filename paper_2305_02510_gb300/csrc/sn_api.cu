@@ -29,7 +29,7 @@ sn_status check_config(const sn_config *cfg) {
     if (cfg->max_delay < 1 || cfg->max_delay > SN_MAX_DELAY)
         return fail(nullptr, SN_EINVAL, "max_delay must be in 1..64");
     if (cfg->record_steps < 0) return fail(nullptr, SN_EINVAL, "record_steps < 0");
-    if (cfg->flags & ~(SN_EXEC_CTA | SN_EXEC_GRID)) return fail(nullptr, SN_EINVAL, "unknown flags");
+    if (cfg->flags & ~(SN_EXEC_CTA | SN_EXEC_GRID | SN_PROP_PULL)) return fail(nullptr, SN_EINVAL, "unknown flags");
     if ((cfg->flags & SN_EXEC_CTA) && (cfg->flags & SN_EXEC_GRID))
         return fail(nullptr, SN_EINVAL, "SN_EXEC_CTA and SN_EXEC_GRID are exclusive");
     return SN_OK;
@@ -68,6 +68,86 @@ sn_status size_sparse_executor(sn_ctx *c) {
     if (chunk > 1024) return fail(nullptr, SN_EUNSUPPORTED, "network too large for the grid executor");
     c->chunk = chunk;
     c->grid = (n + chunk - 1) / chunk;
+    return SN_OK;
+}
+
+// Incoming synapses of every neuron in ascending (delay, pre, input index)
+// order, laid out for the pull kernel: the neurons 32s .. 32s+31 form slice s;
+// entry q of neuron 32s + l is half q % 2 of uint4 number
+// pin_off[s] + (q / 2) * 32 + l, as {((D - d) * Wp + pre / 32) << 7 | pre % 32,
+// weight bits}; unused halves stay all-zero.  Built from the CSR, whose rows
+// keep the input order, so ties of (delay, pre) stay in input order.
+sn_status build_pull_store(sn_ctx *c) {
+    const int n = c->n;
+    const long long m = c->m;
+    if (m >= (1ll << 32)) return fail(c, SN_EUNSUPPORTED, "pull propagation supports m < 2^32");
+    std::vector<uint2> syn(m > 0 ? m : 1);
+    std::vector<long long> rowptr(n + 1);
+    SN_CUDA(c, cudaMemcpy(syn.data(), c->syn, (size_t)(m > 0 ? m : 1) * 8, cudaMemcpyDeviceToHost));
+    SN_CUDA(c, cudaMemcpy(rowptr.data(), c->rowptr, (size_t)(n + 1) * 8, cudaMemcpyDeviceToHost));
+    // CSR positions bucketed by delay, stable (pre ascending, input order)
+    std::vector<long long> dstart(c->D + 2, 0);
+    for (long long p = 0; p < m; ++p) dstart[(syn[p].x >> kPostBits) + 1]++;
+    for (int d = 0; d <= c->D; ++d) dstart[d + 1] += dstart[d];
+    std::vector<uint32_t> byd(m > 0 ? m : 1), pre_of(m > 0 ? m : 1);
+    std::vector<int> len(n, 0);
+    for (int i = 0; i < n; ++i)
+        for (long long p = rowptr[i]; p < rowptr[i + 1]; ++p) {
+            byd[dstart[syn[p].x >> kPostBits]++] = (uint32_t)p;
+            pre_of[p] = (uint32_t)i;
+            len[syn[p].x & kPostMask]++;
+        }
+    const int slices = (n + 31) / 32;
+    std::vector<long long> off(slices);
+    long long total = 0;
+    for (int sl = 0; sl < slices; ++sl) {
+        int L = 0;
+        for (int j = sl * 32; j < std::min(n, sl * 32 + 32); ++j) L = std::max(L, len[j]);
+        off[sl] = total;
+        total += (long long)((L + 1) / 2) * 32;
+    }
+    std::vector<uint4> pin(total > 0 ? total : 1, make_uint4(0, 0, 0, 0));
+    const unsigned wp = (unsigned)((c->words + 3) & ~3);   // window row stride of the pull kernel
+    std::vector<int> fill(n, 0);
+    for (long long k = 0; k < m; ++k) {
+        const uint32_t p = byd[k];
+        const int j = (int)(syn[p].x & kPostMask);
+        const int q = fill[j]++;
+        uint4 &u = pin[off[j >> 5] + (long long)(q >> 1) * 32 + (j & 31)];
+        const unsigned pre = pre_of[p], d = (syn[p].x >> kPostBits) + 1;
+        const unsigned x = (((unsigned)(c->D - d) * wp + (pre >> 5)) << 7) | (pre & 31u);
+        if (q & 1) { u.z = x; u.w = syn[p].y; } else { u.x = x; u.y = syn[p].y; }
+    }
+    sn_status s;
+    if (!c->pin) {
+        if ((s = dalloc(c, &c->pin, (size_t)(total > 0 ? total : 1) * 16)) ||
+            (s = dalloc(c, &c->pin_off, (size_t)slices * 8)) || (s = dalloc(c, &c->pin_len, (size_t)n * 4)))
+            return s;
+    }
+    SN_CUDA(c, cudaMemcpy(c->pin, pin.data(), (size_t)(total > 0 ? total : 1) * 16, cudaMemcpyHostToDevice));
+    SN_CUDA(c, cudaMemcpy(c->pin_off, off.data(), (size_t)slices * 8, cudaMemcpyHostToDevice));
+    SN_CUDA(c, cudaMemcpy(c->pin_len, len.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
+    c->pin_stale = false;
+    return SN_OK;
+}
+
+sn_status select_pull(sn_ctx *c) {
+    if (c->stdp) return fail(c, SN_EUNSUPPORTED, "STDP runs on push propagation");
+    if (c->pull_grid == 0) {
+        cudaError_t e = plan_pull(c->n, c->D, &c->pull_grid, &c->pull_chunk, &c->pull_rows, &c->pull_smem);
+        if (e != cudaSuccess) return cuda_fail(c, e, "pull executor");
+        if (c->pull_grid == 0)
+            return fail(c, SN_EUNSUPPORTED,
+                        "pull propagation needs max_delay * ceil(n/32) spike words within a block's shared "
+                        "memory and at most 1024 neurons per SM");
+    }
+    sn_status s;
+    if (!c->hist) {
+        if ((s = dalloc(c, &c->hist, (size_t)c->D * c->words * 4))) return s;
+        SN_CUDA(c, cudaMemset(c->hist, 0, (size_t)c->D * c->words * 4));
+    }
+    if (c->pin_stale && (s = build_pull_store(c))) return s;
+    c->prop_pull = 1;
     return SN_OK;
 }
 
@@ -212,6 +292,7 @@ sn_status sn_create(const sn_config *cfg, const sn_neurons *nr, const sn_synapse
         return bail(SN_ECUDA);
     }
     if ((s = size_sparse_executor(c))) return bail(s);
+    if ((cfg->flags & SN_PROP_PULL) && (s = select_pull(c))) return bail(s);
     *out = c;
     return SN_OK;
 }
@@ -222,6 +303,7 @@ sn_status sn_create_dense(const sn_config *cfg, const sn_neurons *nr, const floa
     if (s) return s;
     if (!nr || !w || !out) return fail(nullptr, SN_EINVAL, "NULL argument");
     if (cfg->dtype != SN_F32) return fail(nullptr, SN_EUNSUPPORTED, "dense networks are SN_F32 only");
+    if (cfg->flags & SN_PROP_PULL) return fail(nullptr, SN_EUNSUPPORTED, "SN_PROP_PULL applies to sn_create networks");
     const int n = nr->n;
     if (n < 1 || n > 200000) return fail(nullptr, SN_EINVAL, "dense n must be in 1 .. 200000");
     if (delay < 1 || delay > cfg->max_delay) return fail(nullptr, SN_EINVAL, "delay outside 1..max_delay");
@@ -408,6 +490,7 @@ sn_status sn_stdp(sn_ctx *c, float decay, float a_plus, float a_minus, float wmi
         SN_CUDA(c, cudaMemcpy(c->csc, csc.data(), (size_t)(m > 0 ? m : 1) * 8, cudaMemcpyHostToDevice));
     }
     c->stdp = 1;
+    c->prop_pull = 0;                  // STDP rewrites the CSR weights: push propagation
     c->decay = decay; c->a_plus = a_plus; c->a_minus = a_minus; c->wmin = wmin; c->wmax = wmax;
     return SN_OK;
 }
@@ -452,15 +535,39 @@ sn_status sn_run(sn_ctx *c, int32_t steps) {
     a.stdp = c->stdp; a.decay = c->decay; a.a_plus = c->a_plus; a.a_minus = c->a_minus;
     a.wmin = c->wmin; a.wmax = c->wmax; a.trace = c->trace;
     a.ctl = c->ctl;
+    a.hist = c->hist; a.hD = c->D;
     cudaError_t e;
-    if (c->kind == KIND_SPARSE && !c->stdp && c->reg_grid > 0) {
-        a.chunk = c->reg_chunk;
-        e = launch_sparse_reg(a, c->dtype, c->reg_grid, c->stream);
+    if (c->kind == KIND_SPARSE && c->prop_pull && !c->stdp) {
+        if (c->pin_stale) {
+            sn_status st = build_pull_store(c);
+            if (st) return st;
+        }
+        a.pin = c->pin; a.pin_off = c->pin_off; a.pin_len = c->pin_len;
+        a.ring_until = (int)std::min<long long>(c->ring_live_until, 2147483647ll);
+        a.hL = c->pull_rows;
+        a.chunk = c->pull_chunk;
+        e = launch_sparse_pull(a, c->dtype, c->pull_grid, c->pull_smem, c->stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "simulation launch");
+        c->hist_live = true;
     } else {
-        e = c->kind == KIND_SPARSE ? launch_sparse(a, c->dtype, c->grid, c->block, c->stream)
-                                   : launch_dense(a, c->grid, c->block, c->stream);
+        if (c->kind == KIND_SPARSE && c->hist_live) {
+            // spikes of a pull run whose deliveries are still due go to the ring
+            if ((e = launch_pull_flush(a, c->dtype, (int)c->step, c->stream)) != cudaSuccess ||
+                (e = cudaMemsetAsync(c->hist, 0, (size_t)c->D * c->words * 4, c->stream)) != cudaSuccess)
+                return cuda_fail(c, e, "pull-to-push handover");
+            c->hist_live = false;
+        }
+        if (c->kind == KIND_SPARSE && !c->stdp && c->reg_grid > 0) {
+            a.chunk = c->reg_chunk;
+            e = launch_sparse_reg(a, c->dtype, c->reg_grid, c->stream);
+        } else {
+            e = c->kind == KIND_SPARSE ? launch_sparse(a, c->dtype, c->grid, c->block, c->stream)
+                                       : launch_dense(a, c->grid, c->block, c->stream);
+        }
+        if (e != cudaSuccess) return cuda_fail(c, e, "simulation launch");
+        c->ring_live_until = c->step + steps + c->D;
+        if (c->stdp) c->pin_stale = true;
     }
-    if (e != cudaSuccess) return cuda_fail(c, e, "simulation launch");
     c->step += steps;
     if (c->step - c->raster_from > c->cap) c->raster_from = c->step - c->cap;
     return SN_OK;
@@ -489,6 +596,9 @@ sn_status sn_reset(sn_ctx *c) {
     SN_CUDA(c, cudaMemsetAsync(c->ring, 0, c->ring_bytes, c->stream));
     if (c->spk) SN_CUDA(c, cudaMemsetAsync(c->spk, 0, (size_t)2 * c->words * 4, c->stream));
     if (c->trace) SN_CUDA(c, cudaMemsetAsync(c->trace, 0, 3 * vb, c->stream));
+    if (c->hist) SN_CUDA(c, cudaMemsetAsync(c->hist, 0, (size_t)c->D * c->words * 4, c->stream));
+    c->hist_live = false;
+    c->ring_live_until = 0;
     SN_CUDA(c, cudaMemsetAsync(c->raster, 0, (size_t)c->cap * c->words * 4, c->stream));
     SN_CUDA(c, cudaMemsetAsync(c->ctl, 0, sizeof(Control), c->stream));
     c->step = 0;
@@ -599,26 +709,29 @@ sn_status sn_get_counters(sn_ctx *c, int64_t *steps, int64_t *spikes, int64_t *e
 }
 
 // Checkpoint layout: header, V, r, ring, spike bits (dense), trace (if any),
-// weights (sparse CSR words or dense W), counters.
+// weights (sparse CSR words or dense W), spike history of a pull run (if its
+// deliveries may be due), counters in the header.
 struct SaveHeader {
     char magic[8];
-    int kind, dtype, n, D1, S, has_trace;
+    int kind, dtype, n, D1, S, has_trace, has_hist, pad;
     long long m, step;
     unsigned long long spikes, events;
 };
 
-static size_t save_size(const sn_ctx *c) {
+static size_t save_size(const sn_ctx *c, bool has_trace, bool has_hist) {
     size_t s = sizeof(SaveHeader) + (size_t)c->n * 8 + c->ring_bytes;
     if (c->kind == KIND_DENSE) s += (size_t)2 * c->words * 4 + (size_t)c->n * c->n * 4;
     else s += (size_t)(c->m > 0 ? c->m : 0) * 8;
-    if (c->trace) s += (size_t)3 * c->n * 4;
+    if (has_trace) s += (size_t)3 * c->n * 4;
+    if (has_hist) s += (size_t)c->D * c->words * 4;
     return s;
 }
 
 sn_status sn_save(sn_ctx *c, void *buf, size_t *size) {
     if (!c || !size) return fail(c, SN_EINVAL, "NULL argument");
     if (c->kind != KIND_SPARSE && c->kind != KIND_DENSE) return fail(c, SN_ESTATE, "wrong context kind");
-    const size_t need = save_size(c);
+    const bool has_hist = c->kind == KIND_SPARSE && c->hist_live;
+    const size_t need = save_size(c, c->trace != nullptr, has_hist);
     if (!buf) { *size = need; return SN_OK; }
     if (*size < need) return fail(c, SN_EINVAL, "buffer too small");
     SN_CUDA(c, cudaStreamSynchronize(c->stream));
@@ -628,9 +741,9 @@ sn_status sn_save(sn_ctx *c, void *buf, size_t *size) {
     SN_CUDA(c, cudaMemcpy(&h, c->ctl, sizeof(Control), cudaMemcpyDeviceToHost));
     SaveHeader hd;
     memset(&hd, 0, sizeof(hd));
-    memcpy(hd.magic, "SNCKPT1", 8);
+    memcpy(hd.magic, "SNCKPT2", 8);
     hd.kind = c->kind; hd.dtype = c->dtype; hd.n = c->n; hd.D1 = c->D1; hd.S = c->S;
-    hd.has_trace = c->trace != nullptr; hd.m = c->m; hd.step = c->step;
+    hd.has_trace = c->trace != nullptr; hd.has_hist = has_hist; hd.m = c->m; hd.step = c->step;
     hd.spikes = h.spikes; hd.events = h.events;
     uint8_t *p = (uint8_t *)buf;
     memcpy(p, &hd, sizeof(hd)); p += sizeof(hd);
@@ -649,6 +762,7 @@ sn_status sn_save(sn_ctx *c, void *buf, size_t *size) {
         return cuda_fail(c, e, "save");
     }
     if (c->trace && (e = get(c->trace, (size_t)3 * c->n * 4))) return cuda_fail(c, e, "save");
+    if (has_hist && (e = get(c->hist, (size_t)c->D * c->words * 4))) return cuda_fail(c, e, "save");
     *size = need;
     return SN_OK;
 }
@@ -658,15 +772,14 @@ sn_status sn_load(sn_ctx *c, const void *buf, size_t size) {
     if (size < sizeof(SaveHeader)) return fail(c, SN_EINVAL, "buffer too small");
     SaveHeader hd;
     memcpy(&hd, buf, sizeof(hd));
-    if (memcmp(hd.magic, "SNCKPT1", 8) != 0) return fail(c, SN_EINVAL, "not a checkpoint");
+    if (memcmp(hd.magic, "SNCKPT2", 8) != 0) return fail(c, SN_EINVAL, "not a checkpoint");
     if (hd.kind != c->kind || hd.dtype != c->dtype || hd.n != c->n || hd.D1 != c->D1 || hd.m != c->m ||
-        hd.S != c->S)
+        hd.S != c->S || (hd.has_hist && c->kind != KIND_SPARSE))
         return fail(c, SN_EINVAL, "checkpoint is of a different network");
-    if (hd.has_trace && !c->trace) {
-        sn_status s = dalloc(c, &c->trace, (size_t)3 * c->n * 4);
-        if (s) return s;
-    }
-    if (size < save_size(c)) return fail(c, SN_EINVAL, "checkpoint truncated");
+    if (size < save_size(c, hd.has_trace != 0, hd.has_hist != 0)) return fail(c, SN_EINVAL, "checkpoint truncated");
+    sn_status s;
+    if (hd.has_trace && !c->trace && (s = dalloc(c, &c->trace, (size_t)3 * c->n * 4))) return s;
+    if (hd.has_hist && !c->hist && (s = dalloc(c, &c->hist, (size_t)c->D * c->words * 4))) return s;
     SN_CUDA(c, cudaStreamSynchronize(c->stream));
     const uint8_t *p = (const uint8_t *)buf + sizeof(hd);
     auto put = [&](void *dst, size_t bytes) -> cudaError_t {
@@ -684,6 +797,16 @@ sn_status sn_load(sn_ctx *c, const void *buf, size_t size) {
         return cuda_fail(c, e, "load");
     }
     if (hd.has_trace && (e = put(c->trace, (size_t)3 * c->n * 4))) return cuda_fail(c, e, "load");
+    if (hd.has_hist) {
+        if ((e = put(c->hist, (size_t)c->D * c->words * 4))) return cuda_fail(c, e, "load");
+    } else if (c->hist) {
+        SN_CUDA(c, cudaMemset(c->hist, 0, (size_t)c->D * c->words * 4));
+    }
+    if (c->kind == KIND_SPARSE) {
+        c->hist_live = hd.has_hist != 0;
+        c->ring_live_until = hd.step + c->D;   // the loaded ring may hold pending input
+        c->pin_stale = true;                   // the loaded weights replace the CSR's
+    }
     Control h;
     memset(&h, 0, sizeof(h));
     h.spikes = hd.spikes;
@@ -692,6 +815,22 @@ sn_status sn_load(sn_ctx *c, const void *buf, size_t size) {
     c->step = hd.step;
     c->raster_from = hd.step;
     c->failed = 0;
+    return SN_OK;
+}
+
+// Propagation of a sparse network: push (SN_PUSH, every spike adds its
+// weights to the pending input of its targets) or pull (SN_PULL).
+sn_status sn_set_propagation(sn_ctx *c, int32_t mode) {
+    if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
+    if (c->kind != KIND_SPARSE) return fail(c, SN_EUNSUPPORTED, "propagation mode: sparse single networks only");
+    if (mode == SN_PUSH) { c->prop_pull = 0; return SN_OK; }
+    if (mode != SN_PULL) return fail(c, SN_EINVAL, "mode must be SN_PUSH or SN_PULL");
+    return select_pull(c);
+}
+
+sn_status sn_get_propagation(const sn_ctx *c, int32_t *mode) {
+    if (!c || !mode) return SN_EINVAL;
+    *mode = (c->kind == KIND_SPARSE && c->prop_pull && !c->stdp) ? SN_PULL : SN_PUSH;
     return SN_OK;
 }
 
@@ -705,3 +844,44 @@ void sn_destroy(sn_ctx *c) {
 }
 
 }  // extern "C"
+
+namespace sn {
+
+// sn_autotune on a sparse network: time push and (where the network fits it)
+// pull propagation on trial_steps steps from the initial state, keep the
+// faster, reset.  The second of two runs of each is timed (the first also
+// pays first-launch costs).
+sn_status sparse_autotune(sn_ctx *c, int trial_steps, float *best_ms) {
+    cudaEvent_t e0, e1;
+    SN_CUDA(c, cudaEventCreate(&e0));
+    SN_CUDA(c, cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_pull = 0;
+    sn_status st = SN_OK;
+    for (int pull = 0; pull < 2 && st == SN_OK; ++pull) {
+        if (pull) {
+            if (c->stdp || select_pull(c) != SN_OK) { c->err.clear(); break; }
+        } else {
+            c->prop_pull = 0;
+        }
+        float ms = 0.0f;
+        for (int rep = 0; rep < 2 && st == SN_OK; ++rep) {
+            if ((st = sn_reset(c))) break;
+            cudaEventRecord(e0, c->stream);
+            if ((st = sn_run(c, trial_steps))) break;
+            cudaEventRecord(e1, c->stream);
+            if ((st = sn_sync(c))) break;
+            cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (st == SN_OK && ms < best) { best = ms; best_pull = pull; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st) return st;
+    c->prop_pull = best_pull;
+    if ((st = sn_reset(c))) return st;
+    if (best_ms) *best_ms = best;
+    return sn_sync(c);
+}
+
+}  // namespace sn

@@ -256,9 +256,11 @@ sn_status sn_create_batch(const sn_config *cfg, int32_t nets, const sn_neurons *
 
 sn_status sn_autotune(sn_ctx *c, int32_t trial_steps, float *best_ms) {
     if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
-    if (c->kind != KIND_BATCH) return fail(c, SN_EUNSUPPORTED, "autotuning applies to batched contexts");
+    if (c->kind != KIND_BATCH && c->kind != KIND_SPARSE)
+        return fail(c, SN_EUNSUPPORTED, "autotuning applies to batched and sparse contexts");
     if (c->failed) return fail(c, SN_ESTATE, "context has a latched device error");
     if (trial_steps < 1) return fail(c, SN_EINVAL, "trial_steps must be >= 1");
+    if (c->kind == KIND_SPARSE) return sparse_autotune(c, trial_steps, best_ms);
     const int warp_opts[] = {0, 64, 128, 256, 512};
     const int smem_opts[] = {32 * 1024, 64 * 1024, 112 * 1024, 176 * 1024};
     cudaEvent_t e0, e1;

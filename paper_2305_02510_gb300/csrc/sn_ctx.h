@@ -30,6 +30,17 @@ struct sn_ctx {
     // executor
     int grid = 1, block = 256, chunk = 32, S = 1;
     int reg_grid = 0, reg_chunk = 0;   // register-resident sparse executor (0: not usable)
+    // pull propagation of sparse networks (sn_pull.cu)
+    int prop_pull = 0;                 // 1: sparse runs use pull propagation
+    int pull_grid = 0, pull_chunk = 0, pull_rows = 0;
+    size_t pull_smem = 0;
+    uint4 *pin = nullptr;              // incoming synapses in 32-neuron slices
+    long long *pin_off = nullptr;
+    int *pin_len = nullptr;
+    bool pin_stale = true;             // the pull store must be (re)built from the CSR
+    unsigned *hist = nullptr;          // [D][words] spike bits whose deliveries may be due
+    bool hist_live = false;            // hist may hold spikes not yet delivered
+    long long ring_live_until = 0;     // the ring may hold pending input for steps before this
     // device memory
     void *V = nullptr;
     int *r = nullptr;
@@ -154,6 +165,7 @@ sn_status upload_neurons(sn_ctx *c, const sn_neurons *nr);
 sn_status alloc_common(sn_ctx *c, const sn_config *cfg);
 void destroy_all(sn_ctx *c);
 sn_status batch_run(sn_ctx *c, int steps);
+sn_status sparse_autotune(sn_ctx *c, int trial_steps, float *best_ms);
 sn_status shared_run(sn_ctx *c, int steps);
 sn_status shared_set_poisson(sn_ctx *c, int32_t nsrc, const int32_t *neuron, const float *rate,
                              const float *amp, uint64_t seed);

@@ -63,6 +63,15 @@ struct NetArgs {
     const long long *colptr;          // CSC by post (STDP only)
     const uint2 *csc;                 // {pre, CSR position}
     void *ring;                       // [D1][n] pending input (int64 fixed point / int32 / float)
+    // sparse store for pull propagation (sn_pull.cu): incoming synapses of
+    // 32-neuron slices, pairs {pre | (delay-1) << 26, weight bits} x 2
+    const uint4 *pin;
+    const long long *pin_off;         // [slices] first uint4 of each slice
+    const int *pin_len;               // [n] incoming synapses of each neuron
+    unsigned *hist;                   // [hD][words] spike bits of step tau in row tau % hD
+    int hD;                           // history depth (the maximum delay D)
+    int hL;                           // rows of the pull kernel's shared-memory window
+    int ring_until;                   // the ring may hold pending input for steps < ring_until
     // dense store
     float *W;                         // [n][n]
     float *partial;                   // [S][n] gather partial sums
@@ -155,6 +164,14 @@ cudaError_t max_grid_sparse_reg(int *grid);
 cudaError_t launch_sparse_reg(const NetArgs &a, int dtype, int grid, cudaStream_t s);
 constexpr int kSparseRegBlock = 512;
 cudaError_t plan_dense(int n, int *grid, int *chunk);
+// Pull propagation (sn_pull.cu).  plan_pull sets *grid = 0 when the network
+// does not fit the executor (a window of max_delay spike rows above a block's
+// shared memory, or more than one neuron per thread).  Synapse words of the
+// pull store: x = ((D - d) * Wp + pre / 32) << 7 | (pre & 31),
+// Wp = roundup(ceil(n/32), 4).
+cudaError_t plan_pull(int n, int D, int *grid, int *chunk, int *rows, size_t *smem);
+cudaError_t launch_sparse_pull(const NetArgs &a, int dtype, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_pull_flush(const NetArgs &a, int dtype, int t0, cudaStream_t s);
 cudaError_t launch_gather_weights(const uint2 *syn, const long long *perm_inv, long long m,
                                   float *out, cudaStream_t s);
 

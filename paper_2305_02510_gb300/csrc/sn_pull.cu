@@ -1,0 +1,354 @@
+// Pull propagation for sparse networks (Section 2.1, second step of a
+// timestep: the input of neuron j is the sum over its incoming synapses of
+// w * s_i(t - d); Section 2.2: a spike reaches the post-neuron d steps later).
+//
+// Every block keeps the spike bits of recent steps in a shared-memory window
+// of hL rows of Wp = roundup(ceil(n/32), 4) words: the row of step tau sits
+// at position tau - base.  Each thread owns one neuron, holds its state in
+// registers and walks the neuron's incoming synapses in ascending (delay,
+// pre, input index) order, testing the bit of pre at step t - d and adding
+// the weight.  A synapse is stored as x = e << 7 | (pre & 31) with
+// e = (D - d) * Wp + pre / 32, the word offset of its bit from the row of step
+// t - D, so that a test is one shift, one shared load and one funnel shift.
+// The synapses of 32 consecutive neurons form a slice (one warp): entry q of
+// lane l sits in pair q / 2 of the slice, so that each 16-byte load of a warp
+// reads 512 contiguous bytes.  Unused halves of a pair are all-zero entries,
+// which add +0 (an exact no-op: the sum starts at +0 and is never -0).  In
+// SN_F32 mode the sum is a float accumulation in that order, the FP32
+// mirror's order, so the state does not depend on thread timing and matches
+// the mirror bit for bit.
+//
+// One grid barrier per step, split: a block arrives once its spike words of
+// step t are in the global history, then (while the other blocks finish)
+// compacts its window when the next row would fall off its end and loads
+// the first synapses of step t + 1; after the wait it copies row t into the
+// window.  The global history (row of step tau in slot tau % D) holds, between
+// runs, every spike of the last D steps whose deliveries are still due;
+// pull_flush_kernel turns them into pending ring input when the context
+// switches to push propagation.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "sn_device.cuh"
+
+namespace sn {
+namespace {
+
+constexpr int kPullUnroll = 4;      // 16-byte loads (two synapses each) per half of the double buffer
+constexpr int kPullMaxBlock = 1024;
+
+template <int MODE> struct PullAcc;
+template <> struct PullAcc<SN_F32> {
+    using T = float;
+    static __device__ __forceinline__ T add(T acc, unsigned wbits) { return __fadd_rn(acc, __uint_as_float(wbits)); }
+};
+template <> struct PullAcc<SN_I32> {
+    using T = long long;            // exact: int32 weights, at most 2^32 synapses
+    static __device__ __forceinline__ T add(T acc, unsigned wbits) { return acc + (long long)(int)wbits; }
+};
+
+// One synapse: the bit of its pre-neuron at step t - d, from the window whose
+// first row (step t - D) starts at byte `row0` of shared memory.
+template <int MODE>
+__device__ __forceinline__ void pull_one(typename PullAcc<MODE>::T &acc, unsigned x, unsigned wbits,
+                                         const unsigned char *win, unsigned row0) {
+    const unsigned word = *(const unsigned *)(win + row0 + (x >> 5));
+    if (__funnelshift_r(word, word, x) & 1u) acc = PullAcc<MODE>::add(acc, wbits);
+}
+
+template <int MODE>
+__device__ __forceinline__ void pull_batch(typename PullAcc<MODE>::T &acc, const uint4 (&e)[kPullUnroll],
+                                           const unsigned char *win, unsigned row0) {
+#pragma unroll
+    for (int u = 0; u < kPullUnroll; ++u) {
+        pull_one<MODE>(acc, e[u].x, e[u].y, win, row0);
+        pull_one<MODE>(acc, e[u].z, e[u].w, win, row0);
+    }
+}
+
+__device__ __forceinline__ void pull_load(uint4 (&e)[kPullUnroll], const uint4 *ent, int p0, int np) {
+#pragma unroll
+    for (int u = 0; u < kPullUnroll; ++u)
+        e[u] = p0 + u < np ? __ldg(ent + (size_t)(p0 + u) * 32) : make_uint4(0u, 0u, 0u, 0u);
+}
+
+// Thread 0 of each block: arrive at the grid barrier, returning the
+// generation to wait for.
+__device__ __forceinline__ unsigned bar_arrive(Control *ctl) {
+    GridBarrier *b = &ctl->bar;
+    const unsigned gen = ld_acquire_u32(&b->gen);
+    __threadfence();
+    const unsigned arrived = atomicAdd(&b->count, 1u);
+    if (arrived == gridDim.x - 1) {
+        atomicExch(&b->count, 0u);
+        __threadfence();
+        atomicAdd(&b->gen, 1u);
+    }
+    return gen;
+}
+
+// Thread 0: wait until the generation moves on (bounded: wall-clock limit,
+// or a status latched by another block).  Returns false if it gave up.
+__device__ __forceinline__ bool bar_wait(Control *ctl, unsigned gen) {
+    const unsigned long long t_start = global_timer_ns();
+    unsigned spins = 0;
+    while (ld_acquire_u32(&ctl->bar.gen) == gen) {
+        if ((++spins & 63u) == 0) {
+            if (ld_status(ctl) != 0) return false;
+            if (global_timer_ns() - t_start > kBarrierTimeoutNs) {
+                atomicCAS(&ctl->status, 0, (int)SN_ETIMEOUT);
+                return false;
+            }
+        }
+        __nanosleep(32);
+    }
+    __threadfence();
+    return true;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kPullMaxBlock, 1) sparse_pull_kernel(NetArgs a) {
+    using V = typename Tr<MODE>::V;
+    using Acc = typename PullAcc<MODE>::T;
+    extern __shared__ uint4 s_win4[];                 // [hL][Wp] words
+    unsigned *s_win = (unsigned *)s_win4;
+    const unsigned char *win = (const unsigned char *)s_win4;
+    __shared__ int s_ok, s_stop;
+    const int D = a.hD, W = a.words, Wp = (a.words + 3) & ~3, L = a.hL;
+    const int lane = threadIdx.x & 31;
+    int base = a.t0 - D;                              // step of window row 0
+    for (int i = threadIdx.x; i < D * Wp; i += blockDim.x) {
+        const int tau = base + i / Wp, w = i % Wp;
+        s_win[i] = (tau >= 0 && w < W) ? __ldcg(a.hist + (size_t)(tau % D) * W + w) : 0u;
+    }
+
+    const int j = blockIdx.x * a.chunk + threadIdx.x;
+    const bool mine = j < a.n;
+    const int wbase = j - lane;                       // first neuron of this warp's slice
+    V v = 0, th = 0, lk = 0, rs = 0, amp = 0;
+    int rr = 0, R = 0, np = 0;
+    unsigned thr = 0;
+    unsigned long long outdeg = 0;
+    const uint4 *ent = a.pin;
+    if (mine) {
+        v = ((const V *)a.V)[j];
+        rr = a.r[j];
+        th = ((const V *)a.th)[j];
+        lk = ((const V *)a.lk)[j];
+        rs = ((const V *)a.rs)[j];
+        R = a.R[j];
+        thr = a.prate[j];
+        amp = ((const V *)a.pamp)[j];
+        np = (a.pin_len[j] + 1) >> 1;
+        outdeg = (unsigned long long)(a.rowptr[j + 1] - a.rowptr[j]);
+        ent = a.pin + a.pin_off[j >> 5] + lane;
+    }
+    const int npmax = __reduce_max_sync(0xffffffffu, np);   // pairs of the warp's longest list
+    using RA = typename Tr<MODE>::A;
+    RA *ring = (RA *)a.ring;
+    unsigned long long my_spikes = 0, my_events = 0;
+    bool overflow = false;
+    // synapse loads run one half (four pairs) ahead of their use
+    constexpr int P = kPullUnroll;
+    uint4 ea[P], eb[P];
+    pull_load(ea, ent, 0, np);
+    __syncthreads();
+    for (int s = 0; s < a.steps; ++s) {
+        const int t = a.t0 + s;
+        const unsigned row0 = (unsigned)((t - base - D) * Wp) * 4u;
+        bool fire = false;
+        Acc acc = 0;
+        for (int p0 = 0; p0 < npmax; p0 += 2 * P) {
+            pull_load(eb, ent, p0 + P, np);
+            pull_batch<MODE>(acc, ea, win, row0);
+            pull_load(ea, ent, p0 + 2 * P, np);
+            pull_batch<MODE>(acc, eb, win, row0);
+        }
+        if (mine) {
+            // input still pending in the ring from an earlier push run
+            V ring_in = 0;
+            if (t < a.ring_until) {
+                RA *slot = ring + (size_t)(t % a.D1) * a.n + j;
+                ring_in = Tr<MODE>::from_acc(*slot);
+                *slot = 0;
+            }
+            V ext = 0;
+            if (t < a.ev_nsteps) {
+                int lo = a.ev_off[t], hi = a.ev_off[t + 1];
+                const int end = hi;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    if (a.ev_neuron[mid] < j) lo = mid + 1; else hi = mid;
+                }
+                if (lo < end && a.ev_neuron[lo] == j) ext = ((const V *)a.ev_val)[lo];
+            }
+            if (thr && poisson_fires(a.pkey, (unsigned)t, (unsigned)j, thr)) {
+                if (MODE == SN_F32) ext = __fadd_rn(ext, amp); else ext = ext + amp;
+            }
+            if constexpr (MODE == SN_F32) {
+                const float in = t < a.ring_until ? __fadd_rn(acc, ring_in) : acc;
+                fire = lif_update_f32(v, rr, in, ext, th, lk, rs, R);
+            } else {
+                // the integrated state is checked against int32 before the threshold
+                const long long in = acc + (long long)ring_in;
+                long long u;
+                if (v > rs) { u = (long long)v - lk; u = u > rs ? u : rs; }
+                else if (v < rs) { u = (long long)v + lk; u = u < rs ? u : rs; }
+                else u = rs;
+                u += in;
+                u += ext;
+                if (u > 2147483647ll || u < -2147483648ll) overflow = true;
+                fire = (u > th) && (rr == 0);
+                if (fire) { u = rs; rr = R; }
+                else if (rr > 0) rr -= 1;
+                v = (int)u;
+            }
+        }
+        const int tD = t % D;
+        const unsigned ball = __ballot_sync(0xffffffffu, fire);
+        if (lane == 0 && wbase < a.n) {
+            a.hist[(size_t)tD * W + (wbase >> 5)] = ball;
+            a.raster[(size_t)(t % a.cap) * W + (wbase >> 5)] = ball;
+        }
+        if (fire) { my_spikes += 1; my_events += outdeg; }
+        if (overflow) atomicCAS(&a.ctl->status, 0, (int)SN_EOVERFLOW);
+
+        // grid barrier, split: arrive, do this block's independent work, wait
+        __syncthreads();                              // every warp's words of step t are stored
+        unsigned gen = 0;
+        if (threadIdx.x == 0 && gridDim.x > 1) gen = bar_arrive(a.ctl);
+        // the first synapses of step t + 1 (the store is static)
+        pull_load(ea, ent, 0, np);
+        int pos = t - base;                           // window position of row t
+        if (pos >= L) {
+            // rows t-D+1 .. t-1 move down by sh = pos - D + 1 rows to positions
+            // 0 .. D-2, in chunks of at most sh rows' words: a chunk's source and
+            // destination do not overlap, and the barrier between a chunk's reads
+            // and writes orders them against the neighbouring chunks
+            const int sh = pos - D + 1;
+            const int total4 = (D - 1) * Wp / 4, shw4 = sh * Wp / 4;
+            const int per = min((int)blockDim.x, shw4);
+            for (int c0 = 0; c0 < total4; c0 += per) {
+                const int k = c0 + (int)threadIdx.x;
+                uint4 val = make_uint4(0u, 0u, 0u, 0u);
+                const bool act = threadIdx.x < per && k < total4;
+                if (act) val = s_win4[k + shw4];
+                __syncthreads();
+                if (act) s_win4[k] = val;
+            }
+            base = t - D + 1;
+            pos = D - 1;
+        }
+        if (threadIdx.x == 0) {
+            s_ok = gridDim.x > 1 ? bar_wait(a.ctl, gen) : 1;
+            s_stop = ld_status(a.ctl);
+        }
+        __syncthreads();
+        if (!s_ok) break;
+        // row t enters the window
+        for (int i = threadIdx.x; i < W; i += blockDim.x)
+            s_win[(size_t)pos * Wp + i] = __ldcg(a.hist + (size_t)tD * W + i);
+        __syncthreads();
+        if (s_stop) break;
+    }
+    if (mine) {
+        ((V *)a.V)[j] = v;
+        a.r[j] = rr;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        my_spikes += __shfl_down_sync(0xffffffffu, my_spikes, o);
+        my_events += __shfl_down_sync(0xffffffffu, my_events, o);
+    }
+    if (lane == 0 && my_spikes) {
+        atomicAdd(&a.ctl->spikes, my_spikes);
+        atomicAdd(&a.ctl->events, my_events);
+    }
+}
+
+// Spikes of steps t0 - D .. t0 - 1 held in the history go into the ring for
+// their arrival steps >= t0 (earlier arrivals were delivered by the pull
+// kernel), so that push propagation continues the run exactly.
+template <int MODE>
+__global__ void pull_flush_kernel(NetArgs a, int t0) {
+    using RA = typename Tr<MODE>::A;
+    RA *ring = (RA *)a.ring;
+    const int D = a.hD, W = a.words;
+    const long long total = (long long)D * W;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int tau = t0 - (int)(q / W) - 1;
+        const int w = (int)(q % W);
+        if (tau < 0) continue;
+        unsigned bits = a.hist[(size_t)(tau % D) * W + w];
+        while (bits) {
+            const int i = w * 32 + __ffs(bits) - 1;
+            bits &= bits - 1u;
+            if (i >= a.n) break;
+            for (long long p = a.rowptr[i]; p < a.rowptr[i + 1]; ++p) {
+                const uint2 sy = a.syn[p];
+                const int arrive = tau + (int)(sy.x >> kPostBits) + 1;
+                if (arrive < t0) continue;
+                const int post = (int)(sy.x & kPostMask);
+                atomicAdd(ring + (size_t)(arrive % a.D1) * a.n + post, Tr<MODE>::to_acc(sy.y));
+            }
+        }
+    }
+}
+
+const void *pull_fn(int dtype) {
+    return dtype == SN_F32 ? (const void *)sparse_pull_kernel<SN_F32> : (const void *)sparse_pull_kernel<SN_I32>;
+}
+
+}  // namespace
+
+cudaError_t plan_pull(int n, int D, int *grid, int *chunk, int *rows, size_t *smem) {
+    *grid = 0;
+    int dev = 0, sms = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+    const long long words = (n + 31) / 32, wp = (words + 3) & ~3ll;
+    // one neuron per thread, at most one block per SM; a window of at least
+    // D rows must fit a block's shared memory next to the few static words
+    const long long L = std::min<long long>((optin - 64) / (wp * 4), 1 << 14);
+    if (L < D) return cudaSuccess;
+    const long long per = (words + sms - 1) / sms;   // slices per block
+    if (per * 32 > kPullMaxBlock) return cudaSuccess;
+    const long long bytes = L * wp * 4;
+    for (const void *fn : {pull_fn(SN_F32), pull_fn(SN_I32)}) {
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        int p = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, fn, (int)(per * 32), (size_t)bytes);
+        if (e != cudaSuccess) return e;
+        if (p < 1) return cudaSuccess;
+    }
+    *chunk = (int)(per * 32);
+    *grid = (int)((n + *chunk - 1) / *chunk);
+    *rows = (int)L;
+    *smem = (size_t)bytes;
+    return cudaSuccess;
+}
+
+cudaError_t launch_sparse_pull(const NetArgs &a, int dtype, int grid, size_t smem, cudaStream_t s) {
+    void *args[] = {(void *)&a};
+    const void *fn = pull_fn(dtype);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(a.chunk), args, smem, s);
+}
+
+cudaError_t launch_pull_flush(const NetArgs &a, int dtype, int t0, cudaStream_t s) {
+    const long long total = (long long)a.hD * a.words;
+    const int block = 256;
+    const int grid = (int)std::min<long long>((total + block - 1) / block, 4096);
+    if (dtype == SN_F32) pull_flush_kernel<SN_F32><<<grid, block, 0, s>>>(a, t0);
+    else pull_flush_kernel<SN_I32><<<grid, block, 0, s>>>(a, t0);
+    return cudaGetLastError();
+}
+
+}  // namespace sn

@@ -28,6 +28,8 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--repeat", type=int, default=2)
     ap.add_argument("--scale", type=float, default=1.0)
+    ap.add_argument("--propagation", choices=["push", "pull"], default="push",
+                    help="large-sparse: push or pull propagation")
     args = ap.parse_args()
     import __graft_entry__ as G
     G.build()
@@ -53,6 +55,7 @@ def main():
         return
     if wl_name == "large-sparse":
         ctx = S.from_workload(W.large_sparse(steps=T), record_steps=T, stream=stream.cuda_stream)
+        S.sn_set_propagation(ctx, S.SN_PULL if args.propagation == "pull" else S.SN_PUSH)
     elif wl_name in ("large-dense", "large-dense-stdp"):
         n = int(16384 * args.scale) // 32 * 32
         ctx = S.from_workload(W.large_dense(n=n, stdp=wl_name.endswith("stdp"), steps=T), record_steps=T,

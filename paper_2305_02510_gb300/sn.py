@@ -19,7 +19,8 @@ from . import build as _build
 
 SN_OK, SN_EINVAL, SN_ENOMEM, SN_ECUDA, SN_ESTATE, SN_ETIMEOUT, SN_EUNSUPPORTED, SN_EOVERFLOW = range(8)
 SN_F32, SN_I32 = 0, 1
-SN_AUTO, SN_EXEC_CTA, SN_EXEC_GRID = 0, 1, 2
+SN_AUTO, SN_EXEC_CTA, SN_EXEC_GRID, SN_PROP_PULL = 0, 1, 2, 4
+SN_PUSH, SN_PULL = 0, 1
 _NAMES = ["SN_OK", "SN_EINVAL", "SN_ENOMEM", "SN_ECUDA", "SN_ESTATE", "SN_ETIMEOUT",
           "SN_EUNSUPPORTED", "SN_EOVERFLOW"]
 
@@ -103,6 +104,8 @@ def lib():
                 "sn_get_weights": [_P, _P, C.c_int32],
                 "sn_get_counters": [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                     C.POINTER(C.c_int64)],
+                "sn_set_propagation": [_P, C.c_int32],
+                "sn_get_propagation": [_P, C.POINTER(C.c_int32)],
                 "sn_save": [_P, _P, C.POINTER(C.c_size_t)],
                 "sn_load": [_P, _P, C.c_size_t],
             }
@@ -268,6 +271,17 @@ def sn_autotune(ctx: Ctx, trial_steps: int = 20) -> float:
     ms = C.c_float(0)
     _check(lib().sn_autotune(ctx.handle, int(trial_steps), C.byref(ms)), ctx)
     return ms.value
+
+
+def sn_set_propagation(ctx: Ctx, mode: int):
+    """SN_PUSH or SN_PULL propagation for a sparse network."""
+    _check(lib().sn_set_propagation(ctx.handle, int(mode)), ctx)
+
+
+def sn_get_propagation(ctx: Ctx) -> int:
+    m = C.c_int32(0)
+    _check(lib().sn_get_propagation(ctx.handle, C.byref(m)), ctx)
+    return m.value
 
 
 def split_batch_raster(bits, net_n):

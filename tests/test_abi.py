@@ -91,4 +91,6 @@ def test_version_and_null_handles(S):
     assert b"sm_103a" in L.sn_version()
     assert L.sn_run(None, 1) == S.SN_EINVAL
     assert L.sn_sync(None) == S.SN_EINVAL
+    assert L.sn_set_propagation(None, S.SN_PULL) == S.SN_EINVAL
+    assert L.sn_get_propagation(None, None) == S.SN_EINVAL
     L.sn_destroy(None)
