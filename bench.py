@@ -37,9 +37,11 @@ TIMESTEPS = 1000
 # V and r read+write (16), threshold/leak/reset/refractory/Poisson rate and
 # amplitude read (24), pending-input slot read and clear (16)
 STATE_BYTES = 56
-# DRAM bytes per launch of the sparse kernel from the last ncu capture of the
-# current kernel (None until one is taken for this kernel version)
-NCU_TRAFFIC_BYTES = None
+# the pull kernel touches the same state without the pending-input slot
+STATE_BYTES_PULL = 40
+# DRAM bytes (read + write) of one 1000-timestep launch, from the ncu capture
+# of the current kernel version (absent: none taken for that kernel)
+NCU_TRAFFIC_BYTES = {"sparse_pull_kernel<SN_F32>": 3.39e9 + 3.87e6}
 
 
 def replica_seed(seed, rank):
@@ -131,7 +133,7 @@ def algorithmic_bytes_pull(n, m, timesteps):
     the update phase's state traffic and raster bit.  The spike-history rows
     each block copies into shared memory are not counted (L2 reads of a few
     MB per step)."""
-    return timesteps * (m * 8 + n * STATE_BYTES + n / 8)
+    return timesteps * (m * 8 + n * STATE_BYTES_PULL + n / 8)
 
 
 def oracle_sample(wl, warm=40, timed=60):
@@ -508,6 +510,7 @@ def main():
     if rank == 0:
         peak, src = peaks()
         abytes = algorithmic_bytes_pull(n, m, T) if pull else algorithmic_bytes(n, T, spikes, events)
+        kernel = "sparse_pull_kernel<SN_F32>" if pull else "sparse_reg_kernel<SN_F32>"
         achieved = abytes / (ms / 1e3) / 1e9
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -523,8 +526,8 @@ def main():
             "wall_ms_per_step": 1e3 * wall / args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": src,
-                         "traffic": NCU_TRAFFIC_BYTES,
-                         "kernel": "sparse_pull_kernel<SN_F32>" if pull else "sparse_reg_kernel<SN_F32>",
+                         "traffic": NCU_TRAFFIC_BYTES.get(kernel) if T == TIMESTEPS else None,
+                         "kernel": kernel,
                          "algorithmic_bytes_per_launch": abytes},
             "e2e": {"value": e2e_ev_all / e2e_all, "unit": UNIT,
                     "h2d_bytes_per_step": 8 * n,
