@@ -195,7 +195,7 @@ def extras(S, W, torch, stream, flush):
             "spikes_per_timestep": spk / 1000,
             "roofline": {"bound": "hbm", "achieved": abytes / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": abytes / (ms / 1e3) / 1e9 / peak, "peak_source": src,
-                         "kernel": "dense_kernel<CPL,%s>" % ("true" if stdp else "false")}}
+                         "kernel": "dense_kernel<1,true,false>" if stdp else "dense_kernel<1,false,true>"}}
         del ctx
     res["dense_stdp"]["stdp_overhead"] = res["dense_stdp"]["ms"] / res["dense"]["ms"]
     # batched networks against the plain per-network path
@@ -226,6 +226,8 @@ def extras(S, W, torch, stream, flush):
     plain_ms = a.elapsed_time(b2)
     plain_ev = sum(S.sn_get_counters(c)[2] for c in plain)
     del plain
+    res["paper_grid"] = paper_grid_extra(S, W, torch, stream, flush)
+    res["huge_dense"] = huge_dense_extra(S, W, torch, stream, flush)
     res["bptt"] = bptt_extra(S, W, torch, stream)
     res["shared_dense"] = shared_extra(S, W, torch, stream, flush)
     res["batched"] = {
@@ -376,6 +378,83 @@ def shared_extra(S, W, torch, stream, flush):
                          "kernel": "shared_kernel (tcgen05.mma kind::f8f6f4)"},
             "plain_ms": total, "plain_synaptic_events_per_s": pev / (total / 1e3),
             "speedup_vs_plain": total / ms, "launches": 1, "plain_launches": B}
+
+
+# Table 2 of the paper: seconds for 1000 timesteps on its benchmark networks,
+# by simulator, N in (100, 1000, 10000) x p in (.25, .5, .75, 1); None = ">1h".
+# MAT ran on a desktop CPU, ABM and BindsNET on an unnamed GPU (Section 3).
+PAPER_TABLE2 = {
+    "mat": [[0.04, 0.04, 0.05, 0.05], [0.36, 0.52, 0.68, 0.80], [30.37, 40.34, 55.38, 71.62]],
+    "abm": [[1.10, 1.16, 1.18, 1.26], [4.11, 5.59, 7.22, 9.08], [166.72, 325.30, 488.83, 641.36]],
+    "nest": [[0.41, 0.65, 0.91, 1.23], [28.05, 61.42, 81.54, 112.82], [3242.83, None, None, None]],
+    "brian2": [[6.63, 12.43, 18.36, 24.23], [612.43, 1249.31, 1892.19, 2529.77], [None, None, None, None]],
+    "bindsnet": [[2.44, 2.34, 2.46, 2.38], [3.45, 3.67, 4.19, 4.64], [63.73, 117.78, 181.04, 230.07]],
+}
+GRID_N = (100, 1000, 10000)
+GRID_P = (0.25, 0.5, 0.75, 1.0)
+
+
+def huge_dense_extra(S, W, torch, stream, flush, n=100_000, steps=1000):
+    """The paper's 100,000-neuron all-to-all network (Section 4: about five
+    minutes in its matrix mode, step count not stated): 40 GB of float32
+    weights drawn on the device, 1000 timesteps."""
+    peak, src = peaks()
+    wl = W.huge_dense(n=n, steps=steps)
+    w = W.dense_weights_on_device(wl, torch)
+    ctx = S.from_workload(wl, record_steps=steps, stream=stream.cuda_stream, w_device=w)
+    del w
+    torch.cuda.empty_cache()
+    ms, spk, ev = timed_runs(S, torch, stream, flush, ctx, steps, 2)
+    del ctx
+    torch.cuda.empty_cache()
+    abytes = spk * 4 * n + steps * n * STATE_BYTES
+    return {"workload": wl["name"] + " (all-to-all, 4e10 B of weights)", "neurons": n, "timesteps": steps,
+            "ms": ms, "synaptic_events_per_s": ev / (ms / 1e3), "timesteps_per_s": steps / (ms / 1e3),
+            "spikes_per_timestep": spk / steps, "paper": "about 5 minutes, step count not stated (Section 4)",
+            "roofline": {"bound": "hbm", "achieved": abytes / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": abytes / (ms / 1e3) / 1e9 / peak, "peak_source": src,
+                         "kernel": "dense_kernel<8,false,true>"}}
+
+
+def paper_grid_extra(S, W, torch, stream, flush):
+    """The paper's benchmark grid (Section 3): each network simulated for
+    1000 timesteps through the dense path and through the sparse path (push or
+    pull, whichever sn_autotune picks), beside the paper's Table 2 times."""
+    out = []
+    for a, n in enumerate(GRID_N):
+        for b, p in enumerate(GRID_P):
+            wl = W.paper_grid(n, p, steps=1000)
+            m = int(len(wl["pre"]))
+            row = {"n": n, "p": p, "synapses": m}
+            w = np.zeros((n, n), np.float32)
+            w[wl["pre"], wl["post"]] = 1.0
+            ctx = S.sn_create_dense(wl["threshold"], wl["leak"], wl["reset"], wl["refractory"], w, 1,
+                                    max_delay=1, record_steps=1000, stream=stream.cuda_stream)
+            del w
+            ev = wl["events"]
+            S.sn_set_input(ctx, ev["step"], ev["neuron"], ev["value"])
+            ms, spk, _ = timed_runs(S, torch, stream, flush, ctx, 1000, 2)
+            row["dense_ms"] = ms
+            del ctx
+            ctx = S.from_workload(wl, record_steps=1000, stream=stream.cuda_stream)
+            S.sn_autotune(ctx, 1000)
+            prop = "pull" if S.sn_get_propagation(ctx) == S.SN_PULL else "push"
+            ms2, spk2, evs = timed_runs(S, torch, stream, flush, ctx, 1000, 2)
+            del ctx
+            row["sparse_ms"], row["sparse_propagation"] = ms2, prop
+            assert spk2 == spk, "dense and sparse paths disagree on the spike count"
+            # events along existing synapses (the dense path also visits the zeros)
+            row["synaptic_events"] = evs
+            best = min(ms, ms2)
+            row["best_s_per_1000_steps"] = best / 1e3
+            row["synaptic_events_per_s"] = evs / (best / 1e3)
+            for k, tab in PAPER_TABLE2.items():
+                row[f"paper_{k}_s"] = tab[a][b]
+            row["speedup_vs_paper_mat"] = PAPER_TABLE2["mat"][a][b] / (best / 1e3)
+            out.append(row)
+    return {"workload": "paper benchmark grid (Section 3): Bernoulli(p) digraphs, unit weights and delays, "
+                        "3 inputs spiked every 10 steps, 1000 timesteps; paper times are Table 2 "
+                        "(desktop CPU / unnamed GPU)", "points": out}
 
 
 def run_reference(args, wl, rank):

@@ -131,7 +131,9 @@ sn_status sn_create(const sn_config *cfg, const sn_neurons *neurons,
  * (w[i*n + j] is the weight of i -> j, Section 2.1).  Every synapse has delay
  * `delay` (1..cfg->max_delay).  The diagonal takes part in propagation like
  * any entry (pass zeros for no self-synapses) but is never changed by STDP.
- * Only SN_F32 is supported (SN_EUNSUPPORTED otherwise). */
+ * w = NULL starts every weight at zero (install them with sn_set_weights,
+ * e.g. from device memory, without an n x n host copy).  Only SN_F32 is
+ * supported (SN_EUNSUPPORTED otherwise). */
 sn_status sn_create_dense(const sn_config *cfg, const sn_neurons *neurons,
                           const float *w, int32_t delay, sn_ctx **out);
 
@@ -268,6 +270,15 @@ sn_status sn_get_trace(sn_ctx *ctx, float *trace, int32_t on_device);
 /* Current weights: m floats in the order the synapses were given to
  * sn_create, or n*n floats row-major for a dense network. */
 sn_status sn_get_weights(sn_ctx *ctx, float *w, int32_t on_device);
+
+/* Replace the weights (the inverse of sn_get_weights, same layout: m floats
+ * in input order, or n*n floats row-major for a dense network; Section 2.1's
+ * synapse weights).  on_device = 1: `w` is a device pointer, copied on the
+ * stream without validation; 0: host memory (NaN rejected with SN_EINVAL),
+ * copied before the call returns.  Delays, the state and pending input are
+ * kept; runs after the call use the new weights.  Dense contexts and SN_F32
+ * sparse contexts (SN_EUNSUPPORTED for SN_I32, SN_ESTATE for other kinds). */
+sn_status sn_set_weights(sn_ctx *ctx, const float *w, int32_t on_device);
 
 /* Steps run so far, total spikes and total synaptic events (one event = one
  * spike delivered along one synapse), counted on the device. */

@@ -301,14 +301,14 @@ sn_status sn_create_dense(const sn_config *cfg, const sn_neurons *nr, const floa
                           sn_ctx **out) {
     sn_status s = check_config(cfg);
     if (s) return s;
-    if (!nr || !w || !out) return fail(nullptr, SN_EINVAL, "NULL argument");
+    if (!nr || !out) return fail(nullptr, SN_EINVAL, "NULL argument");
     if (cfg->dtype != SN_F32) return fail(nullptr, SN_EUNSUPPORTED, "dense networks are SN_F32 only");
     if (cfg->flags & SN_PROP_PULL) return fail(nullptr, SN_EUNSUPPORTED, "SN_PROP_PULL applies to sn_create networks");
     const int n = nr->n;
     if (n < 1 || n > 200000) return fail(nullptr, SN_EINVAL, "dense n must be in 1 .. 200000");
     if (delay < 1 || delay > cfg->max_delay) return fail(nullptr, SN_EINVAL, "delay outside 1..max_delay");
     const size_t nn = (size_t)n * n;
-    for (size_t q = 0; q < nn; ++q)
+    for (size_t q = 0; w && q < nn; ++q)
         if (!std::isfinite(w[q]) || std::fabs(w[q]) > 1e9f) return fail(nullptr, SN_EINVAL, "weight not finite");
     sn_ctx *c = new (std::nothrow) sn_ctx();
     if (!c) return fail(nullptr, SN_ENOMEM, "host allocation failed");
@@ -339,7 +339,7 @@ sn_status sn_create_dense(const sn_config *cfg, const sn_neurons *nr, const floa
     if ((s = dalloc(c, &c->W, nn * 4)) || (s = dalloc(c, &c->spk, (size_t)2 * c->words * 4)) ||
         (s = dalloc(c, &c->ring, c->ring_bytes)))
         return bail(s);
-    if ((e = cudaMemcpy(c->W, w, nn * 4, cudaMemcpyHostToDevice)) ||
+    if ((e = w ? cudaMemcpy(c->W, w, nn * 4, cudaMemcpyHostToDevice) : cudaMemset(c->W, 0, nn * 4)) ||
         (e = cudaMemset(c->spk, 0, (size_t)2 * c->words * 4)) || (e = cudaMemset(c->ring, 0, c->ring_bytes))) {
         c->err = std::string("upload: ") + cudaGetErrorString(e);
         return bail(SN_ECUDA);
@@ -694,6 +694,43 @@ sn_status sn_get_weights(sn_ctx *c, float *w, int32_t on_device) {
         if (e != cudaSuccess) return cuda_fail(c, e, "weight copy");
         return read_status(c);
     }
+    return SN_OK;
+}
+
+sn_status sn_set_weights(sn_ctx *c, const float *w, int32_t on_device) {
+    if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
+    if (!w) return fail(c, SN_EINVAL, "w is NULL");
+    if (c->failed) return fail(c, SN_ESTATE, "context is in an error state");
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    if (c->kind == KIND_DENSE) {
+        SN_CUDA(c, cudaMemcpyAsync(c->W, w, (size_t)c->n * c->n * 4, kind, c->stream));
+        if (!on_device) SN_CUDA(c, cudaStreamSynchronize(c->stream));
+        return SN_OK;
+    }
+    if (c->kind != KIND_SPARSE) return fail(c, SN_ESTATE, "wrong context kind");
+    if (c->dtype != SN_F32) return fail(c, SN_EUNSUPPORTED, "weights of SN_I32 networks are fixed at creation");
+    if (c->m == 0) return SN_OK;
+    if (!c->perm_inv) {
+        sn_status s = dalloc(c, &c->perm_inv, (size_t)c->m * 8);
+        if (s) return s;
+        SN_CUDA(c, cudaMemcpy(c->perm_inv, c->h_perm_inv.data(), (size_t)c->m * 8, cudaMemcpyHostToDevice));
+    }
+    const float *src = w;
+    float *tmp = nullptr;
+    if (!on_device) {
+        for (long long k = 0; k < c->m; ++k)
+            if (std::isnan(w[k])) return fail(c, SN_EINVAL, "NaN weight");
+        sn_status s = dalloc(c, &tmp, (size_t)c->m * 4);
+        if (s) return s;
+        cudaError_t e = cudaMemcpyAsync(tmp, w, (size_t)c->m * 4, cudaMemcpyHostToDevice, c->stream);
+        if (e != cudaSuccess) { dfree(c, tmp); return cuda_fail(c, e, "weight upload"); }
+        src = tmp;
+    }
+    cudaError_t e = launch_scatter_weights(c->syn, c->perm_inv, c->m, src, c->stream);
+    if (e == cudaSuccess && tmp) e = cudaStreamSynchronize(c->stream);
+    dfree(c, tmp);
+    if (e != cudaSuccess) return cuda_fail(c, e, "weight scatter");
+    c->pin_stale = true;                       // the pull store holds copies of the weights
     return SN_OK;
 }
 

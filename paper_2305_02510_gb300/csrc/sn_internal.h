@@ -174,5 +174,7 @@ cudaError_t launch_sparse_pull(const NetArgs &a, int dtype, int grid, size_t sme
 cudaError_t launch_pull_flush(const NetArgs &a, int dtype, int t0, cudaStream_t s);
 cudaError_t launch_gather_weights(const uint2 *syn, const long long *perm_inv, long long m,
                                   float *out, cudaStream_t s);
+cudaError_t launch_scatter_weights(uint2 *syn, const long long *perm_inv, long long m, const float *w,
+                                   cudaStream_t s);
 
 }  // namespace sn

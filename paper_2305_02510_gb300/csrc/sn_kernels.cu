@@ -409,7 +409,7 @@ cudaError_t max_grid_sparse(int dtype, int stdp, int block, int *grid) {
 // block, so no other synchronisation is needed; the result does not depend on
 // thread timing.
 
-constexpr int kDListMax = 2048;                    // spikers held in shared memory
+constexpr int kDListMax = 4096;                    // spikers held in shared memory
 
 // Spikers of a spike-bit row with rank in [lo, hi) (ascending neuron order).
 __device__ void extract_ranks(const unsigned *rrow, const int *wpre, int words, int lo, int hi,
@@ -465,14 +465,79 @@ __device__ void popcount_prefix(const unsigned *row, int words, int *wpre, int *
     __syncthreads();
 }
 
-template <int CPL, bool STDP>
-__global__ void __launch_bounds__(kBlock) dense_kernel(NetArgs a) {
+// Vector gather of one list chunk (no STDP; n % 4 == 0 and W 16-byte aligned).
+// The slab's 32 * CPL columns are G = 8 * CPL float4 groups.  A warp loads
+// RPI = 32 / min(G, 32) rows per instruction (lane l: sub-row l / LPR, group
+// l % LPR, plus group + 32 when G = 64), so one instruction moves 512 bytes.
+// The warp's rows are list[warp + nwarp * i], i = 0, 1, ...; sub-row q takes
+// i = q, q + RPI, ... in ascending order.  U instructions stay in flight: the
+// load for row i + RPI * U is issued as row i is added (register rotation).
+template <int CPL>
+struct VecGeom {
+    static constexpr int G = 8 * CPL;                  // float4 groups of the slab
+    static constexpr int LPR = G < 32 ? G : 32;        // lanes per row
+    static constexpr int RPI = 32 / LPR;               // rows per instruction
+    static constexpr int F = G > 32 ? G / 32 : 1;      // float4 per lane per row
+    static constexpr int U = F > 1 ? 3 : (CPL == 4 ? 7 : 8);   // instructions in flight
+};
+
+template <int CPL>
+__device__ __forceinline__ void gather_vec(const float *__restrict__ W, int n, int c0, const int *list,
+                                           int cnt, int warp, int lane, float4 (&acc)[VecGeom<CPL>::F]) {
+    using Gm = VecGeom<CPL>;
+    constexpr int nwarp = kBlock / 32, RPI = Gm::RPI, F = Gm::F, U = Gm::U;
+    const int q = lane / Gm::LPR, g = lane % Gm::LPR;
+    // this lane's rows: list[warp + nwarp * (q + RPI * k)], k = 0 .. nk-1
+    const int rows = cnt > warp ? (cnt - warp + nwarp - 1) / nwarp : 0;
+    const int nk = rows > q ? (rows - q + RPI - 1) / RPI : 0;
+    const int *lp = list + warp + nwarp * q;
+    constexpr int lstep = nwarp * RPI;
+    const float4 *wv = (const float4 *)(W + c0) + g;     // this lane's first group, row 0
+    const size_t rs4 = (size_t)(n >> 2);                 // float4 per row
+    const bool cv0 = c0 + 4 * g < n, cv1 = F > 1 && c0 + 4 * (g + 32) < n;
+    float4 buf[U][F];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const bool ok = u < nk;
+        const float4 *p = wv + (ok ? (size_t)lp[lstep * u] * rs4 : 0);
+        buf[u][0] = (ok && cv0) ? __ldg(p) : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (F > 1) buf[u][F - 1] = (ok && cv1) ? __ldg(p + 32) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    for (int k0 = 0; k0 < nk; k0 += U) {
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int k = k0 + u;
+            float4 x[F];
+#pragma unroll
+            for (int f = 0; f < F; ++f) x[f] = buf[u][f];
+            const int kn = k + U;
+            const bool ok = kn < nk;
+            const float4 *p = wv + (ok ? (size_t)lp[lstep * kn] * rs4 : 0);
+            buf[u][0] = (ok && cv0) ? __ldg(p) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (F > 1) buf[u][F - 1] = (ok && cv1) ? __ldg(p + 32) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (k < nk) {
+#pragma unroll
+                for (int f = 0; f < F; ++f) {
+                    acc[f].x = __fadd_rn(acc[f].x, x[f].x);
+                    acc[f].y = __fadd_rn(acc[f].y, x[f].y);
+                    acc[f].z = __fadd_rn(acc[f].z, x[f].z);
+                    acc[f].w = __fadd_rn(acc[f].w, x[f].w);
+                }
+            }
+        }
+    }
+}
+
+template <int CPL, bool STDP, bool VEC>
+__global__ void __launch_bounds__(kBlock, CPL <= 2 ? 4 : 3) dense_kernel(NetArgs a) {
     extern __shared__ int smem[];
     constexpr int cw = 32 * CPL;
     constexpr int nwarp = kBlock / 32;
+    using Gm = VecGeom<CPL>;
     int *wpre = smem;                                  // [words + 1]
     int *list = smem + a.words + 1;                    // [kDListMax]
-    float *wpart = (float *)(list + kDListMax);        // [nwarp][cw]
+    // [nwarp][cw], vector path [nwarp][RPI][cw]; 16-byte aligned
+    float *wpart = (float *)(smem + ((a.words + 1 + kDListMax + 3) & ~3));
     __shared__ int s_scan[kBlock / 32];
     __shared__ int s_stop;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -481,18 +546,22 @@ __global__ void __launch_bounds__(kBlock) dense_kernel(NetArgs a) {
     const int j = c0 + threadIdx.x;
     const bool mine = threadIdx.x < cw && j < n;
     float *ring = (float *)a.ring;
-    float v = 0, th = 0, lk = 0, rs = 0, amp = 0;
-    int rr = 0, R = 0;
-    unsigned thr = 0;
+    // the slab's neuron parameters stay in shared memory for the launch (the
+    // registers go to the gather's loads in flight); state in registers
+    __shared__ float s_th[kBlock], s_lk[kBlock], s_rs[kBlock], s_amp[kBlock];
+    __shared__ int s_R[kBlock];
+    __shared__ unsigned s_thr[kBlock];
+    float v = 0;
+    int rr = 0;
     if (mine) {
         v = ((const float *)a.V)[j];
         rr = a.r[j];
-        th = ((const float *)a.th)[j];
-        lk = ((const float *)a.lk)[j];
-        rs = ((const float *)a.rs)[j];
-        R = a.R[j];
-        thr = a.prate[j];
-        amp = ((const float *)a.pamp)[j];
+        s_th[threadIdx.x] = ((const float *)a.th)[j];
+        s_lk[threadIdx.x] = ((const float *)a.lk)[j];
+        s_rs[threadIdx.x] = ((const float *)a.rs)[j];
+        s_R[threadIdx.x] = a.R[j];
+        s_thr[threadIdx.x] = a.prate[j];
+        s_amp[threadIdx.x] = ((const float *)a.pamp)[j];
     }
     unsigned long long my_spikes = 0;
 
@@ -516,8 +585,10 @@ __global__ void __launch_bounds__(kBlock) dense_kernel(NetArgs a) {
                 }
                 if (lo < end && a.ev_neuron[lo] == j) ext = ((const float *)a.ev_val)[lo];
             }
-            if (thr && poisson_fires(a.pkey, (unsigned)t, (unsigned)j, thr)) ext = __fadd_rn(ext, amp);
-            fire = lif_update_f32(v, rr, acc, ext, th, lk, rs, R);
+            const unsigned thr = s_thr[threadIdx.x];
+            if (thr && poisson_fires(a.pkey, (unsigned)t, (unsigned)j, thr)) ext = __fadd_rn(ext, s_amp[threadIdx.x]);
+            fire = lif_update_f32(v, rr, acc, ext, s_th[threadIdx.x], s_lk[threadIdx.x], s_rs[threadIdx.x],
+                                  s_R[threadIdx.x]);
             if constexpr (STDP) {
                 const float xo = a.trace[(size_t)((t + 2) % 3) * n + j];
                 a.trace[(size_t)(t % 3) * n + j] = __fadd_rn(__fmul_rn(a.decay, xo), fire ? 1.0f : 0.0f);
@@ -542,6 +613,9 @@ __global__ void __launch_bounds__(kBlock) dense_kernel(NetArgs a) {
         float acc[CPL];
         bool sc[CPL];
         float xc[CPL];
+        float4 vacc[Gm::F];
+#pragma unroll
+        for (int f = 0; f < Gm::F; ++f) vacc[f] = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
         for (int q = 0; q < CPL; ++q) {
             acc[q] = 0.0f;
@@ -556,12 +630,17 @@ __global__ void __launch_bounds__(kBlock) dense_kernel(NetArgs a) {
             extract_ranks(row_bits, wpre, a.words, base, base + cnt, list);
             __syncthreads();
             int r = warp;
+            if constexpr (VEC) {
+                gather_vec<CPL>(a.W, n, c0, list, cnt, warp, lane, vacc);
+                continue;
+            }
             if constexpr (!STDP) {
-                // sixteen rows per warp in flight
-                for (; r + 15 * nwarp < cnt; r += 16 * nwarp) {
-                    float w16[16][CPL];
+                // RF rows per warp in flight (16 columns-per-lane loads)
+                constexpr int RF = CPL >= 8 ? 2 : 16 / CPL;
+                for (; r + (RF - 1) * nwarp < cnt; r += RF * nwarp) {
+                    float w16[RF][CPL];
 #pragma unroll
-                    for (int u = 0; u < 16; ++u) {
+                    for (int u = 0; u < RF; ++u) {
                         const float *row = a.W + (size_t)list[r + u * nwarp] * n;
 #pragma unroll
                         for (int q = 0; q < CPL; ++q) {
@@ -570,7 +649,7 @@ __global__ void __launch_bounds__(kBlock) dense_kernel(NetArgs a) {
                         }
                     }
 #pragma unroll
-                    for (int u = 0; u < 16; ++u)
+                    for (int u = 0; u < RF; ++u)
 #pragma unroll
                         for (int q = 0; q < CPL; ++q) acc[q] = __fadd_rn(acc[q], w16[u][q]);
                 }
@@ -609,14 +688,23 @@ __global__ void __launch_bounds__(kBlock) dense_kernel(NetArgs a) {
                 }
             }
         }
-        // fold the warp partials in warp order; the input of t + delay
+        // fold the warp partials in warp order (vector path: warp, then
+        // sub-row); the input of t + delay
+        if constexpr (VEC) {
+            const int q = lane / Gm::LPR, g = lane % Gm::LPR;
 #pragma unroll
-        for (int q = 0; q < CPL; ++q) wpart[warp * cw + lane + 32 * q] = acc[q];
+            for (int f = 0; f < Gm::F; ++f)
+                *(float4 *)&wpart[(warp * Gm::RPI + q) * cw + 4 * (g + 32 * f)] = vacc[f];
+        } else {
+#pragma unroll
+            for (int q = 0; q < CPL; ++q) wpart[warp * cw + lane + 32 * q] = acc[q];
+        }
         __syncthreads();
         if (mine) {
             float sum = 0.0f;
+            constexpr int parts = VEC ? nwarp * Gm::RPI : nwarp;
 #pragma unroll
-            for (int w = 0; w < nwarp; ++w) sum = __fadd_rn(sum, wpart[w * cw + threadIdx.x]);
+            for (int w = 0; w < parts; ++w) sum = __fadd_rn(sum, wpart[w * cw + threadIdx.x]);
             ring[(size_t)((t + a.dense_delay) % a.D1) * n + j] = sum;
         }
         __syncthreads();
@@ -631,16 +719,29 @@ __global__ void __launch_bounds__(kBlock) dense_kernel(NetArgs a) {
     }
 }
 
+// Shared memory of a dense block: spike-count prefix, list chunk, warp
+// partials (the vector path keeps RPI partials per warp: at most 4 * 32 * 4 B
+// per warp for any CPL, as much as CPL = 4's scalar partials).
 static size_t dense_smem(int words, int cpl) {
-    return (size_t)(words + 1 + kDListMax) * sizeof(int) + (size_t)(kBlock / 32) * 32 * cpl * sizeof(float);
+    const size_t part = (size_t)(kBlock / 32) * 32 * (cpl > 4 ? cpl : 4) * sizeof(float);
+    return (size_t)((words + 1 + kDListMax + 3) & ~3) * sizeof(int) + part;
 }
 
-static const void *dense_fn(int cpl, bool stdp) {
+// vec: the vector gather (no STDP, n % 4 == 0, W 16-byte aligned)
+static const void *dense_fn(int cpl, bool stdp, bool vec) {
+    if (vec && !stdp) {
+        switch (cpl) {
+            case 1: return (const void *)dense_kernel<1, false, true>;
+            case 2: return (const void *)dense_kernel<2, false, true>;
+            case 4: return (const void *)dense_kernel<4, false, true>;
+            default: return (const void *)dense_kernel<8, false, true>;
+        }
+    }
     switch (cpl) {
-        case 1: return stdp ? (const void *)dense_kernel<1, true> : (const void *)dense_kernel<1, false>;
-        case 2: return stdp ? (const void *)dense_kernel<2, true> : (const void *)dense_kernel<2, false>;
-        case 4: return stdp ? (const void *)dense_kernel<4, true> : (const void *)dense_kernel<4, false>;
-        default: return stdp ? (const void *)dense_kernel<8, true> : (const void *)dense_kernel<8, false>;
+        case 1: return stdp ? (const void *)dense_kernel<1, true, false> : (const void *)dense_kernel<1, false, false>;
+        case 2: return stdp ? (const void *)dense_kernel<2, true, false> : (const void *)dense_kernel<2, false, false>;
+        case 4: return stdp ? (const void *)dense_kernel<4, true, false> : (const void *)dense_kernel<4, false, false>;
+        default: return stdp ? (const void *)dense_kernel<8, true, false> : (const void *)dense_kernel<8, false, false>;
     }
 }
 
@@ -648,7 +749,8 @@ cudaError_t launch_dense(const NetArgs &a, int grid, int block, cudaStream_t s) 
     (void)block;
     void *args[] = {(void *)&a};
     const size_t smem = dense_smem(a.words, a.chunk / 32);
-    const void *fn = dense_fn(a.chunk / 32, a.stdp != 0);
+    const bool vec = a.n % 4 == 0 && ((uintptr_t)a.W & 15u) == 0;
+    const void *fn = dense_fn(a.chunk / 32, a.stdp != 0, vec);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), args, smem, s);
@@ -666,8 +768,8 @@ cudaError_t plan_dense(int n, int *grid, int *chunk) {
     for (int cpl : {1, 2, 4, 8}) {
         const size_t smem = dense_smem(words, cpl);
         int per = 1 << 30;
-        for (bool st : {false, true}) {
-            const void *fn = dense_fn(cpl, st);
+        for (int v = 0; v < 3; ++v) {
+            const void *fn = dense_fn(cpl, v == 1, v == 2);
             e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
             int p = 0;
@@ -695,6 +797,22 @@ __global__ void gather_weights_kernel(const uint2 *syn, const long long *perm_in
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < m;
          k += (long long)gridDim.x * blockDim.x)
         out[k] = __uint_as_float(syn[perm_inv[k]].y);
+}
+
+// The inverse: weight of input synapse k into its CSR position.
+__global__ void scatter_weights_kernel(uint2 *syn, const long long *perm_inv, long long m, const float *w) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < m;
+         k += (long long)gridDim.x * blockDim.x)
+        syn[perm_inv[k]].y = __float_as_uint(w[k]);
+}
+
+cudaError_t launch_scatter_weights(uint2 *syn, const long long *perm_inv, long long m, const float *w,
+                                   cudaStream_t s) {
+    if (m == 0) return cudaSuccess;
+    long long blocks = (m + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    scatter_weights_kernel<<<(int)blocks, 256, 0, s>>>(syn, perm_inv, m, w);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_gather_weights(const uint2 *syn, const long long *perm_inv, long long m,

@@ -102,6 +102,7 @@ def lib():
                 "sn_get_state": [_P, _P, _P, C.c_int32],
                 "sn_get_trace": [_P, _P, C.c_int32],
                 "sn_get_weights": [_P, _P, C.c_int32],
+                "sn_set_weights": [_P, _P, C.c_int32],
                 "sn_get_counters": [_P, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                     C.POINTER(C.c_int64)],
                 "sn_set_propagation": [_P, C.c_int32],
@@ -202,8 +203,9 @@ def sn_create_dense(threshold, leak, reset, refractory, w, delay=1, *, max_delay
                     flags=SN_AUTO, record_steps=0, stream=None) -> Ctx:
     keep = []
     nr = _neurons(threshold, leak, reset, refractory, keep)
-    w = _arr(w, np.float32)
-    keep.append(w)
+    if w is not None:                  # None: zero weights, set later with sn_set_weights
+        w = _arr(w, np.float32)
+        keep.append(w)
     cfg = _config(SN_F32, max_delay if max_delay is not None else delay, flags, record_steps, stream)
     h = _P()
     _check(lib().sn_create_dense(C.byref(cfg), C.byref(nr), _ptr(w), int(delay), C.byref(h)))
@@ -373,6 +375,18 @@ def sn_get_weights(ctx: Ctx, out=None):
     return out
 
 
+def sn_set_weights(ctx: Ctx, w):
+    """Replace the weights (same layout as sn_get_weights); w is a host array
+    or a device tensor."""
+    if _is_dev(w):
+        _check(lib().sn_set_weights(ctx.handle, _ptr(w), 1), ctx)
+        return
+    w = np.ascontiguousarray(w, dtype=np.float32).reshape(-1)
+    if w.size != ctx.m:
+        raise ValueError(f"expected {ctx.m} weights, got {w.size}")
+    _check(lib().sn_set_weights(ctx.handle, _ptr(w), 0), ctx)
+
+
 def sn_get_counters(ctx: Ctx):
     a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
     _check(lib().sn_get_counters(ctx.handle, C.byref(a), C.byref(b), C.byref(c)), ctx)
@@ -465,11 +479,20 @@ def sn_destroy(ctx: Ctx):
 # ---------------------------------------------------------------------------
 # workload helper (marshalling of a workload dict into the calls above)
 
-def from_workload(wl, *, record_steps=None, flags=SN_AUTO, stream=None) -> Ctx:
+def from_workload(wl, *, record_steps=None, flags=SN_AUTO, stream=None, w_device=None) -> Ctx:
     """Create a context for a workload dict of paper_2305_02510_gb300.workloads
-    and install its inputs (events, Poisson sources, STDP)."""
+    and install its inputs (events, Poisson sources, STDP).  A workload whose
+    dense weights live on the device (huge_dense) takes them as w_device, a
+    device tensor [n, n]."""
     rec = wl["steps"] if record_steps is None else record_steps
-    if "dense_w" in wl:
+    if "dense_w_device" in wl:
+        if w_device is None:
+            raise ValueError("this workload's weights are a device tensor: pass w_device")
+        ctx = sn_create_dense(wl["threshold"], wl["leak"], wl["reset"], wl["refractory"], None,
+                              wl["dense_delay"], max_delay=wl["max_delay"], flags=flags, record_steps=rec,
+                              stream=stream)
+        sn_set_weights(ctx, w_device)
+    elif "dense_w" in wl:
         ctx = sn_create_dense(wl["threshold"], wl["leak"], wl["reset"], wl["refractory"],
                               wl["dense_w"], wl["dense_delay"], max_delay=wl["max_delay"],
                               flags=flags, record_steps=rec, stream=stream)

@@ -183,6 +183,32 @@ def large_dense(n: int = 16384, stdp: bool = False, seed: int = SEED_BASE + 3,
     return wl
 
 
+def huge_dense(n: int = 100_000, seed: int = SEED_BASE + 7, steps: int = 1000):
+    """All-to-all network too large to build on the host (the paper runs a
+    100,000-neuron all-to-all network, Section 4): weights N(0, sigma^2) with
+    sigma = 0.02 * sqrt(16384 / n), which keeps large-dense's per-step input
+    variance, W_ii = 0, delay 1, theta 1, leak 0.05, refractory 1; Poisson
+    0.02/step into every neuron at amplitude 2.  The weights are drawn on the
+    device by dense_weights_on_device (n = 100,000: 40 GB)."""
+    wl = _base(n, "f32", 1.0, 0.05, 0.0, 1, 1, steps)
+    wl.update(dense_w_device=dict(seed=int(seed), sigma=0.02 * math.sqrt(16384.0 / n)), dense_delay=1)
+    wl["poisson"] = _poisson(np.arange(n), 0.02, 2.0, seed * 7 + 3)
+    wl["name"] = f"huge-dense-n{n}"
+    return wl
+
+
+def dense_weights_on_device(wl, torch, device="cuda"):
+    """Device tensor [n, n] float32 with the weights of a huge_dense workload,
+    drawn by a seeded torch generator on the device (W_ii = 0)."""
+    spec, n = wl["dense_w_device"], wl["n"]
+    g = torch.Generator(device=device)
+    g.manual_seed(spec["seed"])
+    w = torch.empty((n, n), dtype=torch.float32, device=device)
+    w.normal_(0.0, spec["sigma"], generator=g)
+    w.fill_diagonal_(0.0)
+    return w
+
+
 def paper_grid(n: int, p: float, seed: int = SEED_BASE + 6, steps: int = 1000,
                amplitude: float = 2.0):
     """The paper's benchmark workload (Section 3): Bernoulli(p) digraph, 3 random

@@ -212,9 +212,11 @@ def test_unsupported_cases():
         S.sn_set_propagation(ctx, S.SN_PULL)
     assert e.value.status == S.SN_EUNSUPPORTED
     # a history of 64 steps x 200,000 neurons does not fit a block's shared memory
-    big = W.random_small(6, n=200000, integer=True, steps=1, p=0.0, max_delay=64)
+    n = 200000
     with pytest.raises(S.SnError) as e:
-        S.from_workload(big, flags=S.SN_PROP_PULL)
+        S.sn_create(np.ones(n), np.zeros(n), np.zeros(n), np.zeros(n, np.int32), np.zeros(0, np.int32),
+                    np.zeros(0, np.int32), np.zeros(0), np.zeros(0, np.int32), dtype=S.SN_I32,
+                    max_delay=64, flags=S.SN_PROP_PULL)
     assert e.value.status == S.SN_EUNSUPPORTED
 
 
