@@ -127,6 +127,17 @@ typedef struct {
 sn_status sn_create(const sn_config *cfg, const sn_neurons *neurons,
                     const sn_synapses *synapses, sn_ctx **out);
 
+/* sn_create with axonal delays (Section 2.2 lists the axonal delay among the
+ * neuron parameters; the benchmark of Section 3 sets it to 0).  Neuron i has
+ * axonal_delay[i] >= 0 (n values; NULL = all 0): its spike at step t reaches
+ * the post-neuron of synapse k (pre[k] = i) at t + axonal_delay[i] + delay[k].
+ * Every such sum must lie in 1..cfg->max_delay (SN_EINVAL otherwise).  The
+ * context is then an sn_create context whose synapse delays are those sums
+ * (checkpoints, propagation modes and getters as for sn_create; STDP needs
+ * every sum to be 1). */
+sn_status sn_create_axonal(const sn_config *cfg, const sn_neurons *neurons, const sn_synapses *synapses,
+                           const int32_t *axonal_delay, sn_ctx **out);
+
 /* Create an all-to-all network from a dense row-major n x n weight matrix
  * (w[i*n + j] is the weight of i -> j, Section 2.1).  Every synapse has delay
  * `delay` (1..cfg->max_delay).  The diagonal takes part in propagation like

@@ -167,10 +167,14 @@ def sampled_dense_step(wl, t, J, v_prev, r_prev, spikers, wcols, mode=O.F32):
 
 def check_sampled_dense_step(wl, t, J, v_prev, r_prev, spikers, wcols, row, v, r):
     """Compare the simulator's step t on the sample J (spikes `row`, state v,
-    r, each of length len(J)) with sampled_dense_step under the float rules
-    (spikes equal except near threshold; state within RTOL * max(|V|,
-    |theta|)).  Returns the number of spikes compared."""
-    want, wv, wr, ct = sampled_dense_step(wl, t, J, v_prev, r_prev, spikers, wcols)
+    r, each of length len(J)) with the float64 oracle's sampled step: spikes
+    equal except where the oracle's compared state is within NEAR * |theta|
+    of theta; state within RTOL * max(|V|, |theta|) of the oracle's.  These
+    networks sum thousands of weights per step, and the float32 mirror's
+    sequential sum then drifts from the exact one by up to ~1e-5 itself, so
+    the float64 potentials are the reference here.  Returns the number of
+    spikes compared."""
+    want, wv, wr, ct = sampled_dense_step(wl, t, J, v_prev, r_prev, spikers, wcols, mode=O.F64)
     th = _theta(wl)[np.asarray(J)]
     diff = np.nonzero(np.asarray(row) != want)[0]
     if diff.size and not np.all(np.abs(ct[diff] - th[diff]) < NEAR * np.abs(th[diff])):

@@ -153,6 +153,10 @@ def run(wl, mode: int, steps: int, state: State | None = None, record_v: bool = 
         pre = np.ascontiguousarray(wl["pre"], np.int32)
         post = np.ascontiguousarray(wl["post"], np.int32)
         dl = np.ascontiguousarray(wl["delay"], np.int32)
+        if wl.get("axonal_delay") is not None:
+            # Section 2.2: the axonal delay is a neuron parameter; a spike
+            # crosses the pre-neuron's axon, then the synapse
+            dl = np.ascontiguousarray(dl + np.asarray(wl["axonal_delay"], np.int32)[pre], np.int32)
         keep += [pre, post, dl]
         net.m = pre.size
         net.pre, net.post, net.delay, net.weight = _p(pre), _p(post), _p(dl), _p(st.w)

@@ -297,6 +297,35 @@ sn_status sn_create(const sn_config *cfg, const sn_neurons *nr, const sn_synapse
     return SN_OK;
 }
 
+sn_status sn_create_axonal(const sn_config *cfg, const sn_neurons *nr, const sn_synapses *sy,
+                           const int32_t *axonal_delay, sn_ctx **out) {
+    if (!axonal_delay) return sn_create(cfg, nr, sy, out);
+    sn_status s = check_config(cfg);
+    if (s) return s;
+    if (!nr || !sy || !out) return fail(nullptr, SN_EINVAL, "NULL argument");
+    const int n = nr->n;
+    if (n < 1 || n >= (1 << kPostBits)) return fail(nullptr, SN_EINVAL, "n must be in 1 .. 2^26-1");
+    if (sy->m < 0) return fail(nullptr, SN_EINVAL, "m < 0");
+    if (sy->m > 0 && (!sy->pre || !sy->delay)) return fail(nullptr, SN_EINVAL, "synapse array is NULL");
+    for (int i = 0; i < n; ++i)
+        if (axonal_delay[i] < 0 || axonal_delay[i] >= cfg->max_delay)
+            return fail(nullptr, SN_EINVAL, "neuron " + std::to_string(i) + ": axonal delay outside 0..max_delay-1");
+    // a spike of i at t travels the axon (axonal_delay[i] steps), then the
+    // synapse (delay[k] >= 1 steps): it arrives at t + axonal_delay[i] + delay[k]
+    std::vector<int32_t> eff(sy->m > 0 ? sy->m : 1);
+    for (long long k = 0; k < sy->m; ++k) {
+        if (sy->pre[k] < 0 || sy->pre[k] >= n)
+            return fail(nullptr, SN_EINVAL, "synapse " + std::to_string(k) + ": neuron index out of range");
+        if (sy->delay[k] < 1 || (long long)sy->delay[k] + axonal_delay[sy->pre[k]] > cfg->max_delay)
+            return fail(nullptr, SN_EINVAL, "synapse " + std::to_string(k) +
+                                                ": delay + axonal delay outside 1..max_delay");
+        eff[k] = sy->delay[k] + axonal_delay[sy->pre[k]];
+    }
+    sn_synapses s2 = *sy;
+    s2.delay = eff.data();
+    return sn_create(cfg, nr, &s2, out);
+}
+
 sn_status sn_create_dense(const sn_config *cfg, const sn_neurons *nr, const float *w, int32_t delay,
                           sn_ctx **out) {
     sn_status s = check_config(cfg);

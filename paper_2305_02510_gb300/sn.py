@@ -79,6 +79,8 @@ def lib():
                               C.POINTER(_P)],
                 "sn_create_dense": [C.POINTER(sn_config), C.POINTER(sn_neurons), _P, C.c_int32,
                                     C.POINTER(_P)],
+                "sn_create_axonal": [C.POINTER(sn_config), C.POINTER(sn_neurons), C.POINTER(sn_synapses), _P,
+                                     C.POINTER(_P)],
                 "sn_create_batch": [C.POINTER(sn_config), C.c_int32, C.POINTER(sn_neurons),
                                     C.POINTER(sn_synapses), C.POINTER(_P)],
                 "sn_batch_config": [_P, C.c_int32, C.c_int32],
@@ -183,7 +185,8 @@ def _neurons(threshold, leak, reset, refractory, keep):
 
 
 def sn_create(threshold, leak, reset, refractory, pre, post, weight, delay, *, dtype=SN_F32,
-              max_delay=None, flags=SN_AUTO, record_steps=0, stream=None) -> Ctx:
+              max_delay=None, flags=SN_AUTO, record_steps=0, stream=None, axonal_delay=None) -> Ctx:
+    """sn_create, or sn_create_axonal when axonal_delay (n values) is given."""
     keep = []
     nr = _neurons(threshold, leak, reset, refractory, keep)
     pre, post = _arr(pre, np.int32), _arr(post, np.int32)
@@ -195,7 +198,14 @@ def sn_create(threshold, leak, reset, refractory, pre, post, weight, delay, *, d
     D = int(max_delay if max_delay is not None else (d.max() if d.size else 1))
     cfg = _config(dtype, D, flags, record_steps, stream)
     h = _P()
-    _check(lib().sn_create(C.byref(cfg), C.byref(nr), C.byref(sy), C.byref(h)))
+    if axonal_delay is None:
+        _check(lib().sn_create(C.byref(cfg), C.byref(nr), C.byref(sy), C.byref(h)))
+    else:
+        ax = _arr(axonal_delay, np.int32)
+        if ax.size != nr.n:
+            raise ValueError(f"axonal_delay needs {nr.n} values, got {ax.size}")
+        keep.append(ax)
+        _check(lib().sn_create_axonal(C.byref(cfg), C.byref(nr), C.byref(sy), _ptr(ax), C.byref(h)))
     return Ctx(h, nr.n, cfg.dtype, (nr.n + 31) // 32, "sparse", pre.size)
 
 
@@ -499,7 +509,8 @@ def from_workload(wl, *, record_steps=None, flags=SN_AUTO, stream=None, w_device
     else:
         ctx = sn_create(wl["threshold"], wl["leak"], wl["reset"], wl["refractory"], wl["pre"],
                         wl["post"], wl["weight"], wl["delay"], dtype=wl["dtype"],
-                        max_delay=wl["max_delay"], flags=flags, record_steps=rec, stream=stream)
+                        max_delay=wl["max_delay"], flags=flags, record_steps=rec, stream=stream,
+                        axonal_delay=wl.get("axonal_delay"))
     ev = wl["events"]
     if len(ev["step"]):
         sn_set_input(ctx, ev["step"], ev["neuron"], ev["value"])

@@ -107,6 +107,40 @@ def test_delay_chain_arrival(delays, mode):
         assert list(np.nonzero(raster[:, k])[0]) == [t0 + sum(delays[:k])]
 
 
+@pytest.mark.parametrize("mode", MODES)
+@pytest.mark.parametrize("delays,axonal", [([1], [0]), ([3, 1, 4], [2, 0, 5]), ([1, 1, 1, 1], [3, 3, 0, 1])])
+def test_axonal_delay_chain_arrival(delays, axonal, mode):
+    """Section 2.2's axonal delay (a neuron parameter): along a chain, neuron k
+    fires at t0 + sum over earlier hops of (axonal delay + synaptic delay).
+    A fan-out neuron adds its axonal delay to every outgoing synapse."""
+    m = len(delays)
+    n = m + 3
+    D = max(d + a for d, a in zip(delays, axonal)) + 2
+    dtype = "i32" if mode == O.INT else "f32"
+    wl = W._base(n, dtype, 1, 1, 0, 0, D, 0)
+    ax = np.zeros(n, np.int32)
+    ax[:m] = axonal
+    ax[m] = 1                      # the end of the chain fans out to two neurons
+    wl.update(pre=np.concatenate([np.arange(m), [m, m]]).astype(np.int32),
+              post=np.concatenate([np.arange(1, n - 2), [m + 1, m + 2]]).astype(np.int32),
+              weight=np.full(m + 2, 2.0), delay=np.array(list(delays) + [1, 2], np.int32), axonal_delay=ax)
+    t0 = 5
+    wl["events"] = dict(step=np.array([t0], np.int32), neuron=np.array([0], np.int32),
+                        value=np.array([2.0]))
+    hop = [d + a for d, a in zip(delays, axonal)]
+    steps = t0 + sum(hop) + 10
+    _, raster, _ = O.run(wl, mode, steps)
+    for k in range(m + 1):
+        assert list(np.nonzero(raster[:, k])[0]) == [t0 + sum(hop[:k])]
+    tm = t0 + sum(hop)
+    assert list(np.nonzero(raster[:, m + 1])[0]) == [tm + 1 + 1]
+    assert list(np.nonzero(raster[:, m + 2])[0]) == [tm + 1 + 2]
+    # all axonal delays 0: the plain network
+    wl0 = dict(wl, axonal_delay=np.zeros(n, np.int32))
+    wl1 = {k: v for k, v in wl.items() if k != "axonal_delay"}
+    assert np.array_equal(O.run(wl0, mode, steps)[1], O.run(wl1, mode, steps)[1])
+
+
 def _check_isi(raster, refr):
     for j in range(raster.shape[1]):
         t = np.nonzero(raster[:, j])[0]

@@ -32,8 +32,15 @@ def test_sampled_step_equals_full_step(seed):
     assert np.array_equal(row, want[0][J])
     assert np.array_equal(sv, st.v[J])
     assert np.array_equal(sr, st.r[J])
-    assert compare.check_sampled_dense_step(wl, t, J, v[J], r[J], spikers, wcols, want[0][J], st.v[J],
-                                            st.r[J]) == int(want[0][J].sum())
+    # the float64 trajectory likewise
+    s64 = O.state_from(wl, t, v, r, spk[None, :])
+    s64, want64, _ = O.run(wl, O.F64, 1, state=s64)
+    row64, sv64, sr64, _ = compare.sampled_dense_step(wl, t, J, v[J], r[J], spikers, wcols, mode=O.F64)
+    assert np.array_equal(row64, want64[0][J])
+    assert np.array_equal(sv64, s64.v[J])
+    assert np.array_equal(sr64, s64.r[J])
+    assert compare.check_sampled_dense_step(wl, t, J, v[J], r[J], spikers, wcols, want64[0][J], s64.v[J],
+                                            s64.r[J]) == int(want64[0][J].sum())
 
 
 def test_sampled_step_catches_a_wrong_weight():
