@@ -286,9 +286,15 @@ sn_status sn_get_weights(sn_ctx *ctx, float *w, int32_t on_device);
  * in input order, or n*n floats row-major for a dense network; Section 2.1's
  * synapse weights).  on_device = 1: `w` is a device pointer, copied on the
  * stream without validation; 0: host memory (NaN rejected with SN_EINVAL),
- * copied before the call returns.  Delays, the state and pending input are
- * kept; runs after the call use the new weights.  Dense contexts and SN_F32
- * sparse contexts (SN_EUNSUPPORTED for SN_I32, SN_ESTATE for other kinds). */
+ * copied before the call returns.  Delays and the state are kept.  A spike
+ * delivered at step t uses the weight in place at t (as in the oracle's
+ * delay registers): for a sparse context the call rebuilds the input of
+ * spikes still in flight from the raster, which must then hold the last
+ * max_delay steps (record_steps >= max_delay, else SN_EUNSUPPORTED); a dense
+ * context accepts new weights only at step 0 (after creation, sn_reset or an
+ * sn_load of a step-0 checkpoint; SN_ESTATE otherwise).  Dense contexts and
+ * SN_F32 sparse contexts (SN_EUNSUPPORTED for SN_I32, SN_ESTATE for other
+ * kinds). */
 sn_status sn_set_weights(sn_ctx *ctx, const float *w, int32_t on_device);
 
 /* Steps run so far, total spikes and total synaptic events (one event = one

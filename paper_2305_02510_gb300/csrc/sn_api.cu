@@ -680,6 +680,10 @@ sn_status sn_get_state(sn_ctx *c, void *v, int32_t *refr, int32_t on_device) {
     if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
     sn_status s;
     if (c->kind == KIND_FF) return fail(c, SN_ESTATE, "feedforward contexts: use sn_ff_get_checkpoints");
+    if (c->kind == KIND_SHARED_I8) {
+        if ((s = shared_get_state(c, v, refr, on_device))) return s;
+        return on_device ? SN_OK : read_status(c);
+    }
     const size_t bytes = (size_t)state_elems(c) * 4;
     if (v && (s = copy_out(c, v, c->V, bytes, on_device))) return s;
     if (refr && (s = copy_out(c, refr, c->r, bytes, on_device))) return s;
@@ -726,12 +730,50 @@ sn_status sn_get_weights(sn_ctx *c, float *w, int32_t on_device) {
     return SN_OK;
 }
 
+// Spikes in flight (emitted at step tau < t0, arriving at tau + d >= t0) are
+// delivered with the weights in place when they arrive.  After the weights
+// change, the pending input is rebuilt from the spike rows of the last D
+// steps (the raster): pull keeps them as its history, push re-sends them into
+// a cleared ring with the new weights.
+static sn_status rebuild_pending(sn_ctx *c) {
+    const long long t0 = c->step;
+    const int D = c->D;
+    const long long first = std::max<long long>(0, t0 - D);
+    if (first >= t0) return SN_OK;                      // nothing emitted yet
+    if (first < c->raster_from || t0 - first > c->cap)
+        return fail(c, SN_EUNSUPPORTED, "spikes in flight are older than the raster (record_steps < max_delay)");
+    const size_t row = (size_t)c->words * 4;
+    SN_CUDA(c, cudaMemsetAsync(c->hist, 0, (size_t)D * row, c->stream));
+    for (long long tau = first; tau < t0; ++tau)
+        SN_CUDA(c, cudaMemcpyAsync((char *)c->hist + (size_t)(tau % D) * row,
+                                   (const char *)c->raster + (size_t)(tau % c->cap) * row, row,
+                                   cudaMemcpyDeviceToDevice, c->stream));
+    SN_CUDA(c, cudaMemsetAsync(c->ring, 0, c->ring_bytes, c->stream));
+    if (c->prop_pull && !c->stdp) {
+        c->hist_live = true;
+        c->ring_live_until = t0;
+        return SN_OK;
+    }
+    NetArgs a;
+    memset(&a, 0, sizeof(a));
+    a.n = c->n; a.D1 = c->D1; a.words = c->words;
+    a.rowptr = c->rowptr; a.syn = c->syn; a.ring = c->ring; a.hist = c->hist; a.hD = D;
+    cudaError_t e = launch_pull_flush(a, c->dtype, (int)t0, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pending input rebuild");
+    SN_CUDA(c, cudaMemsetAsync(c->hist, 0, (size_t)D * row, c->stream));
+    c->hist_live = false;
+    c->ring_live_until = t0 + D;
+    return SN_OK;
+}
+
 sn_status sn_set_weights(sn_ctx *c, const float *w, int32_t on_device) {
     if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
     if (!w) return fail(c, SN_EINVAL, "w is NULL");
     if (c->failed) return fail(c, SN_ESTATE, "context is in an error state");
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (c->kind == KIND_DENSE) {
+        if (c->step != 0)
+            return fail(c, SN_ESTATE, "dense weights change only at step 0 (after creation, sn_reset or a load)");
         SN_CUDA(c, cudaMemcpyAsync(c->W, w, (size_t)c->n * c->n * 4, kind, c->stream));
         if (!on_device) SN_CUDA(c, cudaStreamSynchronize(c->stream));
         return SN_OK;
@@ -760,7 +802,7 @@ sn_status sn_set_weights(sn_ctx *c, const float *w, int32_t on_device) {
     dfree(c, tmp);
     if (e != cudaSuccess) return cuda_fail(c, e, "weight scatter");
     c->pin_stale = true;                       // the pull store holds copies of the weights
-    return SN_OK;
+    return rebuild_pending(c);
 }
 
 sn_status sn_get_counters(sn_ctx *c, int64_t *steps, int64_t *spikes, int64_t *events) {

@@ -141,6 +141,7 @@ struct SharedHostArgs {
 cudaError_t launch_shared(const void *tmaps, const SharedHostArgs &h, int grid, cudaStream_t s);
 cudaError_t max_grid_shared(int *grid);
 size_t shared_smem_bytes();
+cudaError_t launch_shared_transpose(const int *src, int *dst, int n, int B, cudaStream_t s);
 
 // Feedforward (BPTT) kernels, sn_ff.cu
 cudaError_t ff_pack(const uint8_t *in, int rows, int n, int words, unsigned *out, cudaStream_t s);

@@ -12,14 +12,18 @@
 //
 // Tile = 128 trains x 128 post-neurons, accumulated in TMEM over the K = n
 // pre-neurons in 128-byte stages loaded by TMA (128B swizzle, 6 stages).
-// Warp 0 lane 0 issues TMA, warp 1 lane 0 issues the MMAs; afterwards the eight
-// warps read the accumulator rows (tcgen05.ld: warps w and w+4 share TMEM lane
-// quarter w, each taking half of the columns) and apply the integer LIF rule
-// (Section 2.1 order), write the spike bytes that are the next step's A
-// operand, the raster bits and the state.  A persistent cooperative launch
-// runs all steps; a grid barrier separates them.  Every wait is bounded: on
-// expiry the kernel latches SN_ETIMEOUT, drains its own copies and MMAs,
-// frees its TMEM and returns.
+// Warp 0 lane 0 issues TMA, warp 1 lane 0 issues the MMAs; meanwhile warps
+// 2..7 draw the tile's Poisson input of step t (one bit per train and neuron)
+// and stage the tile's neuron parameters in shared memory.  Afterwards the
+// eight warps read the accumulator rows (tcgen05.ld: warps w and w+4 share TMEM
+// lane quarter w, each taking half of the columns) and apply the integer LIF
+// rule (Section 2.1 order).  The state is neuron-major ([n][B]: lane = train,
+// so every load and store of V and r is one 128-byte line per warp); the
+// spike bytes that are the next step's A operand go through a shared-memory
+// transpose and leave as whole 128-byte rows.  A persistent cooperative
+// launch runs all steps; a grid barrier separates them.  Every wait is
+// bounded: on expiry the kernel latches SN_ETIMEOUT, drains its own copies
+// and MMAs, frees its TMEM and returns.
 
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -37,6 +41,10 @@ constexpr int kStages = 6;
 constexpr int kStageA = kTM * kTK;             // 16 KiB
 constexpr int kStageBytes = (kTM + kTN) * kTK; // 32 KiB
 constexpr int kShThreads = 256;
+// epilogue staging after the pipeline stages: spike bytes [128][kSaPitch],
+// raster words and Poisson bits [128][4], parameters [5][128]
+constexpr int kSaPitch = 144;                  // 128 B + 16: conflict-free 16-byte stores
+constexpr int kEpiBytes = kTM * kSaPitch + 2 * kTM * 4 * 4 + 5 * kTN * 4;
 constexpr unsigned kTmemCols = 128;
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
@@ -124,7 +132,7 @@ struct SharedArgs {
     int n, B, t0, steps, cap, words;
     int tiles_m, tiles;
     unsigned char *A0, *A1;        // spike operands [B][n] bytes, A_(t & 1) holds step t
-    int *V, *r;                    // [B][n]
+    int *V, *r;                    // [n][B] (neuron-major)
     const int *th, *lk, *rs, *R;   // [n]
     const unsigned *prate;         // [n]
     const int *pamp;               // [n]
@@ -143,6 +151,11 @@ shared_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ 
     __shared__ int s_abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t sbase = smem_addr(smem);
+    unsigned char *sA = smem + kStages * kStageBytes;                 // [128][kSaPitch]
+    unsigned *sR = (unsigned *)(sA + kTM * kSaPitch);                 // [128][4] raster words
+    unsigned *sP = sR + kTM * 4;                                      // [128][4] Poisson bits
+    int *sTh = (int *)(sP + kTM * 4), *sLk = sTh + kTN, *sRs = sLk + kTN, *sRf = sRs + kTN,
+        *sAmp = sRf + kTN;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -206,6 +219,26 @@ shared_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ 
                     mma_commit(smem_addr(&empty[st]));
                 }
                 mma_commit(smem_addr(&accbar));
+            } else if (warp >= 2) {
+                // the tile's external input of step t and its parameters,
+                // while the tensor cores run
+                const int tid = threadIdx.x - 64;
+                for (int c = tid; c < kTN; c += kShThreads - 64) {
+                    const int j = n0 + c;
+                    sTh[c] = __ldg(a.th + j); sLk[c] = __ldg(a.lk + j); sRs[c] = __ldg(a.rs + j);
+                    sRf[c] = __ldg(a.R + j); sAmp[c] = __ldg(a.pamp + j);
+                }
+                for (int i = tid; i < kTM * 4; i += kShThreads - 64) {
+                    const int bl = i >> 2, w = i & 3;
+                    const unsigned long long key = __ldg(a.pkey + m0 + bl);
+                    unsigned bits = 0;
+                    for (int q = 0; q < 32; ++q) {
+                        const int j = n0 + w * 32 + q;
+                        const unsigned thr = __ldg(a.prate + j);
+                        if (thr && poisson_fires(key, (unsigned)t, (unsigned)j, thr)) bits |= 1u << q;
+                    }
+                    sP[i] = bits;
+                }
             }
             __syncwarp();
             // epilogue: warps w and w+4 own TMEM lanes (tile rows) 32(w%4) ..,
@@ -213,50 +246,71 @@ shared_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ 
             const bool ok = mbar_wait(smem_addr(&accbar), tiles_done & 1u, a.ctl);
             ++tiles_done;
             if (!ok) s_abort = 1;
-            __syncwarp();
+            __syncthreads();                   // Poisson bits and parameters staged
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             const int quarter = warp & 3, half = warp >> 2;
-            const int b = m0 + quarter * 32 + lane;
-            const unsigned long long key = a.pkey[b];
-            unsigned *rrow = a.raster + ((size_t)(t % a.cap) * a.B + b) * a.words;
-            for (int c = half * (kTN / 64); c < (half + 1) * (kTN / 64); ++c) {
+            const int bl = quarter * 32 + lane;            // tile row = TMEM lane
+            const int b = m0 + bl;
+            for (int cc = 0; cc < 2; ++cc) {
+                const int c0 = half * 64 + cc * 32;        // tile column of register 0
                 uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(c * 32), v);
+                tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
                 if (!ok) continue;
-                const int j0 = n0 + c * 32;
-                int4 *Vp = (int4 *)(a.V + (size_t)b * a.n + j0);
-                int4 *rp = (int4 *)(a.r + (size_t)b * a.n + j0);
+                const int j0 = n0 + c0;
+                // column q of this train at V[(j0 + q) * B + b]: two halves of
+                // 16 columns, loads of a half issued together
+                int *Vp = a.V + (size_t)j0 * a.B + b;
+                int *rp = a.r + (size_t)j0 * a.B + b;
+                const unsigned pb = sP[bl * 4 + (c0 >> 5)];
                 unsigned bits = 0;
                 uint32_t outw[8];
 #pragma unroll
-                for (int q4 = 0; q4 < 8; ++q4) {
-                    const int4 vv = Vp[q4], rr4 = rp[q4];
-                    const int4 th4 = __ldg((const int4 *)(a.th + j0) + q4), lk4 = __ldg((const int4 *)(a.lk + j0) + q4);
-                    const int4 rs4 = __ldg((const int4 *)(a.rs + j0) + q4), R4 = __ldg((const int4 *)(a.R + j0) + q4);
-                    int vin[4] = {vv.x, vv.y, vv.z, vv.w}, rin[4] = {rr4.x, rr4.y, rr4.z, rr4.w};
-                    const int thv[4] = {th4.x, th4.y, th4.z, th4.w}, lkv[4] = {lk4.x, lk4.y, lk4.z, lk4.w};
-                    const int rsv[4] = {rs4.x, rs4.y, rs4.z, rs4.w}, Rv[4] = {R4.x, R4.y, R4.z, R4.w};
-                    uint32_t bytes = 0;
+                for (int h = 0; h < 2; ++h) {
+                    int vin[16], rin[16];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const int q = q4 * 4 + e, j = j0 + q;
-                        const int acc = __float2int_rn(__uint_as_float(v[q]));
-                        int ext = 0;
-                        const unsigned thr = __ldg(a.prate + j);
-                        if (thr && poisson_fires(key, (unsigned)t, (unsigned)j, thr)) ext = __ldg(a.pamp + j);
-                        const bool fire = lif_update_i32(vin[e], rin[e], acc, ext, thv[e], lkv[e], rsv[e], Rv[e], overflow);
-                        bits |= (unsigned)fire << q;
-                        bytes |= (fire ? 0x38u : 0u) << (8 * e);      // E4M3 1.0
+                    for (int q = 0; q < 16; ++q) {
+                        vin[q] = __ldcg(Vp + (unsigned)((h * 16 + q) * a.B));
+                        rin[q] = __ldcg(rp + (unsigned)((h * 16 + q) * a.B));
                     }
-                    Vp[q4] = make_int4(vin[0], vin[1], vin[2], vin[3]);
-                    rp[q4] = make_int4(rin[0], rin[1], rin[2], rin[3]);
-                    outw[q4] = bytes;
+#pragma unroll
+                    for (int q4 = 0; q4 < 4; ++q4) {
+                        uint32_t bytes = 0;
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int qq = q4 * 4 + e, q = h * 16 + qq, c = c0 + q;
+                            const int acc = __float2int_rn(__uint_as_float(v[q]));
+                            const int ext = ((pb >> q) & 1u) ? sAmp[c] : 0;
+                            const bool fire = lif_update_i32(vin[qq], rin[qq], acc, ext, sTh[c], sLk[c], sRs[c],
+                                                             sRf[c], overflow);
+                            bits |= (unsigned)fire << q;
+                            bytes |= (fire ? 0x38u : 0u) << (8 * e);      // E4M3 1.0
+                        }
+                        outw[h * 4 + q4] = bytes;
+                    }
+#pragma unroll
+                    for (int q = 0; q < 16; ++q) {
+                        __stcg(Vp + (unsigned)((h * 16 + q) * a.B), vin[q]);
+                        __stcg(rp + (unsigned)((h * 16 + q) * a.B), rin[q]);
+                    }
                 }
-                uint4 *dst = (uint4 *)(Aout + (size_t)b * a.n + j0);
+                uint4 *dst = (uint4 *)(sA + bl * kSaPitch + c0);
                 dst[0] = make_uint4(outw[0], outw[1], outw[2], outw[3]);
                 dst[1] = make_uint4(outw[4], outw[5], outw[6], outw[7]);
-                rrow[j0 >> 5] = bits;
+                sR[bl * 4 + (c0 >> 5)] = bits;
                 my_spikes += (unsigned long long)__popc(bits);
+            }
+            __syncthreads();
+            if (ok) {
+                // spike bytes: 128-byte rows of A (the next step's operand);
+                // raster: the tile's four words of each train
+                for (int row = warp; row < kTM; row += kShThreads / 32)
+                    *(uint32_t *)(Aout + (size_t)(m0 + row) * a.n + n0 + lane * 4) =
+                        *(const uint32_t *)(sA + row * kSaPitch + lane * 4);
+                if (threadIdx.x < kTM) {
+                    const int row = threadIdx.x;
+                    *(uint4 *)(a.raster + ((size_t)(t % a.cap) * a.B + m0 + row) * a.words + (n0 >> 5)) =
+                        *(const uint4 *)(sR + row * 4);
+                }
             }
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             __syncthreads();
@@ -292,7 +346,21 @@ shared_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ 
     }
 }
 
-size_t shared_smem_bytes() { return (size_t)kStages * kStageBytes + 1024; }
+size_t shared_smem_bytes() { return (size_t)kStages * kStageBytes + kEpiBytes + 1024; }
+
+// [n][B] state -> [B][n] (the ABI's train-major order), 32 x 32 tiles
+__global__ void shared_transpose_kernel(const int *src, int *dst, int n, int B) {
+    __shared__ int tile[32][33];
+    const int j0 = blockIdx.x * 32, b0 = blockIdx.y * 32;
+    for (int y = threadIdx.y; y < 32; y += 8) tile[y][threadIdx.x] = src[(size_t)(j0 + y) * B + b0 + threadIdx.x];
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += 8) dst[(size_t)(b0 + y) * n + j0 + threadIdx.x] = tile[threadIdx.x][y];
+}
+
+cudaError_t launch_shared_transpose(const int *src, int *dst, int n, int B, cudaStream_t s) {
+    shared_transpose_kernel<<<dim3(n / 32, B / 32), dim3(32, 8), 0, s>>>(src, dst, n, B);
+    return cudaGetLastError();
+}
 
 cudaError_t max_grid_shared(int *grid) {
     int dev = 0, sms = 0, per = 0;

@@ -55,6 +55,28 @@ sn_status shared_run(sn_ctx *c, int steps) {
     return SN_OK;
 }
 
+// State in the ABI's order [trains][n] from the kernel's [n][trains].
+sn_status shared_get_state(sn_ctx *c, void *v, int32_t *refr, int32_t on_device) {
+    const size_t bn = (size_t)c->sh_B * c->n;
+    int *tmp = nullptr;
+    sn_status s = SN_OK;
+    if (!on_device && (s = dalloc(c, &tmp, bn * 4))) return s;
+    void *outs[2] = {v, refr};
+    const int *src[2] = {(const int *)c->V, c->r};
+    for (int k = 0; k < 2 && s == SN_OK; ++k) {
+        if (!outs[k]) continue;
+        int *dst = on_device ? (int *)outs[k] : tmp;
+        cudaError_t e = launch_shared_transpose(src[k], dst, c->n, c->sh_B, c->stream);
+        if (e == cudaSuccess && !on_device) {
+            e = cudaMemcpyAsync(outs[k], tmp, bn * 4, cudaMemcpyDeviceToHost, c->stream);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        }
+        if (e != cudaSuccess) s = cuda_fail(c, e, "state transpose");
+    }
+    dfree(c, tmp);
+    return s;
+}
+
 sn_status shared_set_poisson(sn_ctx *c, int32_t nsrc, const int32_t *neuron, const float *rate,
                              const float *amp, uint64_t seed) {
     const int n = c->n;
@@ -126,9 +148,10 @@ extern "C" sn_status sn_create_shared_dense_i8(const sn_config *cfg, const sn_ne
         for (int v = -8; v <= 8; ++v) lut[v + 8] = e4m3_of_int(v);
         for (int i = 0; i < n; ++i)
             for (int j = 0; j < n; ++j) wt[(size_t)j * n + i] = lut[w[(size_t)i * n + j] + 8];
+        // the kernel keeps the state neuron-major, [n][trains]
         std::vector<int> v0(bn);
-        for (int b = 0; b < trains; ++b)
-            for (int j = 0; j < n; ++j) v0[(size_t)b * n + j] = (int)nr->reset[j];
+        for (int j = 0; j < n; ++j)
+            for (int b = 0; b < trains; ++b) v0[(size_t)j * trains + b] = (int)nr->reset[j];
         std::vector<unsigned long long> keys(trains);
         for (int b = 0; b < trains; ++b) keys[b] = host_splitmix64(0ull ^ host_splitmix64((unsigned long long)b));
         cudaError_t e;
