@@ -743,6 +743,10 @@ static sn_status rebuild_pending(sn_ctx *c) {
     if (first < c->raster_from || t0 - first > c->cap)
         return fail(c, SN_EUNSUPPORTED, "spikes in flight are older than the raster (record_steps < max_delay)");
     const size_t row = (size_t)c->words * 4;
+    if (!c->hist) {
+        sn_status s = dalloc(c, &c->hist, (size_t)D * row);
+        if (s) return s;
+    }
     SN_CUDA(c, cudaMemsetAsync(c->hist, 0, (size_t)D * row, c->stream));
     for (long long tau = first; tau < t0; ++tau)
         SN_CUDA(c, cudaMemcpyAsync((char *)c->hist + (size_t)(tau % D) * row,
