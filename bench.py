@@ -226,6 +226,7 @@ def extras(S, W, torch, stream, flush):
     plain_ms = a.elapsed_time(b2)
     plain_ev = sum(S.sn_get_counters(c)[2] for c in plain)
     del plain
+    res["tiny"] = tiny_extra(S, W, torch, stream, flush)
     res["paper_grid"] = paper_grid_extra(S, W, torch, stream, flush)
     res["huge_dense"] = huge_dense_extra(S, W, torch, stream, flush)
     res["bptt"] = bptt_extra(S, W, torch, stream)
@@ -319,6 +320,15 @@ def bptt_extra(S, W, torch, stream):
         return a.elapsed_time(b) / reps
 
     ms = timed(ours, 3, 10)
+    net_simt = bptt.FFNet.from_task(task, engine="simt")
+
+    def ours_simt():
+        for w in ws:
+            w.grad = None
+        counts = bptt.SNNFunction.apply(net_simt, x, *ws)
+        torch.nn.functional.cross_entropy(counts, labels).backward()
+
+    simt_ms = timed(ours_simt, 3, 10)
     masks = [[torch.tensor(task["delay"][l] == d, device=dev, dtype=torch.float32) for d in range(1, 5)]
              for l in range(len(ws))]
     spike = _Spike.make(torch)
@@ -334,6 +344,8 @@ def bptt_extra(S, W, torch, stream):
     syn = sum(a * b for a, b in zip(sizes[:-1], sizes[1:]))
     return {"workload": "700-1024-1024-20 LIF, per-synapse delays 1..4, batch 128, 100 steps, "
                         "checkpoint every 10", "synapses": syn, "ms_per_training_step": ms,
+            "engine": "forward FP32 SIMT (exact simulator), backward contractions on tcgen05 BF16 tensor cores",
+            "simt_backward_ms_per_training_step": simt_ms,
             "plain_torch_ms_per_training_step": plain_ms, "speedup_vs_plain_torch": plain_ms / ms}
 
 
@@ -392,6 +404,24 @@ PAPER_TABLE2 = {
 }
 GRID_N = (100, 1000, 10000)
 GRID_P = (0.25, 0.5, 0.75, 1.0)
+
+
+def tiny_extra(S, W, torch, stream, flush):
+    """The tiny network (100 neurons, p = 0.05, delays 1..4, Poisson input
+    into 10 neurons), float and integer copies, 1000 timesteps in one launch:
+    a latency-bound run reported in timesteps/s."""
+    out = {}
+    for integer in (False, True):
+        wl = W.tiny(integer=integer, steps=1000)
+        ctx = S.from_workload(wl, record_steps=1000, stream=stream.cuda_stream)
+        S.sn_autotune(ctx, 1000)
+        prop = "pull" if S.sn_get_propagation(ctx) == S.SN_PULL else "push"
+        ms, spk, ev = timed_runs(S, torch, stream, flush, ctx, 1000, 3)
+        out["int" if integer else "float"] = {
+            "workload": wl["name"], "ms": ms, "timesteps_per_s": 1000 / (ms / 1e3),
+            "synaptic_events_per_s": ev / (ms / 1e3), "spikes_per_timestep": spk / 1000, "propagation": prop}
+        del ctx
+    return out
 
 
 def huge_dense_extra(S, W, torch, stream, flush, n=100_000, steps=1000):

@@ -360,6 +360,20 @@ sn_status sn_ff_forward(sn_ctx *ctx, const uint8_t *input, const float *const *w
  * receive dLoss/dW_l.  on_device must be 1. */
 sn_status sn_backward(sn_ctx *ctx, const float *grad_counts, float *const *grad_w, int32_t on_device);
 
+/* Engine of the backward contractions (weight gradient, spike gradient):
+ * SN_FF_SIMT (CUDA-core FP32; the weight gradient exploits spike sparsity)
+ * or SN_FF_TENSOR (tcgen05 BF16 tensor cores: one GEMM per delay with the
+ * weights of that delay; FP32 weights and gradients enter as two-part BF16
+ * splits, about 16 significant bits per factor, relative error near 2^-16
+ * per product).  SN_FF_AUTO (the default) takes the tensor cores where the
+ * shapes allow (batch a multiple of 8); SN_FF_TENSOR on shapes that do not
+ * fit returns SN_EUNSUPPORTED.  The forward pass (and its recomputation in
+ * sn_backward) is the exact FP32 simulator on either engine. */
+#define SN_FF_AUTO 0
+#define SN_FF_SIMT 1
+#define SN_FF_TENSOR 2
+sn_status sn_ff_set_engine(sn_ctx *ctx, int32_t engine);
+
 /* Spikes of layer l (0 = input) of the last forward: [steps][batch][ceil(n_l/32)]
  * words.  Membrane checkpoints of layer l >= 1: [steps/k][batch][n_l] floats,
  * entry c = state after step (c+1)k - 1. */

@@ -94,6 +94,12 @@ struct sn_ctx {
     float *ff_I = nullptr, *ff_gI = nullptr, *ff_gS = nullptr, *ff_part = nullptr;
     std::vector<const float *> ff_w;   // weights of the last forward (caller's device memory)
     bool ff_have_forward = false;
+    // tensor-core contractions (sn_ff_tc.cu): engine choice and BF16 operands
+    int ff_engine = 0;                 // SN_FF_AUTO, SN_FF_SIMT or SN_FF_TENSOR
+    bool ff_tc_ok = false;             // the shapes fit the tensor-core path
+    void *ff_ST = nullptr, *ff_G = nullptr, *ff_GT = nullptr;
+    std::vector<void *> ff_Wb;         // backward weight parts per layer
+    void *ff_encode = nullptr;         // the driver's cuTensorMapEncodeTiled
     // shared dense network driven by many trains (tensor cores)
     int sh_B = 0, sh_grid = 0;
     unsigned char *sh_A0 = nullptr, *sh_A1 = nullptr, *sh_WT = nullptr;

@@ -484,4 +484,9 @@ cudaError_t ff_dw(const float *gI, const unsigned *sprev, int words_in, const ui
     return cudaGetLastError();
 }
 
+cudaError_t ff_dw_reduce(const float *part, int splits, long long count, float *dW, cudaStream_t s) {
+    ff_dw_reduce_kernel<<<blocks_for(count, 256), 256, 0, s>>>(part, splits, count, dW);
+    return cudaGetLastError();
+}
+
 }  // namespace sn

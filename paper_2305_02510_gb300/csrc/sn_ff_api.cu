@@ -9,9 +9,155 @@
 #include <string>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "sn_ctx.h"
 
+namespace sn {
+namespace {
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+inline int up(int x, int m) { return (x + m - 1) / m * m; }
+
+// Row-major BF16 [rows][cols] (cols a multiple of 64), boxes of 128 rows x 64
+// columns, 128-byte swizzle; coordinates outside the tensor read as zero.
+sn_status bf16_map(sn_ctx *c, CUtensorMap *out, const void *base, long long rows, long long cols) {
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {64, 128};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = ((EncodeTiledFn)c->ff_encode)(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)base, dims, strides,
+                                               box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(c, SN_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return SN_OK;
+}
+
+bool use_tc(const sn_ctx *c) { return c->ff_tc_ok && c->ff_engine != SN_FF_SIMT; }
+
+// Weight gradient of layer l from gI (already split and transposed into GT)
+// and the transposed spikes ST: 4 delays x 2 gradient parts, one accumulator
+// per delay, split over K (the rows) to fill the GPU, then reduced in order.
+sn_status tc_weight_grad(sn_ctx *c, int l, float *dW) {
+    const int B = c->ff_batch, rows = B * c->ff_steps;
+    const int nin = c->ff_sizes[l - 1], nout = c->ff_sizes[l];
+    const int rows_p = up(rows, 64);
+    FfTcMaps maps;
+    FfTcArgs a;
+    memset(&maps, 0, sizeof(maps));
+    memset(&a, 0, sizeof(a));
+    sn_status s;
+    const __nv_bfloat16 *GT = (const __nv_bfloat16 *)c->ff_GT;
+    if ((s = bf16_map(c, &maps.m[0], c->ff_ST, nin, rows_p)) ||
+        (s = bf16_map(c, &maps.m[1], GT, nout, rows_p)) ||
+        (s = bf16_map(c, &maps.m[2], GT + (size_t)nout * rows_p, nout, rows_p)))
+        return s;
+    for (int d = 1; d <= 4; ++d)
+        for (int p = 0; p < 2; ++p) {
+            FfTcPass &ps = a.pass[a.npass++];
+            ps.amap = 0; ps.a_y = 0; ps.a_x = -d * B;
+            ps.bmap = 1 + p; ps.b_y = 0; ps.b_x = 0;
+            ps.kblocks = rows_p / 64; ps.acc = d - 1;
+        }
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    a.M = nin; a.N = nout;
+    a.tiles_m = (nin + 127) / 128; a.tiles_n = (nout + 127) / 128;
+    const int tiles = a.tiles_m * a.tiles_n;
+    int ks = std::max(1, std::min({sms / std::max(1, tiles), c->ff_splits, rows_p / 64 / 8}));
+    a.ksplit = ks;
+    a.nacc = 4; a.mode = 1; a.D = c->ff_D[l - 1]; a.ldc = nout; a.ctl = c->ctl;
+    const long long count = (long long)nin * nout;
+    a.C = ks == 1 ? dW : c->ff_part;
+    a.cstride = count;
+    cudaError_t e = ff_tc_gemm(maps, a, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tensor-core weight gradient");
+    if (ks > 1 && (e = ff_dw_reduce(c->ff_part, ks, count, dW, c->stream)) != cudaSuccess)
+        return cuda_fail(c, e, "weight gradient reduction");
+    return SN_OK;
+}
+
+// Gradient of the spikes of layer l-1: gS[r][i] = sum_d sum_j gI[r + dB][j] W_d[i][j],
+// with the two-part splits hi*hi + hi*mid + mid*hi: 12 passes.
+sn_status tc_spike_grad(sn_ctx *c, int l) {
+    const int B = c->ff_batch, rows = B * c->ff_steps;
+    const int nin = c->ff_sizes[l - 1], nout = c->ff_sizes[l];
+    const int nout_p = up(nout, 64), rows_in = up(nin, 128);
+    FfTcMaps maps;
+    FfTcArgs a;
+    memset(&maps, 0, sizeof(maps));
+    memset(&a, 0, sizeof(a));
+    sn_status s;
+    const __nv_bfloat16 *G = (const __nv_bfloat16 *)c->ff_G;
+    if ((s = bf16_map(c, &maps.m[0], G, rows, nout_p)) ||
+        (s = bf16_map(c, &maps.m[1], G + (size_t)rows * nout_p, rows, nout_p)) ||
+        (s = bf16_map(c, &maps.m[2], c->ff_Wb[l - 1], 8LL * rows_in, nout_p)))
+        return s;
+    static const int ga[3] = {0, 0, 1}, wb[3] = {0, 1, 0};   // (gradient part, weight part)
+    for (int d = 1; d <= 4; ++d)
+        for (int p = 0; p < 3; ++p) {
+            FfTcPass &ps = a.pass[a.npass++];
+            ps.amap = ga[p]; ps.a_y = d * B; ps.a_x = 0;
+            ps.bmap = 2; ps.b_y = ((d - 1) * 2 + wb[p]) * rows_in; ps.b_x = 0;
+            ps.kblocks = nout_p / 64; ps.acc = 0;
+        }
+    a.M = rows; a.N = nin;
+    a.tiles_m = (rows + 127) / 128; a.tiles_n = (nin + 127) / 128; a.ksplit = 1;
+    a.nacc = 1; a.mode = 0; a.C = c->ff_gS; a.ldc = nin; a.cstride = 0; a.ctl = c->ctl;
+    cudaError_t e = ff_tc_gemm(maps, a, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "tensor-core spike gradient");
+    return SN_OK;
+}
+
+// Allocate the BF16 operand buffers and look up the tensor-map encoder; on
+// any failure the context keeps the SIMT engine only.
+void tc_setup(sn_ctx *c) {
+    const int L = c->ff_layers, B = c->ff_batch, rows = B * c->ff_steps;
+    if (B % 8 != 0) return;                    // delay shifts of d * B rows must stay 16-byte aligned in K
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+        return;
+    c->ff_encode = fn;
+    const int rows_p = up(rows, 64);
+    size_t st_elems = 0, g_elems = 0, gt_elems = 0;
+    c->ff_Wb.assign(L, nullptr);
+    for (int l = 1; l <= L; ++l) {
+        const int nin = c->ff_sizes[l - 1], nout = c->ff_sizes[l];
+        st_elems = std::max(st_elems, (size_t)nin * rows_p);
+        g_elems = std::max(g_elems, (size_t)2 * rows * up(nout, 64));
+        gt_elems = std::max(gt_elems, (size_t)2 * nout * rows_p);
+        if (dalloc(c, &c->ff_Wb[l - 1], (size_t)8 * up(nin, 128) * up(nout, 64) * 2)) return;
+    }
+    if (dalloc(c, &c->ff_ST, st_elems * 2) || dalloc(c, &c->ff_G, g_elems * 2) || dalloc(c, &c->ff_GT, gt_elems * 2))
+        return;
+    // padding columns and rows of the operands stay zero from here on
+    if (cudaMemset(c->ff_ST, 0, st_elems * 2) || cudaMemset(c->ff_G, 0, g_elems * 2) ||
+        cudaMemset(c->ff_GT, 0, gt_elems * 2))
+        return;
+    c->ff_tc_ok = true;
+}
+
+}  // namespace
+}  // namespace sn
+
 extern "C" {
+
+sn_status sn_ff_set_engine(sn_ctx *c, int32_t engine) {
+    if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
+    if (c->kind != KIND_FF) return fail(c, SN_ESTATE, "not a feedforward context");
+    if (engine != SN_FF_AUTO && engine != SN_FF_SIMT && engine != SN_FF_TENSOR)
+        return fail(c, SN_EINVAL, "unknown engine");
+    if (engine == SN_FF_TENSOR && !c->ff_tc_ok)
+        return fail(c, SN_EUNSUPPORTED, "the tensor-core engine needs a batch that is a multiple of 8");
+    c->ff_engine = engine;
+    return SN_OK;
+}
 
 sn_status sn_create_ff(const sn_config *cfg, int32_t layers, const int32_t *sizes, const uint8_t *const *delays,
                        const sn_ff_params *p, int32_t batch, int32_t steps, sn_ctx **out) {
@@ -102,6 +248,8 @@ sn_status sn_create_ff(const sn_config *cfg, int32_t layers, const int32_t *size
         return bail(s);
     if (cudaMemset(c->ctl, 0, sizeof(Control)) != cudaSuccess) return bail(SN_ECUDA);
     c->ff_w.assign(layers, nullptr);
+    tc_setup(c);
+    c->err.clear();
     *out = c;
     return SN_OK;
 }
@@ -139,10 +287,12 @@ sn_status sn_backward(sn_ctx *c, const float *grad_counts, float *const *grad_w,
     const int B = c->ff_batch, T = c->ff_steps, L = c->ff_layers;
     const int rows = B * T;
     cudaError_t e;
+    for (int l = 1; l <= L; ++l)
+        if (!grad_w[l - 1]) return fail(c, SN_EINVAL, "gradient pointer is NULL");
+    const bool tc = use_tc(c);
     for (int l = L; l >= 1; --l) {
         const int nin = c->ff_sizes[l - 1], nout = c->ff_sizes[l];
         const int words_in = (nin + 31) / 32;
-        if (!grad_w[l - 1]) return fail(c, SN_EINVAL, "gradient pointer is NULL");
         // recompute the synaptic input (the forward kept only spikes and checkpoints)
         if ((e = ff_delay_fwd(c->ff_S[l - 1], words_in, c->ff_w[l - 1], c->ff_DM[l - 1], nin, nout, B, 0, rows,
                               c->ff_I, c->stream)))
@@ -151,6 +301,19 @@ sn_status sn_backward(sn_ctx *c, const float *grad_counts, float *const *grad_w,
                              c->ff_slope, c->ff_vck[l], c->ff_rck[l], l == L ? nullptr : c->ff_gS,
                              l == L ? grad_counts : nullptr, c->ff_gI, c->stream)))
             return cuda_fail(c, e, "adjoint recurrence");
+        if (tc) {
+            const int nout_p = (nout + 63) / 64 * 64, rows_p = (rows + 63) / 64 * 64;
+            if ((e = ff_tc_spikes(c->ff_S[l - 1], rows, nin, words_in, rows_p, c->ff_ST, c->stream)) ||
+                (e = ff_tc_gsplit(c->ff_gI, rows, nout, nout_p, rows_p, l > 1 ? c->ff_G : nullptr, c->ff_GT,
+                                  c->stream)) ||
+                (l > 1 && (e = ff_tc_weights(c->ff_w[l - 1], c->ff_D[l - 1], nin, nout, nout_p,
+                                             (nin + 127) / 128 * 128, c->ff_Wb[l - 1], c->stream))))
+                return cuda_fail(c, e, "tensor-core operands");
+            sn_status st = tc_weight_grad(c, l, grad_w[l - 1]);
+            if (st) return st;
+            if (l > 1 && (st = tc_spike_grad(c, l))) return st;
+            continue;
+        }
         if ((e = ff_dw(c->ff_gI, c->ff_S[l - 1], words_in, c->ff_D[l - 1], nin, nout, B, T, c->ff_splits,
                        c->ff_part, grad_w[l - 1], c->stream)))
             return cuda_fail(c, e, "weight gradient");

@@ -1,0 +1,311 @@
+// Tensor-core (tcgen05, BF16 operands, FP32 accumulation in TMEM) contractions
+// of the feedforward network's backward pass (sn_ff.cu has the forward, the
+// recurrences and the SIMT forms of these contractions).
+//
+// A delay-shifted contraction is a sum of plain GEMMs, one per delay d, with
+// the weights restricted to the synapses of delay d (W_d = W masked by
+// [D == d]) and the gradient or spike rows shifted by d steps (d * B rows):
+//   gS[r][i] = sum_d sum_j gI[r + dB][j] W_d[i][j]
+//   dW[i][j] = sum_d [D[i][j] = d] sum_r S[r - dB][i] gI[r][j]
+// with r = t * B + b, rows outside [0, T * B) contributing zero (TMA fills
+// coordinates outside a tensor with zeros).  FP32 weights and gradients enter
+// as two-term BF16 splits x = hi + mid (about 16 significant bits), spikes as
+// exact 0/1, and the cross products hi*hi + hi*mid + mid*hi are accumulated in
+// FP32 (relative error near 2^-16 per product).  The forward pass stays on the
+// SIMT kernels: the tensor cores' FP32 accumulation drifts by more than the
+// state tolerance over 100 integrated steps.
+//
+// One kernel runs a list of passes, each a K loop of 64-element (128-byte)
+// blocks of an A and a B tensor map at given coordinate offsets, into one of
+// up to four TMEM accumulators of a 128 x 128 output tile.  The structure is
+// that of sn_shared.cu: warp 0 lane 0 issues TMA into a 6-stage ring, warp 1
+// lane 0 issues the MMAs, then all eight warps drain the accumulators through
+// shared memory into coalesced FP32 rows.  Work items are (tile, K split)
+// pairs taken by a persistent grid; every wait is bounded.
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sn_internal.h"
+#include "sn_tc.cuh"
+
+namespace sn {
+
+namespace {
+
+constexpr int kT = 128;                         // tile rows (M) and columns (N)
+constexpr int kKB = 64;                         // BF16 elements of K per stage (128 bytes)
+constexpr int kSt = 6;
+constexpr int kStageA = kT * 128;               // 16 KiB
+constexpr int kStageBytes = 2 * kStageA;        // 32 KiB
+constexpr int kThreads = 256;
+constexpr int kCPitch = kT + 4;                 // floats per staged output row
+
+__global__ void __launch_bounds__(kThreads, 1) ff_tc_kernel(const __grid_constant__ FfTcMaps maps, FfTcArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full[kSt], empty[kSt], accbar;
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort, s_started;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t sbase = smem_addr(smem);
+    const unsigned ncols = a.nacc <= 1 ? 128u : a.nacc == 2 ? 256u : 512u;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kSt; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(smem_addr(&full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(smem_addr(&empty[s])));
+        }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(smem_addr(&accbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        s_abort = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
+                     :: "r"(smem_addr(&s_tmem)), "r"(ncols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    constexpr uint32_t idesc = idesc_bf16_f32(kT, kT);
+    unsigned g_prod = 0, g_mma = 0, items_done = 0;
+    const int items = a.tiles_m * a.tiles_n * a.ksplit;
+
+    for (int item = blockIdx.x; item < items && !s_abort; item += gridDim.x) {
+        const int ks = item % a.ksplit, tile = item / a.ksplit;
+        const int tm = tile % a.tiles_m, tn = tile / a.tiles_m;
+        if (warp == 0 && lane == 0) {
+            // TMA producer over every pass's K blocks of this split
+            for (int p = 0; p < a.npass && !s_abort; ++p) {
+                const FfTcPass &ps = a.pass[p];
+                const int kb0 = (int)((long long)ps.kblocks * ks / a.ksplit);
+                const int kb1 = (int)((long long)ps.kblocks * (ks + 1) / a.ksplit);
+                for (int kb = kb0; kb < kb1; ++kb, ++g_prod) {
+                    const int st = g_prod % kSt;
+                    const unsigned round = g_prod / kSt;
+                    if (round > 0 && !mbar_wait(smem_addr(&empty[st]), (round - 1) & 1u, a.ctl)) {
+                        s_abort = 1;
+                        break;
+                    }
+                    const uint32_t fb = smem_addr(&full[st]);
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
+                                 :: "r"(fb), "r"(kStageBytes) : "memory");
+                    const uint32_t dA = sbase + st * kStageBytes;
+                    tma_load_2d(dA, &maps.m[ps.amap], ps.a_x + kb * kKB, ps.a_y + tm * kT, fb);
+                    tma_load_2d(dA + kStageA, &maps.m[ps.bmap], ps.b_x + kb * kKB, ps.b_y + tn * kT, fb);
+                }
+            }
+        } else if (warp == 1 && lane == 0) {
+            // MMA issuer; an accumulator's first MMA of this item overwrites it
+            int started = 0;
+            for (int p = 0; p < a.npass && !s_abort; ++p) {
+                const FfTcPass &ps = a.pass[p];
+                const int kb0 = (int)((long long)ps.kblocks * ks / a.ksplit);
+                const int kb1 = (int)((long long)ps.kblocks * (ks + 1) / a.ksplit);
+                const uint32_t tacc = tmem + (uint32_t)(ps.acc * kT);
+                for (int kb = kb0; kb < kb1; ++kb, ++g_mma) {
+                    const int st = g_mma % kSt;
+                    const unsigned round = g_mma / kSt;
+                    if (!mbar_wait(smem_addr(&full[st]), round & 1u, a.ctl)) { s_abort = 1; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    const uint32_t dA = sbase + st * kStageBytes;
+#pragma unroll
+                    for (int kk = 0; kk < 128 / 32; ++kk) {
+                        const int on = ((started >> ps.acc) & 1) | (kk > 0);
+                        mma_bf16(tacc, umma_desc_sw128(dA + kk * 32), umma_desc_sw128(dA + kStageA + kk * 32),
+                                 idesc, on);
+                    }
+                    started |= 1 << ps.acc;
+                    mma_commit(smem_addr(&empty[st]));
+                }
+            }
+            s_started = started;
+            mma_commit(smem_addr(&accbar));
+        }
+        __syncwarp();
+        const bool ok = mbar_wait(smem_addr(&accbar), items_done & 1u, a.ctl);
+        ++items_done;
+        if (!ok) s_abort = 1;
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        // epilogue: warps w and w+4 read TMEM lane quarter w (tile rows), each
+        // half of the columns; values go to a staged tile in the (now idle)
+        // pipeline buffers, then leave as coalesced rows
+        float *Cs = (float *)smem;                  // [128][kCPitch]
+        const int quarter = warp & 3, half = warp >> 2;
+        const int ml = quarter * 32 + lane, m = tm * kT + ml;
+        const int started = s_started;
+        for (int cc = 0; cc < 2; ++cc) {
+            const int c0 = half * 64 + cc * 32;
+            const int n0 = tn * kT + c0;
+            float out[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) out[q] = 0.0f;
+            const int nacc = a.mode == 1 ? a.nacc : 1;
+            for (int d = 0; d < nacc; ++d) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(d * kT + c0), v);
+                if (!ok || !((started >> d) & 1)) continue;
+                if (a.mode == 0) {
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) out[q] = __uint_as_float(v[q]);
+                } else if (m < a.M) {
+                    // the weight gradient of (m, n) is that of its own delay
+                    const uint8_t *Dr = a.D + (size_t)m * a.N;
+#pragma unroll
+                    for (int q = 0; q < 32; ++q)
+                        if (n0 + q < a.N && Dr[n0 + q] == d + 1) out[q] = __uint_as_float(v[q]);
+                }
+            }
+            float4 *dst = (float4 *)(Cs + ml * kCPitch + c0);
+#pragma unroll
+            for (int q4 = 0; q4 < 8; ++q4)
+                dst[q4] = make_float4(out[4 * q4], out[4 * q4 + 1], out[4 * q4 + 2], out[4 * q4 + 3]);
+        }
+        __syncthreads();
+        if (ok) {
+            float *C = a.C + (size_t)ks * a.cstride;
+            const int ncol = min(kT, a.N - tn * kT);
+            for (int row = warp; row < kT; row += kThreads / 32) {
+                const int mm = tm * kT + row;
+                if (mm >= a.M) break;
+                float *crow = C + (size_t)mm * a.ldc + tn * kT;
+                const float *srow = Cs + row * kCPitch;
+                for (int c = lane; c < ncol; c += 32) crow[c] = srow[c];
+            }
+        }
+        // the staged tile was written and read through the generic proxy; the
+        // next item's TMA (async proxy) reuses those bytes
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncthreads();
+    }
+
+    // drain: copies issued and MMAs committed complete before shared memory and
+    // TMEM go away (bounded waits; no-ops when the phases have completed)
+    if (warp == 0 && lane == 0) {
+        for (unsigned i = g_prod > kSt ? g_prod - kSt : 0; i < g_prod; ++i)
+            mbar_wait(smem_addr(&full[i % kSt]), (i / kSt) & 1u, a.ctl);
+    }
+    if (warp == 1 && lane == 0) {
+        for (unsigned i = g_mma > kSt ? g_mma - kSt : 0; i < g_mma; ++i)
+            mbar_wait(smem_addr(&empty[i % kSt]), (i / kSt) & 1u, a.ctl);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(tmem), "r"(ncols));
+}
+
+// Weight parts of the backward: Wb[(d-1)*2 + s] = part s (hi, mid) of W_d
+// ([rows_in][nout_p], rows_in = n_in rounded up to 128); the buffer starts
+// zeroed.
+__global__ void ff_tc_weights_kernel(const float *__restrict__ W, const uint8_t *__restrict__ D, int n_in,
+                                     int n_out, int nout_p, int rows_in, __nv_bfloat16 *Wb) {
+    const long long cnt = (long long)n_in * n_out;
+    const size_t bsz = (size_t)rows_in * nout_p;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(q / n_out), j = (int)(q % n_out);
+        const int d = D[q];
+        const float w = W[q];
+        const __nv_bfloat16 hi = __float2bfloat16_rn(w);
+        const __nv_bfloat16 mid = __float2bfloat16_rn(__fsub_rn(w, __bfloat162float(hi)));
+        const size_t b = (size_t)i * nout_p + j;
+        Wb[(size_t)((d - 1) * 2 + 0) * bsz + b] = hi;
+        Wb[(size_t)((d - 1) * 2 + 1) * bsz + b] = mid;
+    }
+}
+
+// Spike bits [rows][words] -> transposed 0/1 BF16 [n_in][rows_p] (padding
+// stays zero).
+__global__ void ff_tc_spikes_kernel(const unsigned *__restrict__ bits, int rows, int n_in, int words, int rows_p,
+                                    __nv_bfloat16 *ST) {
+    const long long cnt = (long long)rows * n_in;
+    const __nv_bfloat16 one = __float2bfloat16_rn(1.0f), zero = __float2bfloat16_rn(0.0f);
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(q / n_in), i = (int)(q % n_in);
+        const bool s = (bits[(size_t)r * words + (i >> 5)] >> (i & 31)) & 1u;
+        ST[(size_t)i * rows_p + r] = s ? one : zero;
+    }
+}
+
+// Gradient gI [rows][n_out] -> two-term BF16 split G[s] ([rows][nout_p]) and,
+// if GT is given, its transpose GT[s] ([n_out][rows_p]).
+__global__ void ff_tc_gsplit_kernel(const float *__restrict__ g, int rows, int n_out, int nout_p, int rows_p,
+                                    __nv_bfloat16 *G, __nv_bfloat16 *GT) {
+    const long long cnt = (long long)rows * n_out;
+    const size_t gsz = (size_t)rows * nout_p, tsz = (size_t)n_out * rows_p;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(q / n_out), j = (int)(q % n_out);
+        const float x = g[q];
+        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+        const __nv_bfloat16 mid = __float2bfloat16_rn(__fsub_rn(x, __bfloat162float(hi)));
+        if (G) {
+            G[(size_t)r * nout_p + j] = hi;
+            G[gsz + (size_t)r * nout_p + j] = mid;
+        }
+        if (GT) {
+            GT[(size_t)j * rows_p + r] = hi;
+            GT[tsz + (size_t)j * rows_p + r] = mid;
+        }
+    }
+}
+
+int grid_for(long long work) {
+    long long b = (work + 255) / 256;
+    if (b > 8192) b = 8192;
+    return (int)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+size_t ff_tc_smem_bytes() { return (size_t)kSt * kStageBytes + 1024; }
+
+cudaError_t ff_tc_gemm(const FfTcMaps &maps, const FfTcArgs &args, cudaStream_t s) {
+    static_assert(kT * kCPitch * 4 <= kSt * kStageBytes, "staged output tile fits the stage buffers");
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const size_t smem = ff_tc_smem_bytes();
+    if ((e = cudaFuncSetAttribute((const void *)ff_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) != cudaSuccess)
+        return e;
+    const int items = args.tiles_m * args.tiles_n * args.ksplit;
+    const int grid = items < sms ? items : sms;
+    ff_tc_kernel<<<grid, kThreads, smem, s>>>(maps, args);
+    return cudaGetLastError();
+}
+
+cudaError_t ff_tc_weights(const float *W, const uint8_t *D, int n_in, int n_out, int nout_p, int rows_in,
+                          void *Wb, cudaStream_t s) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(Wb, 0, (size_t)8 * rows_in * nout_p * 2, s)) != cudaSuccess) return e;
+    ff_tc_weights_kernel<<<grid_for((long long)n_in * n_out), 256, 0, s>>>(W, D, n_in, n_out, nout_p, rows_in,
+                                                                        (__nv_bfloat16 *)Wb);
+    return cudaGetLastError();
+}
+
+cudaError_t ff_tc_spikes(const unsigned *bits, int rows, int n_in, int words, int rows_p, void *ST,
+                         cudaStream_t s) {
+    ff_tc_spikes_kernel<<<grid_for((long long)rows * n_in), 256, 0, s>>>(bits, rows, n_in, words, rows_p,
+                                                                       (__nv_bfloat16 *)ST);
+    return cudaGetLastError();
+}
+
+cudaError_t ff_tc_gsplit(const float *g, int rows, int n_out, int nout_p, int rows_p, void *G, void *GT,
+                         cudaStream_t s) {
+    ff_tc_gsplit_kernel<<<grid_for((long long)rows * n_out), 256, 0, s>>>(
+        g, rows, n_out, nout_p, rows_p, (__nv_bfloat16 *)G, (__nv_bfloat16 *)GT);
+    return cudaGetLastError();
+}
+
+}  // namespace sn

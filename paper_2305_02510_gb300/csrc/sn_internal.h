@@ -2,6 +2,7 @@
 // translation units.  Not part of the public ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -156,6 +157,38 @@ cudaError_t ff_bwd_data(const float *gI, const float *W, const uint8_t *D, int n
                         float *gsp, cudaStream_t s);
 cudaError_t ff_dw(const float *gI, const unsigned *sprev, int words_in, const uint8_t *D, int n_in, int n_out,
                   int B, int T, int splits, float *part, float *dW, cudaStream_t s);
+
+// Tensor-core contractions of the feedforward network (sn_ff_tc.cu).  A pass
+// is a K loop over `kblocks` 64-element blocks: A tile rows a_y + 128 * tm,
+// K a_x + 64 * kb of map amap; B tile rows b_y + 128 * tn, K b_x + 64 * kb of
+// map bmap; into accumulator acc.  mode 0: C[m][n] = acc 0; mode 1: C[m][n] =
+// acc (D[m][n] - 1) (delay-selected weight gradient).  With ksplit > 1 the
+// work item of split ks covers its share of every pass's K blocks and writes
+// C + ks * cstride.
+constexpr int kFfTcMaxMaps = 4;
+constexpr int kFfTcMaxPasses = 16;
+struct FfTcMaps {
+    CUtensorMap m[kFfTcMaxMaps];
+};
+struct FfTcPass {
+    int amap, bmap, a_y, a_x, b_y, b_x, kblocks, acc;
+};
+struct FfTcArgs {
+    int M, N, tiles_m, tiles_n, ksplit, npass, nacc, mode;
+    FfTcPass pass[kFfTcMaxPasses];
+    float *C;
+    long long ldc, cstride;
+    const uint8_t *D;
+    Control *ctl;
+};
+cudaError_t ff_tc_gemm(const FfTcMaps &maps, const FfTcArgs &args, cudaStream_t s);
+cudaError_t ff_tc_weights(const float *W, const uint8_t *D, int n_in, int n_out, int nout_p, int rows_in,
+                          void *Wb, cudaStream_t s);
+cudaError_t ff_tc_spikes(const unsigned *bits, int rows, int n_in, int words, int rows_p, void *ST,
+                         cudaStream_t s);
+cudaError_t ff_tc_gsplit(const float *g, int rows, int n_out, int nout_p, int rows_p, void *G, void *GT,
+                         cudaStream_t s);
+cudaError_t ff_dw_reduce(const float *part, int splits, long long count, float *dW, cudaStream_t s);
 
 // Launchers (kernels live in sn_kernels.cu).  Return a CUDA error code.
 cudaError_t launch_sparse(const NetArgs &a, int dtype, int grid, int block, cudaStream_t s);

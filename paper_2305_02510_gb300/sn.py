@@ -21,6 +21,7 @@ SN_OK, SN_EINVAL, SN_ENOMEM, SN_ECUDA, SN_ESTATE, SN_ETIMEOUT, SN_EUNSUPPORTED, 
 SN_F32, SN_I32 = 0, 1
 SN_AUTO, SN_EXEC_CTA, SN_EXEC_GRID, SN_PROP_PULL = 0, 1, 2, 4
 SN_PUSH, SN_PULL = 0, 1
+SN_FF_AUTO, SN_FF_SIMT, SN_FF_TENSOR = 0, 1, 2
 _NAMES = ["SN_OK", "SN_EINVAL", "SN_ENOMEM", "SN_ECUDA", "SN_ESTATE", "SN_ETIMEOUT",
           "SN_EUNSUPPORTED", "SN_EOVERFLOW"]
 
@@ -92,6 +93,7 @@ def lib():
                 "sn_ff_forward": [_P, _P, _P, _P],
                 "sn_backward": [_P, _P, _P, C.c_int32],
                 "sn_ff_get_spikes": [_P, C.c_int32, _P, C.c_int32],
+                "sn_ff_set_engine": [_P, C.c_int32],
                 "sn_ff_get_checkpoints": [_P, C.c_int32, _P, C.c_int32],
                 "sn_set_input": [_P, C.c_int64, _P, _P, _P],
                 "sn_set_poisson": [_P, C.c_int32, _P, _P, _P, C.c_uint64],
@@ -447,6 +449,10 @@ def sn_create_ff(sizes, delays, *, threshold, leak, reset, refractory, slope, ch
     ctx = Ctx(h, int(sz[-1]), SN_F32, 0, "ff", 0)
     ctx.sizes, ctx.batch, ctx.steps, ctx.k = [int(x) for x in sz], int(batch), int(steps), int(checkpoint_every)
     return ctx
+
+
+def sn_ff_set_engine(ctx: Ctx, engine: int):
+    _check(lib().sn_ff_set_engine(ctx.handle, int(engine)), ctx)
 
 
 def sn_ff_forward(ctx: Ctx, input_spikes, weights, counts):

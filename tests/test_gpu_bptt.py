@@ -31,9 +31,9 @@ def built():
     g.build()
 
 
-def run_gpu(task):
+def run_gpu(task, engine=None):
     from paper_2305_02510_gb300 import bptt, sn as S
-    net = bptt.FFNet.from_task(task)
+    net = bptt.FFNet.from_task(task, engine=engine)
     dev = torch.device("cuda")
     x = torch.tensor(task["input"], device=dev)
     ws = [torch.tensor(w, device=dev, requires_grad=True) for w in task["w"]]
@@ -108,10 +108,25 @@ def compare_grads(g_gpu, g_ref, level, near):
     (3, 20, (50, 40, 5), 2, 45),
 ])
 def test_bptt_small_free_running(seed, k, sizes, B, T):
+    check_small_free_running(seed, k, sizes, B, T, None)
+
+
+@pytest.mark.parametrize("seed,k,sizes,B,T", [
+    (4, 10, (40, 48, 36, 6), 8, 30),
+    (5, 5, (130, 200, 20, 7), 16, 25),
+    (6, 20, (64, 129, 10), 8, 40),
+])
+def test_bptt_small_free_running_tensor(seed, k, sizes, B, T):
+    """The tensor-core engine (batches that are multiples of 8), ragged sizes
+    across 64-column and 128-row tile edges."""
+    check_small_free_running(seed, k, sizes, B, T, "tensor")
+
+
+def check_small_free_running(seed, k, sizes, B, T, engine):
     task = W.bptt_task(batch=B, sizes=sizes, steps=T, seed=seed)
     task["w"] = [w * 1.5 for w in task["w"]]
     task["checkpoint_every"] = k
-    loss, counts, grads, spikes, ck = run_gpu(task)
+    loss, counts, grads, spikes, ck = run_gpu(task, engine)
     ref_loss, ref_counts, ref_grads = R.gradients(task)
     ws = [torch.tensor(w, dtype=torch.float64) for w in task["w"]]
     _, ref_spikes, ref_pre = R.forward(task, ws, record=True)
@@ -125,9 +140,10 @@ def test_bptt_small_free_running(seed, k, sizes, B, T):
     compare_grads(grads, ref_grads, fp32_level(task, None), near)
 
 
-def test_bptt_full_size_teacher_forced():
+@pytest.mark.parametrize("engine", ["simt", "tensor"])
+def test_bptt_full_size_teacher_forced(engine):
     task = W.bptt_task()           # 700-1024-1024-20, batch 128, 100 steps, k = 10
-    loss, counts, grads, spikes, ck = run_gpu(task)
+    loss, counts, grads, spikes, ck = run_gpu(task, engine)
     T, L = task["steps"], len(task["sizes"]) - 1
     given = [[torch.tensor(spikes[l + 1][t], dtype=torch.float64) for t in range(T)] for l in range(L)]
     ws = [torch.tensor(w, dtype=torch.float64, requires_grad=True) for w in task["w"]]
