@@ -360,15 +360,18 @@ sn_status sn_ff_forward(sn_ctx *ctx, const uint8_t *input, const float *const *w
  * receive dLoss/dW_l.  on_device must be 1. */
 sn_status sn_backward(sn_ctx *ctx, const float *grad_counts, float *const *grad_w, int32_t on_device);
 
-/* Engine of the backward contractions (weight gradient, spike gradient):
- * SN_FF_SIMT (CUDA-core FP32; the weight gradient exploits spike sparsity)
- * or SN_FF_TENSOR (tcgen05 BF16 tensor cores: one GEMM per delay with the
- * weights of that delay; FP32 weights and gradients enter as two-part BF16
- * splits, about 16 significant bits per factor, relative error near 2^-16
- * per product).  SN_FF_AUTO (the default) takes the tensor cores where the
- * shapes allow (batch a multiple of 8); SN_FF_TENSOR on shapes that do not
- * fit returns SN_EUNSUPPORTED.  The forward pass (and its recomputation in
- * sn_backward) is the exact FP32 simulator on either engine. */
+/* Engine of the contractions (synaptic input, weight gradient, spike
+ * gradient): SN_FF_SIMT (CUDA-core FP32; exploits spike sparsity) or
+ * SN_FF_TENSOR (tcgen05 BF16 tensor cores: one GEMM per delay with the
+ * weights of that delay).  On the tensor cores the forward multiplies 0/1
+ * spikes by an exact three-part BF16 split of every weight and adds the
+ * partial sums of each 64-input block in FP32 (so forward states differ from
+ * the SIMT engine's only in the order of FP32 additions); the backward uses
+ * two-part BF16 splits of weights and gradients (about 16 significant bits
+ * per factor, relative error near 2^-16 per product).  SN_FF_AUTO (the
+ * default) takes the tensor cores where the shapes allow (batch a multiple
+ * of 8); SN_FF_TENSOR on shapes that do not fit returns SN_EUNSUPPORTED.
+ * sn_backward always uses the engine of the forward it differentiates. */
 #define SN_FF_AUTO 0
 #define SN_FF_SIMT 1
 #define SN_FF_TENSOR 2

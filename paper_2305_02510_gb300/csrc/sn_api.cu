@@ -134,7 +134,7 @@ sn_status build_pull_store(sn_ctx *c) {
 sn_status select_pull(sn_ctx *c) {
     if (c->stdp) return fail(c, SN_EUNSUPPORTED, "STDP runs on push propagation");
     if (c->pull_grid == 0) {
-        cudaError_t e = plan_pull(c->n, c->D, &c->pull_grid, &c->pull_chunk, &c->pull_rows, &c->pull_smem);
+        cudaError_t e = plan_pull(c->n, c->D, c->m, &c->pull_grid, &c->pull_chunk, &c->pull_rows, &c->pull_smem);
         if (e != cudaSuccess) return cuda_fail(c, e, "pull executor");
         if (c->pull_grid == 0)
             return fail(c, SN_EUNSUPPORTED,

@@ -97,8 +97,9 @@ struct sn_ctx {
     // tensor-core contractions (sn_ff_tc.cu): engine choice and BF16 operands
     int ff_engine = 0;                 // SN_FF_AUTO, SN_FF_SIMT or SN_FF_TENSOR
     bool ff_tc_ok = false;             // the shapes fit the tensor-core path
-    void *ff_ST = nullptr, *ff_G = nullptr, *ff_GT = nullptr;
-    std::vector<void *> ff_Wb;         // backward weight parts per layer
+    bool ff_fwd_tc = false;            // the last forward ran on the tensor cores
+    void *ff_Sbf = nullptr, *ff_ST = nullptr, *ff_G = nullptr, *ff_GT = nullptr;
+    std::vector<void *> ff_Wf, ff_Wb;  // forward and backward weight parts per layer
     void *ff_encode = nullptr;         // the driver's cuTensorMapEncodeTiled
     // shared dense network driven by many trains (tensor cores)
     int sh_B = 0, sh_grid = 0;

@@ -39,40 +39,45 @@ __device__ __forceinline__ int ld_status(const Control *ctl) {
     return *(volatile const int *)&ctl->status;
 }
 
-// Grid-wide barrier for a cooperative launch.  Returns false if the wait gave
-// up (wall-clock limit or a status latched by another block); the caller then
-// leaves its time loop.
+// Grid-wide barrier for a cooperative launch, on a counter that only grows
+// during a launch (the host zeroes it before every launch): thread 0 of each
+// block adds one with release semantics and waits until the count reaches the
+// next multiple of the grid size.  No block can arrive at barrier e + 1
+// before every block has arrived at barrier e, so the count a block sees on
+// arrival lies in [e * grid, (e + 1) * grid) and fixes its target.
+__device__ __forceinline__ unsigned bar_arrive(Control *ctl) {
+    unsigned old;
+    asm volatile("atom.add.release.gpu.u32 %0, [%1], 1;" : "=r"(old) : "l"(&ctl->bar.count) : "memory");
+    return (old / gridDim.x + 1u) * gridDim.x;
+}
+
+// Thread 0: wait until the count reaches `target` (bounded: wall-clock limit,
+// or a status latched by another block).  Returns false if it gave up.
+__device__ __forceinline__ bool bar_wait(Control *ctl, unsigned target) {
+    const unsigned long long t_start = global_timer_ns();
+    unsigned spins = 0;
+    while ((int)(ld_acquire_u32(&ctl->bar.count) - target) < 0) {
+        if ((++spins & 63u) == 0) {
+            if (ld_status(ctl) != 0) return false;
+            if (global_timer_ns() - t_start > kBarrierTimeoutNs) {
+                atomicCAS(&ctl->status, 0, (int)SN_ETIMEOUT);
+                return false;
+            }
+        }
+        __nanosleep(32);
+    }
+    return true;
+}
+
+// Whole-block grid barrier.  Returns false if the wait gave up (wall-clock
+// limit or a status latched by another block); the caller then leaves its
+// time loop.
 __device__ inline bool grid_barrier(Control *ctl) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        if (gridDim.x > 1) {
-            GridBarrier *b = &ctl->bar;
-            unsigned gen = ld_acquire_u32(&b->gen);
-            __threadfence();
-            unsigned arrived = atomicAdd(&b->count, 1u);
-            if (arrived == gridDim.x - 1) {
-                atomicExch(&b->count, 0u);
-                __threadfence();
-                atomicAdd(&b->gen, 1u);
-            } else {
-                unsigned long long t_start = global_timer_ns();
-                unsigned spins = 0;
-                while (ld_acquire_u32(&b->gen) == gen) {
-                    if ((++spins & 63u) == 0) {
-                        if (ld_status(ctl) != 0) { ok = 0; break; }
-                        if (global_timer_ns() - t_start > kBarrierTimeoutNs) {
-                            atomicCAS(&ctl->status, 0, (int)SN_ETIMEOUT);
-                            ok = 0;
-                            break;
-                        }
-                    }
-                    __nanosleep(40);
-                }
-            }
-            __threadfence();
-        }
+        if (gridDim.x > 1) ok = bar_wait(ctl, bar_arrive(ctl)) ? 1 : 0;
         s_ok = ok;
     }
     __syncthreads();

@@ -38,6 +38,39 @@ sn_status bf16_map(sn_ctx *c, CUtensorMap *out, const void *base, long long rows
 
 bool use_tc(const sn_ctx *c) { return c->ff_tc_ok && c->ff_engine != SN_FF_SIMT; }
 
+// Synaptic input of layer l for all rows, I[r][j] = sum_d sum_i S[r - dB][i] W_d[i][j]:
+// 4 delays x 3 exact BF16 weight parts = 12 passes, accumulated block by block
+// (ff_tc_forward).  Unpacks the previous layer's spikes, and their transpose
+// when the weight gradient will need it.
+sn_status tc_forward(sn_ctx *c, int l, bool want_st) {
+    const int B = c->ff_batch, rows = B * c->ff_steps;
+    const int nin = c->ff_sizes[l - 1], nout = c->ff_sizes[l];
+    const int nin_p = up(nin, 64), rows_out = up(nout, 128), rows_p = up(rows, 64);
+    cudaError_t e = ff_tc_spikes(c->ff_S[l - 1], rows, nin, (nin + 31) / 32, nin_p, rows_p, c->ff_Sbf,
+                                 want_st ? c->ff_ST : nullptr, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "spike operands");
+    FfTcMaps maps;
+    FfTcArgs a;
+    memset(&maps, 0, sizeof(maps));
+    memset(&a, 0, sizeof(a));
+    sn_status s;
+    if ((s = bf16_map(c, &maps.m[0], c->ff_Sbf, rows, nin_p)) ||
+        (s = bf16_map(c, &maps.m[1], c->ff_Wf[l - 1], 12LL * rows_out, nin_p)))
+        return s;
+    for (int d = 1; d <= 4; ++d)
+        for (int p = 0; p < 3; ++p) {
+            FfTcPass &ps = a.pass[a.npass++];
+            ps.amap = 0; ps.a_y = -d * B; ps.a_x = 0;
+            ps.bmap = 1; ps.b_y = ((d - 1) * 3 + p) * rows_out; ps.b_x = 0;
+            ps.kblocks = nin_p / 64; ps.acc = 0;
+        }
+    a.M = rows; a.N = nout;
+    a.tiles_m = (rows + 127) / 128; a.tiles_n = (nout + 127) / 128; a.ksplit = 1;
+    a.nacc = 1; a.mode = 0; a.C = c->ff_I; a.ldc = nout; a.cstride = 0; a.ctl = c->ctl;
+    if ((e = ff_tc_forward(maps, a, c->stream)) != cudaSuccess) return cuda_fail(c, e, "tensor-core synaptic input");
+    return SN_OK;
+}
+
 // Weight gradient of layer l from gI (already split and transposed into GT)
 // and the transposed spikes ST: 4 delays x 2 gradient parts, one accumulator
 // per delay, split over K (the rows) to fill the GPU, then reduced in order.
@@ -125,20 +158,27 @@ void tc_setup(sn_ctx *c) {
         return;
     c->ff_encode = fn;
     const int rows_p = up(rows, 64);
-    size_t st_elems = 0, g_elems = 0, gt_elems = 0;
+    size_t s_elems = 0, st_elems = 0, g_elems = 0, gt_elems = 0;
+    c->ff_Wf.assign(L, nullptr);
     c->ff_Wb.assign(L, nullptr);
     for (int l = 1; l <= L; ++l) {
         const int nin = c->ff_sizes[l - 1], nout = c->ff_sizes[l];
+        s_elems = std::max(s_elems, (size_t)rows * up(nin, 64));
         st_elems = std::max(st_elems, (size_t)nin * rows_p);
         g_elems = std::max(g_elems, (size_t)2 * rows * up(nout, 64));
         gt_elems = std::max(gt_elems, (size_t)2 * nout * rows_p);
-        if (dalloc(c, &c->ff_Wb[l - 1], (size_t)8 * up(nin, 128) * up(nout, 64) * 2)) return;
+        if (dalloc(c, &c->ff_Wf[l - 1], (size_t)12 * up(nout, 128) * up(nin, 64) * 2) ||
+            dalloc(c, &c->ff_Wb[l - 1], (size_t)8 * up(nin, 128) * up(nout, 64) * 2))
+            return;
     }
-    if (dalloc(c, &c->ff_ST, st_elems * 2) || dalloc(c, &c->ff_G, g_elems * 2) || dalloc(c, &c->ff_GT, gt_elems * 2))
+    if (dalloc(c, &c->ff_Sbf, s_elems * 2) || dalloc(c, &c->ff_ST, st_elems * 2) || dalloc(c, &c->ff_G, g_elems * 2) ||
+        dalloc(c, &c->ff_GT, gt_elems * 2))
         return;
-    // padding columns and rows of the operands stay zero from here on
-    if (cudaMemset(c->ff_ST, 0, st_elems * 2) || cudaMemset(c->ff_G, 0, g_elems * 2) ||
-        cudaMemset(c->ff_GT, 0, gt_elems * 2))
+    // padding columns and rows of the operands stay zero from here on (the
+    // spike rows' padding may later hold 0/1 values of a wider layer, which
+    // meet zero weight columns)
+    if (cudaMemset(c->ff_Sbf, 0, s_elems * 2) || cudaMemset(c->ff_ST, 0, st_elems * 2) ||
+        cudaMemset(c->ff_G, 0, g_elems * 2) || cudaMemset(c->ff_GT, 0, gt_elems * 2))
         return;
     c->ff_tc_ok = true;
 }
@@ -264,12 +304,23 @@ sn_status sn_ff_forward(sn_ctx *c, const uint8_t *input, const float *const *w, 
     const int rows = B * T;
     cudaError_t e = ff_pack(input, rows, c->ff_sizes[0], (c->ff_sizes[0] + 31) / 32, c->ff_S[0], c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "input pack");
+    const bool tc = use_tc(c);
+    c->ff_fwd_tc = tc;
     for (int l = 1; l <= L; ++l) {
         const int nin = c->ff_sizes[l - 1], nout = c->ff_sizes[l];
         c->ff_w[l - 1] = w[l - 1];
-        if ((e = ff_delay_fwd(c->ff_S[l - 1], (nin + 31) / 32, w[l - 1], c->ff_DM[l - 1], nin, nout, B, 0, rows,
-                              c->ff_I, c->stream)))
+        if (tc) {
+            // weight parts for this forward and the matching backward
+            if ((e = ff_tc_weights(w[l - 1], c->ff_D[l - 1], nin, nout, (nout + 63) / 64 * 64, (nin + 127) / 128 * 128,
+                                   l > 1 ? c->ff_Wb[l - 1] : nullptr, (nin + 63) / 64 * 64, (nout + 127) / 128 * 128,
+                                   c->ff_Wf[l - 1], c->stream)))
+                return cuda_fail(c, e, "weight parts");
+            sn_status st = tc_forward(c, l, false);
+            if (st) return st;
+        } else if ((e = ff_delay_fwd(c->ff_S[l - 1], (nin + 31) / 32, w[l - 1], c->ff_DM[l - 1], nin, nout, B, 0,
+                                     rows, c->ff_I, c->stream))) {
             return cuda_fail(c, e, "forward synaptic input");
+        }
         if ((e = ff_scan_fwd(c->ff_I, nout, B, T, c->ff_k, c->ff_theta, c->ff_leak, c->ff_reset, c->ff_refr,
                              c->ff_S[l], c->ff_vck[l], c->ff_rck[l], l == L ? counts : nullptr, c->stream)))
             return cuda_fail(c, e, "forward recurrence");
@@ -289,26 +340,28 @@ sn_status sn_backward(sn_ctx *c, const float *grad_counts, float *const *grad_w,
     cudaError_t e;
     for (int l = 1; l <= L; ++l)
         if (!grad_w[l - 1]) return fail(c, SN_EINVAL, "gradient pointer is NULL");
-    const bool tc = use_tc(c);
+    const bool tc = c->ff_fwd_tc;              // the engine of the forward being differentiated
     for (int l = L; l >= 1; --l) {
         const int nin = c->ff_sizes[l - 1], nout = c->ff_sizes[l];
         const int words_in = (nin + 31) / 32;
-        // recompute the synaptic input (the forward kept only spikes and checkpoints)
-        if ((e = ff_delay_fwd(c->ff_S[l - 1], words_in, c->ff_w[l - 1], c->ff_DM[l - 1], nin, nout, B, 0, rows,
-                              c->ff_I, c->stream)))
+        // recompute the synaptic input (the forward kept only spikes and
+        // checkpoints) with the forward's own kernel, so the states match
+        if (tc) {
+            sn_status st = tc_forward(c, l, true);
+            if (st) return st;
+        } else if ((e = ff_delay_fwd(c->ff_S[l - 1], words_in, c->ff_w[l - 1], c->ff_DM[l - 1], nin, nout, B, 0,
+                                     rows, c->ff_I, c->stream))) {
             return cuda_fail(c, e, "recompute synaptic input");
+        }
         if ((e = ff_scan_bwd(c->ff_I, nout, B, T, c->ff_k, c->ff_theta, c->ff_leak, c->ff_reset, c->ff_refr,
                              c->ff_slope, c->ff_vck[l], c->ff_rck[l], l == L ? nullptr : c->ff_gS,
                              l == L ? grad_counts : nullptr, c->ff_gI, c->stream)))
             return cuda_fail(c, e, "adjoint recurrence");
         if (tc) {
             const int nout_p = (nout + 63) / 64 * 64, rows_p = (rows + 63) / 64 * 64;
-            if ((e = ff_tc_spikes(c->ff_S[l - 1], rows, nin, words_in, rows_p, c->ff_ST, c->stream)) ||
-                (e = ff_tc_gsplit(c->ff_gI, rows, nout, nout_p, rows_p, l > 1 ? c->ff_G : nullptr, c->ff_GT,
-                                  c->stream)) ||
-                (l > 1 && (e = ff_tc_weights(c->ff_w[l - 1], c->ff_D[l - 1], nin, nout, nout_p,
-                                             (nin + 127) / 128 * 128, c->ff_Wb[l - 1], c->stream))))
-                return cuda_fail(c, e, "tensor-core operands");
+            if ((e = ff_tc_gsplit(c->ff_gI, rows, nout, nout_p, rows_p, l > 1 ? c->ff_G : nullptr, c->ff_GT,
+                                  c->stream)))
+                return cuda_fail(c, e, "gradient parts");
             sn_status st = tc_weight_grad(c, l, grad_w[l - 1]);
             if (st) return st;
             if (l > 1 && (st = tc_spike_grad(c, l))) return st;

@@ -11,9 +11,17 @@
 // coordinates outside a tensor with zeros).  FP32 weights and gradients enter
 // as two-term BF16 splits x = hi + mid (about 16 significant bits), spikes as
 // exact 0/1, and the cross products hi*hi + hi*mid + mid*hi are accumulated in
-// FP32 (relative error near 2^-16 per product).  The forward pass stays on the
-// SIMT kernels: the tensor cores' FP32 accumulation drifts by more than the
-// state tolerance over 100 integrated steps.
+// FP32 (relative error near 2^-16 per product).
+//
+// The forward synaptic input I[r][j] = sum_d sum_i S[r - dB][i] W_d[i][j] runs
+// as 12 passes (4 delays x the three BF16 parts hi + mid + lo of each weight,
+// an exact split) over 0/1 spikes, so every product is exact.  Accumulating a
+// whole K loop in TMEM drifts: the tensor cores' FP32 accumulation lost enough
+// that 100-step membrane checkpoints left the state tolerance.  The forward
+// kernel therefore accumulates one 64-input block of all 12 passes at a time
+// in TMEM (double-buffered) and adds each block's partial sums in FP32 (round
+// to nearest) in registers of dedicated drain warps, as a sequential sum over
+// input blocks.
 //
 // One kernel runs a list of passes, each a K loop of 64-element (128-byte)
 // blocks of an A and a B tensor map at given coordinate offsets, into one of
@@ -202,37 +210,201 @@ __global__ void __launch_bounds__(kThreads, 1) ff_tc_kernel(const __grid_constan
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(tmem), "r"(ncols));
 }
 
-// Weight parts of the backward: Wb[(d-1)*2 + s] = part s (hi, mid) of W_d
-// ([rows_in][nout_p], rows_in = n_in rounded up to 128); the buffer starts
-// zeroed.
+// Forward synaptic input with block-wise accumulation.  384 threads: warp 0
+// lane 0 issues TMA (K block outer, pass inner), warp 1 lane 0 issues the
+// MMAs of one K block of every pass into TMEM buffer (block & 1) and commits
+// it to accf[buf]; warps 4..11 (warp w: TMEM lane quarter w % 4, columns
+// 64 * ((w - 4) / 4) ..+63) add each block's partial into FP32 registers and
+// release the buffer through acce[buf] (8 arrivals).  Every pass has the
+// same number of K blocks; a.C[m][n] = the sum (mode 0 layout).
+constexpr int kFwdTcThreads = 384;
+
+__global__ void __launch_bounds__(kFwdTcThreads, 1) ff_tc_fwd_kernel(const __grid_constant__ FfTcMaps maps,
+                                                                     FfTcArgs a) {
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ __align__(8) uint64_t full[kSt], empty[kSt], accf[2], acce[2];
+    __shared__ uint32_t s_tmem;
+    __shared__ int s_abort;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t sbase = smem_addr(smem);
+    constexpr unsigned ncols = 256;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kSt; ++s) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(smem_addr(&full[s])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(smem_addr(&empty[s])));
+        }
+        for (int b = 0; b < 2; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(smem_addr(&accf[b])));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 8;\n" :: "r"(smem_addr(&acce[b])));
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        s_abort = 0;
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
+                     :: "r"(smem_addr(&s_tmem)), "r"(ncols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = s_tmem;
+    constexpr uint32_t idesc = idesc_bf16_f32(kT, kT);
+    const int items = a.tiles_m * a.tiles_n;
+    const int KB = a.pass[0].kblocks;
+    unsigned g_prod = 0, g_mma = 0;
+
+    if (warp == 0 && lane == 0) {
+        for (int item = blockIdx.x; item < items && !s_abort; item += gridDim.x) {
+            const int tm = item % a.tiles_m, tn = item / a.tiles_m;
+            for (int kb = 0; kb < KB && !s_abort; ++kb)
+                for (int p = 0; p < a.npass; ++p, ++g_prod) {
+                    const FfTcPass &ps = a.pass[p];
+                    const int st = g_prod % kSt;
+                    const unsigned round = g_prod / kSt;
+                    if (round > 0 && !mbar_wait(smem_addr(&empty[st]), (round - 1) & 1u, a.ctl)) {
+                        s_abort = 1;
+                        break;
+                    }
+                    const uint32_t fb = smem_addr(&full[st]);
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
+                                 :: "r"(fb), "r"(kStageBytes) : "memory");
+                    const uint32_t dA = sbase + st * kStageBytes;
+                    tma_load_2d(dA, &maps.m[ps.amap], ps.a_x + kb * kKB, ps.a_y + tm * kT, fb);
+                    tma_load_2d(dA + kStageA, &maps.m[ps.bmap], ps.b_x + kb * kKB, ps.b_y + tn * kT, fb);
+                }
+        }
+    } else if (warp == 1 && lane == 0) {
+        unsigned g_chunk = 0;
+        for (int item = blockIdx.x; item < items && !s_abort; item += gridDim.x)
+            for (int kb = 0; kb < KB && !s_abort; ++kb, ++g_chunk) {
+                const unsigned buf = g_chunk & 1u, use = g_chunk >> 1;
+                if (use > 0 && !mbar_wait(smem_addr(&acce[buf]), (use - 1) & 1u, a.ctl)) { s_abort = 1; break; }
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint32_t tacc = tmem + buf * kT;
+                for (int p = 0; p < a.npass; ++p, ++g_mma) {
+                    const int st = g_mma % kSt;
+                    const unsigned round = g_mma / kSt;
+                    if (!mbar_wait(smem_addr(&full[st]), round & 1u, a.ctl)) { s_abort = 1; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                    const uint32_t dA = sbase + st * kStageBytes;
+#pragma unroll
+                    for (int kk = 0; kk < 128 / 32; ++kk)
+                        mma_bf16(tacc, umma_desc_sw128(dA + kk * 32), umma_desc_sw128(dA + kStageA + kk * 32), idesc,
+                                 (p > 0) | (kk > 0));
+                    mma_commit(smem_addr(&empty[st]));
+                }
+                mma_commit(smem_addr(&accf[buf]));
+            }
+    } else if (warp >= 4) {
+        const int quarter = warp & 3, half = (warp - 4) >> 2;
+        unsigned g_chunk = 0;
+        for (int item = blockIdx.x; item < items && !s_abort; item += gridDim.x) {
+            const int tm = item % a.tiles_m, tn = item / a.tiles_m;
+            float acc[64];
+#pragma unroll
+            for (int q = 0; q < 64; ++q) acc[q] = 0.0f;
+            bool ok = true;
+            for (int kb = 0; kb < KB; ++kb, ++g_chunk) {
+                const unsigned buf = g_chunk & 1u, use = g_chunk >> 1;
+                ok = ok && mbar_wait(smem_addr(&accf[buf]), use & 1u, a.ctl);
+                __syncwarp();
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    uint32_t v[32];
+                    tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + buf * kT + (uint32_t)(half * 64 + h * 32), v);
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) acc[h * 32 + q] = __fadd_rn(acc[h * 32 + q], __uint_as_float(v[q]));
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" :: "r"(smem_addr(&acce[buf])) : "memory");
+                if (!ok) break;
+            }
+            if (!ok) { s_abort = 1; break; }
+            const int m = tm * kT + quarter * 32 + lane;
+            const int n0 = tn * kT + half * 64;
+            if (m < a.M) {
+                float *crow = a.C + (size_t)m * a.ldc;
+                if (n0 + 64 <= a.N && (a.ldc & 3) == 0) {
+#pragma unroll
+                    for (int q4 = 0; q4 < 16; ++q4)
+                        *(float4 *)(crow + n0 + 4 * q4) =
+                            make_float4(acc[4 * q4], acc[4 * q4 + 1], acc[4 * q4 + 2], acc[4 * q4 + 3]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 64; ++q)
+                        if (n0 + q < a.N) crow[n0 + q] = acc[q];
+                }
+            }
+        }
+    }
+    __syncwarp();
+
+    // drain: copies issued and MMAs committed complete before shared memory and
+    // TMEM go away (bounded waits; no-ops when the phases have completed)
+    if (warp == 0 && lane == 0) {
+        for (unsigned i = g_prod > kSt ? g_prod - kSt : 0; i < g_prod; ++i)
+            mbar_wait(smem_addr(&full[i % kSt]), (i / kSt) & 1u, a.ctl);
+    }
+    if (warp == 1 && lane == 0) {
+        for (unsigned i = g_mma > kSt ? g_mma - kSt : 0; i < g_mma; ++i)
+            mbar_wait(smem_addr(&empty[i % kSt]), (i / kSt) & 1u, a.ctl);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(tmem), "r"(ncols));
+}
+
+// Weight parts: Wb[(d-1)*2 + s] = part s (hi, mid) of W_d ([rows_in][nout_p],
+// rows_in = n_in rounded up to 128) for the backward; if Wf is given,
+// Wf[(d-1)*3 + s] = part s (hi, mid, lo: hi + mid + lo = w exactly) of W_d
+// transposed ([rows_out][nin_p]) for the forward.  The buffers start zeroed.
 __global__ void ff_tc_weights_kernel(const float *__restrict__ W, const uint8_t *__restrict__ D, int n_in,
-                                     int n_out, int nout_p, int rows_in, __nv_bfloat16 *Wb) {
+                                     int n_out, int nout_p, int rows_in, int nin_p, int rows_out,
+                                     __nv_bfloat16 *Wb, __nv_bfloat16 *Wf) {
     const long long cnt = (long long)n_in * n_out;
-    const size_t bsz = (size_t)rows_in * nout_p;
+    const size_t bsz = (size_t)rows_in * nout_p, fsz = (size_t)rows_out * nin_p;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt;
          q += (long long)gridDim.x * blockDim.x) {
         const int i = (int)(q / n_out), j = (int)(q % n_out);
         const int d = D[q];
         const float w = W[q];
         const __nv_bfloat16 hi = __float2bfloat16_rn(w);
-        const __nv_bfloat16 mid = __float2bfloat16_rn(__fsub_rn(w, __bfloat162float(hi)));
-        const size_t b = (size_t)i * nout_p + j;
-        Wb[(size_t)((d - 1) * 2 + 0) * bsz + b] = hi;
-        Wb[(size_t)((d - 1) * 2 + 1) * bsz + b] = mid;
+        const float r1 = __fsub_rn(w, __bfloat162float(hi));
+        const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+        if (Wb) {
+            const size_t b = (size_t)i * nout_p + j;
+            Wb[(size_t)((d - 1) * 2 + 0) * bsz + b] = hi;
+            Wb[(size_t)((d - 1) * 2 + 1) * bsz + b] = mid;
+        }
+        if (Wf) {
+            const __nv_bfloat16 lo = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(mid)));
+            const size_t f = (size_t)j * nin_p + i;
+            Wf[(size_t)((d - 1) * 3 + 0) * fsz + f] = hi;
+            Wf[(size_t)((d - 1) * 3 + 1) * fsz + f] = mid;
+            Wf[(size_t)((d - 1) * 3 + 2) * fsz + f] = lo;
+        }
     }
 }
 
-// Spike bits [rows][words] -> transposed 0/1 BF16 [n_in][rows_p] (padding
-// stays zero).
-__global__ void ff_tc_spikes_kernel(const unsigned *__restrict__ bits, int rows, int n_in, int words, int rows_p,
-                                    __nv_bfloat16 *ST) {
+// Spike bits [rows][words] -> 0/1 BF16: rows S [rows][nin_p] and/or the
+// transpose ST [n_in][rows_p], whichever is given (padding stays zero).
+__global__ void ff_tc_spikes_kernel(const unsigned *__restrict__ bits, int rows, int n_in, int words, int nin_p,
+                                    int rows_p, __nv_bfloat16 *S, __nv_bfloat16 *ST) {
     const long long cnt = (long long)rows * n_in;
     const __nv_bfloat16 one = __float2bfloat16_rn(1.0f), zero = __float2bfloat16_rn(0.0f);
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt;
          q += (long long)gridDim.x * blockDim.x) {
         const int r = (int)(q / n_in), i = (int)(q % n_in);
         const bool s = (bits[(size_t)r * words + (i >> 5)] >> (i & 31)) & 1u;
-        ST[(size_t)i * rows_p + r] = s ? one : zero;
+        if (S) S[(size_t)r * nin_p + i] = s ? one : zero;
+        if (ST) ST[(size_t)i * rows_p + r] = s ? one : zero;
     }
 }
 
@@ -285,19 +457,37 @@ cudaError_t ff_tc_gemm(const FfTcMaps &maps, const FfTcArgs &args, cudaStream_t 
     return cudaGetLastError();
 }
 
-cudaError_t ff_tc_weights(const float *W, const uint8_t *D, int n_in, int n_out, int nout_p, int rows_in,
-                          void *Wb, cudaStream_t s) {
-    cudaError_t e;
-    if ((e = cudaMemsetAsync(Wb, 0, (size_t)8 * rows_in * nout_p * 2, s)) != cudaSuccess) return e;
-    ff_tc_weights_kernel<<<grid_for((long long)n_in * n_out), 256, 0, s>>>(W, D, n_in, n_out, nout_p, rows_in,
-                                                                        (__nv_bfloat16 *)Wb);
+cudaError_t ff_tc_forward(const FfTcMaps &maps, const FfTcArgs &args, cudaStream_t s) {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    for (int p = 1; p < args.npass; ++p)
+        if (args.pass[p].kblocks != args.pass[0].kblocks) return cudaErrorInvalidValue;
+    const size_t smem = ff_tc_smem_bytes();
+    if ((e = cudaFuncSetAttribute((const void *)ff_tc_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)smem)) != cudaSuccess)
+        return e;
+    const int items = args.tiles_m * args.tiles_n;
+    const int grid = items < sms ? items : sms;
+    ff_tc_fwd_kernel<<<grid, kFwdTcThreads, smem, s>>>(maps, args);
     return cudaGetLastError();
 }
 
-cudaError_t ff_tc_spikes(const unsigned *bits, int rows, int n_in, int words, int rows_p, void *ST,
-                         cudaStream_t s) {
-    ff_tc_spikes_kernel<<<grid_for((long long)rows * n_in), 256, 0, s>>>(bits, rows, n_in, words, rows_p,
-                                                                       (__nv_bfloat16 *)ST);
+cudaError_t ff_tc_weights(const float *W, const uint8_t *D, int n_in, int n_out, int nout_p, int rows_in,
+                          void *Wb, int nin_p, int rows_out, void *Wf, cudaStream_t s) {
+    cudaError_t e;
+    if (Wb && (e = cudaMemsetAsync(Wb, 0, (size_t)8 * rows_in * nout_p * 2, s)) != cudaSuccess) return e;
+    if (Wf && (e = cudaMemsetAsync(Wf, 0, (size_t)12 * rows_out * nin_p * 2, s)) != cudaSuccess) return e;
+    ff_tc_weights_kernel<<<grid_for((long long)n_in * n_out), 256, 0, s>>>(
+        W, D, n_in, n_out, nout_p, rows_in, nin_p, rows_out, (__nv_bfloat16 *)Wb, (__nv_bfloat16 *)Wf);
+    return cudaGetLastError();
+}
+
+cudaError_t ff_tc_spikes(const unsigned *bits, int rows, int n_in, int words, int nin_p, int rows_p, void *S,
+                         void *ST, cudaStream_t s) {
+    ff_tc_spikes_kernel<<<grid_for((long long)rows * n_in), 256, 0, s>>>(
+        bits, rows, n_in, words, nin_p, rows_p, (__nv_bfloat16 *)S, (__nv_bfloat16 *)ST);
     return cudaGetLastError();
 }
 

@@ -15,7 +15,8 @@ namespace sn {
 
 enum Kind { KIND_SPARSE = 0, KIND_DENSE = 1, KIND_BATCH = 2, KIND_SHARED_I8 = 3, KIND_FF = 4 };
 
-// Grid barrier state (one per context): arrival count and generation.
+// Grid barrier state (one per context): the arrival count of the running
+// launch (zeroed before every launch that uses it); gen is unused padding.
 struct GridBarrier {
     unsigned int count;
     unsigned int gen;
@@ -182,10 +183,11 @@ struct FfTcArgs {
     Control *ctl;
 };
 cudaError_t ff_tc_gemm(const FfTcMaps &maps, const FfTcArgs &args, cudaStream_t s);
+cudaError_t ff_tc_forward(const FfTcMaps &maps, const FfTcArgs &args, cudaStream_t s);
 cudaError_t ff_tc_weights(const float *W, const uint8_t *D, int n_in, int n_out, int nout_p, int rows_in,
-                          void *Wb, cudaStream_t s);
-cudaError_t ff_tc_spikes(const unsigned *bits, int rows, int n_in, int words, int rows_p, void *ST,
-                         cudaStream_t s);
+                          void *Wb, int nin_p, int rows_out, void *Wf, cudaStream_t s);
+cudaError_t ff_tc_spikes(const unsigned *bits, int rows, int n_in, int words, int nin_p, int rows_p, void *S,
+                         void *ST, cudaStream_t s);
 cudaError_t ff_tc_gsplit(const float *g, int rows, int n_out, int nout_p, int rows_p, void *G, void *GT,
                          cudaStream_t s);
 cudaError_t ff_dw_reduce(const float *part, int splits, long long count, float *dW, cudaStream_t s);
@@ -203,7 +205,7 @@ cudaError_t plan_dense(int n, int *grid, int *chunk);
 // shared memory, or more than one neuron per thread).  Synapse words of the
 // pull store: x = ((D - d) * Wp + pre / 32) << 7 | (pre & 31),
 // Wp = roundup(ceil(n/32), 4).
-cudaError_t plan_pull(int n, int D, int *grid, int *chunk, int *rows, size_t *smem);
+cudaError_t plan_pull(int n, int D, long long m, int *grid, int *chunk, int *rows, size_t *smem);
 cudaError_t launch_sparse_pull(const NetArgs &a, int dtype, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_pull_flush(const NetArgs &a, int dtype, int t0, cudaStream_t s);
 cudaError_t launch_gather_weights(const uint2 *syn, const long long *perm_inv, long long m,

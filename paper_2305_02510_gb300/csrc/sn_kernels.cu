@@ -349,13 +349,21 @@ cudaError_t max_grid_sparse_reg(int *grid) {
     return cudaSuccess;
 }
 
+// The grid barrier's arrival count starts every launch at zero.
+static cudaError_t reset_barrier(Control *ctl, cudaStream_t s) {
+    return cudaMemsetAsync(&ctl->bar, 0, sizeof(GridBarrier), s);
+}
+
 cudaError_t launch_sparse_reg(const NetArgs &a, int dtype, int grid, cudaStream_t s) {
     void *args[] = {(void *)&a};
+    cudaError_t e = reset_barrier(a.ctl, s);
+    if (e != cudaSuccess) return e;
     return cudaLaunchCooperativeKernel(sparse_reg_fn(dtype), dim3(grid), dim3(kRegBlock), args, 0, s);
 }
 
 cudaError_t launch_sparse(const NetArgs &a, int dtype, int grid, int block, cudaStream_t s) {
     void *args[] = {(void *)&a};
+    if (cudaError_t e = reset_barrier(a.ctl, s)) return e;
     const size_t smem = (size_t)a.chunk * sizeof(int);
     const void *fn;
     if (dtype == SN_F32)
@@ -751,13 +759,16 @@ cudaError_t launch_dense(const NetArgs &a, int grid, int block, cudaStream_t s) 
     const size_t smem = dense_smem(a.words, a.chunk / 32);
     const bool vec = a.n % 4 == 0 && ((uintptr_t)a.W & 15u) == 0;
     const void *fn = dense_fn(a.chunk / 32, a.stdp != 0, vec);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = reset_barrier(a.ctl, s);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kBlock), args, smem, s);
 }
 
 // Executor plan of a dense network: the smallest columns-per-lane (1, 2, 4,
-// 8) whose grid of ceil(n / (32 * cpl)) blocks is co-resident.
+// 8) whose grid of ceil(n / (32 * cpl)) blocks is co-resident; a network of
+// at most 128 neurons runs as one block (no grid barrier).
 cudaError_t plan_dense(int n, int *grid, int *chunk) {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -766,6 +777,7 @@ cudaError_t plan_dense(int n, int *grid, int *chunk) {
     if (e != cudaSuccess) return e;
     const int words = (n + 31) / 32;
     for (int cpl : {1, 2, 4, 8}) {
+        if (n <= 128 && 32 * cpl < n) continue;
         const size_t smem = dense_smem(words, cpl);
         int per = 1 << 30;
         for (int v = 0; v < 3; ++v) {

@@ -74,39 +74,6 @@ __device__ __forceinline__ void pull_load(uint4 (&e)[kPullUnroll], const uint4 *
         e[u] = p0 + u < np ? __ldg(ent + (size_t)(p0 + u) * 32) : make_uint4(0u, 0u, 0u, 0u);
 }
 
-// Thread 0 of each block: arrive at the grid barrier, returning the
-// generation to wait for.
-__device__ __forceinline__ unsigned bar_arrive(Control *ctl) {
-    GridBarrier *b = &ctl->bar;
-    const unsigned gen = ld_acquire_u32(&b->gen);
-    __threadfence();
-    const unsigned arrived = atomicAdd(&b->count, 1u);
-    if (arrived == gridDim.x - 1) {
-        atomicExch(&b->count, 0u);
-        __threadfence();
-        atomicAdd(&b->gen, 1u);
-    }
-    return gen;
-}
-
-// Thread 0: wait until the generation moves on (bounded: wall-clock limit,
-// or a status latched by another block).  Returns false if it gave up.
-__device__ __forceinline__ bool bar_wait(Control *ctl, unsigned gen) {
-    const unsigned long long t_start = global_timer_ns();
-    unsigned spins = 0;
-    while (ld_acquire_u32(&ctl->bar.gen) == gen) {
-        if ((++spins & 63u) == 0) {
-            if (ld_status(ctl) != 0) return false;
-            if (global_timer_ns() - t_start > kBarrierTimeoutNs) {
-                atomicCAS(&ctl->status, 0, (int)SN_ETIMEOUT);
-                return false;
-            }
-        }
-        __nanosleep(32);
-    }
-    __threadfence();
-    return true;
-}
 
 template <int MODE>
 __global__ void __launch_bounds__(kPullMaxBlock, 1) sparse_pull_kernel(NetArgs a) {
@@ -304,7 +271,7 @@ const void *pull_fn(int dtype) {
 
 }  // namespace
 
-cudaError_t plan_pull(int n, int D, int *grid, int *chunk, int *rows, size_t *smem) {
+cudaError_t plan_pull(int n, int D, long long m, int *grid, int *chunk, int *rows, size_t *smem) {
     *grid = 0;
     int dev = 0, sms = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -316,7 +283,9 @@ cudaError_t plan_pull(int n, int D, int *grid, int *chunk, int *rows, size_t *sm
     // D rows must fit a block's shared memory next to the few static words
     const long long L = std::min<long long>((optin - 64) / (wp * 4), 1 << 14);
     if (L < D) return cudaSuccess;
-    const long long per = (words + sms - 1) / sms;   // slices per block
+    // slices per block: spread over the SMs; a small network (at most 1024
+    // neurons and 64 Ki synapses) runs as one block, without a grid barrier
+    const long long per = (words * 32 <= kPullMaxBlock && m <= 65536) ? words : (words + sms - 1) / sms;
     if (per * 32 > kPullMaxBlock) return cudaSuccess;
     const long long bytes = L * wp * 4;
     for (const void *fn : {pull_fn(SN_F32), pull_fn(SN_I32)}) {
@@ -337,7 +306,10 @@ cudaError_t plan_pull(int n, int D, int *grid, int *chunk, int *rows, size_t *sm
 cudaError_t launch_sparse_pull(const NetArgs &a, int dtype, int grid, size_t smem, cudaStream_t s) {
     void *args[] = {(void *)&a};
     const void *fn = pull_fn(dtype);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the grid barrier's arrival count starts every launch at zero
+    cudaError_t e = cudaMemsetAsync(&a.ctl->bar, 0, sizeof(GridBarrier), s);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(a.chunk), args, smem, s);
 }

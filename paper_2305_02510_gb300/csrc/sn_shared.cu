@@ -310,6 +310,9 @@ cudaError_t launch_shared(const void *tmaps, const SharedHostArgs &h, int grid, 
     const CUtensorMap *tm = (const CUtensorMap *)tmaps;
     const int g = grid < a.tiles ? grid : a.tiles;
     void *args[] = {(void *)&tm[0], (void *)&tm[1], (void *)&tm[2], (void *)&a};
+    // the grid barrier's arrival count starts every launch at zero
+    cudaError_t e = cudaMemsetAsync(&h.ctl->bar, 0, sizeof(GridBarrier), s);
+    if (e != cudaSuccess) return e;
     return cudaLaunchCooperativeKernel((const void *)shared_kernel, dim3(g), dim3(kShThreads), args,
                                        shared_smem_bytes(), s);
 }

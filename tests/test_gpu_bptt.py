@@ -3,7 +3,8 @@ SNNFunction) against the float64 unrolled reference trained by torch
 autograd (oracle/bptt_ref.py).
 
 Forward: spikes and counts equal the reference's; membrane checkpoints within
-1e-5 of max(|V|, theta).  Backward: per layer, the Frobenius-relative and the
+1e-5 of max(|V|, theta), or at the full size (100 integrated steps) within
+twice the deviation of a plain float32 evaluation of the reference.  Backward: per layer, the Frobenius-relative and the
 largest elementwise deviation of dLoss/dW from the float64 reference must be
 within max(1e-4, 2 x the deviation of a plain float32 evaluation of the same
 reference with the same spike decisions).  (At the full size the first
@@ -148,6 +149,13 @@ def test_bptt_full_size_teacher_forced(engine):
     given = [[torch.tensor(spikes[l + 1][t], dtype=torch.float64) for t in range(T)] for l in range(L)]
     ws = [torch.tensor(w, dtype=torch.float64, requires_grad=True) for w in task["w"]]
     ref_counts, _, ref_pre = R.forward(task, ws, given=given, record=True)
+    # the same teacher-forced forward in plain float32 arithmetic: over 100
+    # integrated steps float32 itself drifts from float64 by about the state
+    # tolerance, so the kernels' states are held to max(1e-5 relative, twice
+    # plain float32's deviation), as the gradients are
+    w32 = [torch.tensor(w, dtype=torch.float32) for w in task["w"]]
+    _, _, pre32 = R.forward(task, w32, dtype=torch.float32, given=[[g.float() for g in x] for x in given],
+                            record=True)
     # every spike decision of the kernels agrees with the reference's state
     # unless that state lies within 1e-4 * theta of the threshold
     th = task["threshold"]
@@ -161,7 +169,12 @@ def test_bptt_full_size_teacher_forced(engine):
         # checkpoints: state after steps k-1, 2k-1, ...
         k = task["checkpoint_every"]
         v = np.where(s, task["reset"], u)[k - 1::k][:ck[l + 1].shape[0]]
-        assert np.all(np.abs(ck[l + 1] - v) <= 1e-5 * np.maximum(np.abs(v), th) + 1e-6), l
+        u32 = torch.stack([pre32[l][t].detach() for t in range(T)]).double().numpy()
+        v32 = np.where(s, task["reset"], u32)[k - 1::k][:ck[l + 1].shape[0]]
+        tol = 1e-5 * np.maximum(np.abs(v), th) + 1e-6
+        level = float((np.abs(v32 - v) / tol).max())
+        worst = float((np.abs(ck[l + 1] - v) / tol).max())
+        assert worst <= max(1.0, 2.0 * level), (l, worst, level)
     assert spikes[L].sum() > 0
     assert np.array_equal(counts, ref_counts.detach().numpy())
     ref_loss = R.loss_fn(ref_counts, task["labels"])
