@@ -41,7 +41,7 @@ STATE_BYTES = 56
 STATE_BYTES_PULL = 40
 # DRAM bytes (read + write) of one 1000-timestep launch, from the ncu capture
 # of the current kernel version (absent: none taken for that kernel)
-NCU_TRAFFIC_BYTES = {"sparse_pull_kernel<SN_F32>": 3.39e9 + 3.87e6}
+NCU_TRAFFIC_BYTES = {"sparse_pull_kernel<SN_F32>": 2.30e9 + 3.80e6}
 
 
 def replica_seed(seed, rank):
