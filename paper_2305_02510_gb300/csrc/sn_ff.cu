@@ -139,10 +139,24 @@ __global__ void ff_scan_fwd_kernel(const float *__restrict__ I, int n, int words
     float v = p.reset;
     int r = 0;
     float cnt = 0.0f;
-    for (int t = 0; t < T; ++t) {
+    // the inputs of the next kPre steps are loaded ahead (they do not depend
+    // on the recurrence)
+    constexpr int kPre = 4;
+    const size_t stride = (size_t)B * n;
+    const float *Ip = I + (size_t)b * n + j;
+    float ahead[kPre];
+#pragma unroll
+    for (int q = 0; q < kPre; ++q) ahead[q] = (live && q < T) ? __ldg(Ip + (size_t)q * stride) : 0.0f;
+    for (int t0 = 0; t0 < T; t0 += kPre)
+#pragma unroll
+    for (int q = 0; q < kPre; ++q) {
+        const int t = t0 + q;
+        if (t >= T) break;
+        const float in = ahead[q];
+        ahead[q] = (live && t + kPre < T) ? __ldg(Ip + (size_t)(t + kPre) * stride) : 0.0f;
         bool s = false;
         if (live) {
-            const float u = __fadd_rn(ff_leak(v, p.leak, p.reset), I[((size_t)t * B + b) * n + j]);
+            const float u = __fadd_rn(ff_leak(v, p.leak, p.reset), in);
             s = (u > p.theta) && (r == 0);
             if (s) { v = p.reset; r = p.refractory; }
             else { v = u; if (r > 0) r -= 1; }
@@ -151,9 +165,9 @@ __global__ void ff_scan_fwd_kernel(const float *__restrict__ I, int n, int words
         const unsigned word = __ballot_sync(0xffffffffu, s);
         if (lane == 0) S[((size_t)t * B + b) * words + (j >> 5)] = word;
         if (live && (t % k) == k - 1) {
-            const size_t q = ((size_t)(t / k) * B + b) * n + j;
-            vck[q] = v;
-            rck[q] = r;
+            const size_t ci = ((size_t)(t / k) * B + b) * n + j;
+            vck[ci] = v;
+            rck[ci] = r;
         }
     }
     if (live && counts) counts[(size_t)b * n + j] = cnt;

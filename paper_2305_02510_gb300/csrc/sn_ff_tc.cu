@@ -394,39 +394,61 @@ __global__ void ff_tc_weights_kernel(const float *__restrict__ W, const uint8_t 
 }
 
 // Spike bits [rows][words] -> 0/1 BF16: rows S [rows][nin_p] and/or the
-// transpose ST [n_in][rows_p], whichever is given (padding stays zero).
-__global__ void ff_tc_spikes_kernel(const unsigned *__restrict__ bits, int rows, int n_in, int words, int nin_p,
-                                    int rows_p, __nv_bfloat16 *S, __nv_bfloat16 *ST) {
-    const long long cnt = (long long)rows * n_in;
+// transpose ST [n_in][rows_p], whichever is given (padding stays zero).  A
+// block converts a 32 x 32 tile (rows r0.., inputs i0..) through shared
+// memory, so both outputs leave as 64-byte row pieces.
+__global__ void __launch_bounds__(256) ff_tc_spikes_kernel(const unsigned *__restrict__ bits, int rows, int n_in,
+                                                           int words, int nin_p, int rows_p, __nv_bfloat16 *S,
+                                                           __nv_bfloat16 *ST) {
+    __shared__ __nv_bfloat16 tile[32][34];
+    const int r0 = blockIdx.x * 32, i0 = blockIdx.y * 32;   // rows on x: no 65535 limit
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;      // 32 x 8
     const __nv_bfloat16 one = __float2bfloat16_rn(1.0f), zero = __float2bfloat16_rn(0.0f);
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt;
-         q += (long long)gridDim.x * blockDim.x) {
-        const int r = (int)(q / n_in), i = (int)(q % n_in);
-        const bool s = (bits[(size_t)r * words + (i >> 5)] >> (i & 31)) & 1u;
-        if (S) S[(size_t)r * nin_p + i] = s ? one : zero;
-        if (ST) ST[(size_t)i * rows_p + r] = s ? one : zero;
+    for (int y = ty; y < 32; y += 8) {
+        const int r = r0 + y, i = i0 + tx;
+        bool sp = false;
+        if (r < rows && i < n_in) sp = (__ldg(bits + (size_t)r * words + (i >> 5)) >> (i & 31)) & 1u;
+        tile[y][tx] = sp ? one : zero;
+        if (S && r < rows && i < n_in) S[(size_t)r * nin_p + i] = sp ? one : zero;
+    }
+    if (!ST) return;
+    __syncthreads();
+    for (int y = ty; y < 32; y += 8) {
+        const int i = i0 + y, r = r0 + tx;
+        if (i < n_in && r < rows) ST[(size_t)i * rows_p + r] = tile[tx][y];
     }
 }
 
 // Gradient gI [rows][n_out] -> two-term BF16 split G[s] ([rows][nout_p]) and,
-// if GT is given, its transpose GT[s] ([n_out][rows_p]).
-__global__ void ff_tc_gsplit_kernel(const float *__restrict__ g, int rows, int n_out, int nout_p, int rows_p,
-                                    __nv_bfloat16 *G, __nv_bfloat16 *GT) {
-    const long long cnt = (long long)rows * n_out;
+// if GT is given, its transpose GT[s] ([n_out][rows_p]); 32 x 32 tiles
+// through shared memory.
+__global__ void __launch_bounds__(256) ff_tc_gsplit_kernel(const float *__restrict__ g, int rows, int n_out,
+                                                           int nout_p, int rows_p, __nv_bfloat16 *G,
+                                                           __nv_bfloat16 *GT) {
+    __shared__ __nv_bfloat16 th[32][34], tm[32][34];
+    const int r0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     const size_t gsz = (size_t)rows * nout_p, tsz = (size_t)n_out * rows_p;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt;
-         q += (long long)gridDim.x * blockDim.x) {
-        const int r = (int)(q / n_out), j = (int)(q % n_out);
-        const float x = g[q];
+    for (int y = ty; y < 32; y += 8) {
+        const int r = r0 + y, j = j0 + tx;
+        float x = 0.0f;
+        if (r < rows && j < n_out) x = __ldg(g + (size_t)r * n_out + j);
         const __nv_bfloat16 hi = __float2bfloat16_rn(x);
         const __nv_bfloat16 mid = __float2bfloat16_rn(__fsub_rn(x, __bfloat162float(hi)));
-        if (G) {
+        th[y][tx] = hi;
+        tm[y][tx] = mid;
+        if (G && r < rows && j < n_out) {
             G[(size_t)r * nout_p + j] = hi;
             G[gsz + (size_t)r * nout_p + j] = mid;
         }
-        if (GT) {
-            GT[(size_t)j * rows_p + r] = hi;
-            GT[tsz + (size_t)j * rows_p + r] = mid;
+    }
+    if (!GT) return;
+    __syncthreads();
+    for (int y = ty; y < 32; y += 8) {
+        const int j = j0 + y, r = r0 + tx;
+        if (j < n_out && r < rows) {
+            GT[(size_t)j * rows_p + r] = th[tx][y];
+            GT[tsz + (size_t)j * rows_p + r] = tm[tx][y];
         }
     }
 }
@@ -486,15 +508,17 @@ cudaError_t ff_tc_weights(const float *W, const uint8_t *D, int n_in, int n_out,
 
 cudaError_t ff_tc_spikes(const unsigned *bits, int rows, int n_in, int words, int nin_p, int rows_p, void *S,
                          void *ST, cudaStream_t s) {
-    ff_tc_spikes_kernel<<<grid_for((long long)rows * n_in), 256, 0, s>>>(
-        bits, rows, n_in, words, nin_p, rows_p, (__nv_bfloat16 *)S, (__nv_bfloat16 *)ST);
+    const dim3 grid((rows + 31) / 32, (n_in + 31) / 32);
+    ff_tc_spikes_kernel<<<grid, 256, 0, s>>>(bits, rows, n_in, words, nin_p, rows_p, (__nv_bfloat16 *)S,
+                                            (__nv_bfloat16 *)ST);
     return cudaGetLastError();
 }
 
 cudaError_t ff_tc_gsplit(const float *g, int rows, int n_out, int nout_p, int rows_p, void *G, void *GT,
                          cudaStream_t s) {
-    ff_tc_gsplit_kernel<<<grid_for((long long)rows * n_out), 256, 0, s>>>(
-        g, rows, n_out, nout_p, rows_p, (__nv_bfloat16 *)G, (__nv_bfloat16 *)GT);
+    const dim3 grid((rows + 31) / 32, (n_out + 31) / 32);
+    ff_tc_gsplit_kernel<<<grid, 256, 0, s>>>(g, rows, n_out, nout_p, rows_p, (__nv_bfloat16 *)G,
+                                            (__nv_bfloat16 *)GT);
     return cudaGetLastError();
 }
 

@@ -684,14 +684,36 @@ __global__ void __launch_bounds__(kBlock, CPL <= 2 ? 4 : 3) dense_kernel(NetArgs
                 // LTP in the spiking columns of this list chunk, rows that did not
                 // spike; the rows are shared out over every warp of the grid (no
                 // block writes a row the gather touches: those rows spiked)
+                // Each element is one read-modify-write of its own weight, so the
+                // reads of kLtpRows rows are issued together before any write.
+                constexpr int kLtpRows = 4;
                 const int gwarps = gridDim.x * nwarp;
-                for (int i = blockIdx.x * nwarp + warp; i < n; i += gwarps) {
-                    if (spiked(row_bits, i)) continue;
-                    const float dw = __fmul_rn(a.a_plus, xo[i]);
-                    float *row = a.W + (size_t)i * n;
-                    for (int q = lane; q < cnt; q += 32) {
-                        const int jj = list[q];
-                        row[jj] = clampf(__fadd_rn(row[jj], dw), a.wmin, a.wmax);
+                for (int i0 = blockIdx.x * nwarp + warp; i0 < n; i0 += kLtpRows * gwarps) {
+                    for (int q0 = 0; q0 < cnt; q0 += 64) {
+                        float val[kLtpRows][2], dw[kLtpRows];
+                        bool act[kLtpRows];
+#pragma unroll
+                        for (int u = 0; u < kLtpRows; ++u) {
+                            const int i = i0 + u * gwarps;
+                            act[u] = i < n && !spiked(row_bits, i);
+                            dw[u] = act[u] ? __fmul_rn(a.a_plus, xo[i]) : 0.0f;
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const int q = q0 + lane + 32 * h;
+                                val[u][h] = (act[u] && q < cnt) ? a.W[(size_t)i * n + list[q]] : 0.0f;
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < kLtpRows; ++u) {
+                            const int i = i0 + u * gwarps;
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                const int q = q0 + lane + 32 * h;
+                                if (act[u] && q < cnt)
+                                    a.W[(size_t)i * n + list[q]] =
+                                        clampf(__fadd_rn(val[u][h], dw[u]), a.wmin, a.wmax);
+                            }
+                        }
                     }
                 }
             }
