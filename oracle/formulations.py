@@ -54,12 +54,23 @@ def mat_proxy(wl, steps: int, integer: bool = True):
     dt = np.int64 if integer else np.float64
     pre, post = np.asarray(wl["pre"]), np.asarray(wl["post"])
     w, d = np.asarray(wl["weight"]), np.asarray(wl["delay"])
-    n_proxy = int(np.sum(np.maximum(d - 1, 0)))
+    # axonal delays (Section 2.2): neuron i's spikes first cross a chain of
+    # axonal_delay[i] proxies shared by all of its outgoing synapses
+    ax = np.asarray(wl.get("axonal_delay") if wl.get("axonal_delay") is not None else np.zeros(n), np.int64)
+    n_proxy = int(np.sum(np.maximum(d - 1, 0))) + int(ax.sum())
     tot = n + n_proxy
     W = np.zeros((tot, tot), dtype=dt)
     nxt = n
+    axon_end = np.arange(n)
+    for i in range(n):
+        src = i
+        for _ in range(int(ax[i])):
+            W[src, nxt] += 1
+            src = nxt
+            nxt += 1
+        axon_end[i] = src
     for i, j, wk, dk in zip(pre, post, w, d):
-        src = int(i)
+        src = int(axon_end[int(i)])
         for _ in range(int(dk) - 1):          # proxy chain, unit-weight hops
             W[src, nxt] += 1
             src = nxt

@@ -141,6 +141,22 @@ def test_axonal_delay_chain_arrival(delays, axonal, mode):
     assert np.array_equal(O.run(wl0, mode, steps)[1], O.run(wl1, mode, steps)[1])
 
 
+@pytest.mark.parametrize("seed", range(60))
+def test_axonal_oracle_equals_shared_axon_proxies(seed):
+    """The oracle composes each synapse's delay with its pre-neuron's axonal
+    delay; the matrix formulation instead routes all of a neuron's outgoing
+    synapses through one shared chain of axonal proxy neurons.  Rasters must
+    agree bit for bit (integer networks)."""
+    wl = W.random_small(7000 + seed, integer=True, steps=120, events_rate=0.5)
+    rng = np.random.default_rng(seed)
+    wl["axonal_delay"] = rng.integers(0, 4, wl["n"]).astype(np.int32)
+    wl["max_delay"] = int(wl["max_delay"]) + 3
+    _, want, _ = O.run(wl, O.INT, 120)
+    got, _, _ = mat_proxy(wl, 120, integer=True)
+    assert np.array_equal(got, want)
+    assert want.sum() > 0 or len(wl["pre"]) == 0
+
+
 def _check_isi(raster, refr):
     for j in range(raster.shape[1]):
         t = np.nonzero(raster[:, j])[0]
