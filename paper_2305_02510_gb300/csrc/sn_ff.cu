@@ -18,6 +18,10 @@
 //   gs_{l-1}[t][b][i] = sum_j W[i][j] gI[t + D[i][j]][b][j]
 //   dW[i][j]          = sum_{t,b} gI[t][b][j] s_{l-1}[t - D[i][j]][b][i]
 // u(t) is recomputed from membrane checkpoints stored every k steps.
+//
+// This file holds the recurrences and the CUDA-core (SIMT) forms of the three
+// contractions; sn_ff_tc.cu holds their tensor-core forms, which the host
+// code uses by default (sn_ff_set_engine).
 
 #include <cuda_runtime.h>
 #include <stdint.h>

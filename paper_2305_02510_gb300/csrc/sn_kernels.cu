@@ -403,12 +403,14 @@ cudaError_t max_grid_sparse(int dtype, int stdp, int block, int *grid) {
 // Dense network: W[n][n] row-major (row = pre), one grid barrier per step.
 // Block c owns the column slab [c * cw, c * cw + cw), cw = 32 * CPL, and the
 // neurons with the same indices.  Step t:
-//   update(t):  own neurons (state in registers), input from the block's own
-//               ring slot t; spikes -> spike bits of t (double buffer), raster;
+//   update(t):  own neurons (state in registers, parameters in shared
+//               memory), input from the block's own ring slot t; spikes ->
+//               spike bits of t (double buffer), raster;
 //   grid barrier;
 //   gather(t):  every block walks the spikers of step t in ascending order,
-//               each warp taking every eighth row, and sums W[i][own columns];
-//               the eight warp partials are folded in warp order and stored as
+//               each warp taking every eighth row, and sums W[i][own columns]
+//               (vector form: gather_vec, four rows per float4 instruction);
+//               the warp partials are folded in a fixed order and stored as
 //               the input arriving at t + delay.  With STDP the block also
 //               updates its columns of the spiking rows (LTD, and LTP where the
 //               column spiked) before using them, and its spiking columns in
