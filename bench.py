@@ -74,49 +74,74 @@ def peaks():
 
 
 class Clocks:
-    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    """nvidia-smi samples (every 50 ms) of SM clock and throttle reasons.  The
+    sampler starts before the warm-up so that it is running when the timed
+    region begins; the summary keeps the samples whose timestamps fall inside
+    the marked region (or, for a region shorter than the sampling interval,
+    the samples nearest to it)."""
 
-    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    Q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, index):
         self.index = index
         self.p = None
+        self.t0 = self.t1 = None
+        self.rows = []
 
-    def __enter__(self):
+    def start(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.p = None
         return self
 
-    def __exit__(self, *a):
-        self.rows = []
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_end(self):
+        self.t1 = time.time()
+
+    def stop(self):
         if self.p is None:
             return
+        time.sleep(0.1)
         self.p.terminate()
         try:
             out, _ = self.p.communicate(timeout=5)
         except Exception:
             self.p.kill()
             out = ""
+        import datetime
         for line in out.strip().splitlines():
             f = [x.strip() for x in line.split(",")]
-            if len(f) >= 9:
-                self.rows.append(f)
+            if len(f) < 10:
+                continue
+            try:
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+            except ValueError:
+                continue
+            self.rows.append((ts, f[1:]))
 
     def summary(self):
-        if not getattr(self, "rows", None):
+        if not self.rows or self.t0 is None or self.t1 is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
-        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        inside = [r for ts, r in self.rows if self.t0 <= ts <= self.t1]
+        window = "timed region"
+        if not inside:
+            mid = 0.5 * (self.t0 + self.t1)
+            near = sorted(self.rows, key=lambda x: abs(x[0] - mid))[:2]
+            inside = [r for _, r in near]
+            window = "nearest to a timed region shorter than the 50 ms sampling interval"
+        sm = [float(r[1]) for r in inside if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in inside if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k] == "Active"})
+        reasons = sorted({names[k] for r in inside for k in range(4) if r[5 + k] == "Active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+                "reasons": reasons, "samples": len(inside), "window": window}
 
 
 def algorithmic_bytes(n, timesteps, spikes, events):
@@ -231,9 +256,17 @@ def extras(S, W, torch, stream, flush):
     res["huge_dense"] = huge_dense_extra(S, W, torch, stream, flush)
     res["bptt"] = bptt_extra(S, W, torch, stream)
     res["shared_dense"] = shared_extra(S, W, torch, stream, flush)
+    peak, src = peaks()
+    nsum = int(sum(w["n"] for w in nets))
+    # per neuron and step the update's state traffic; per spike its CSR row
+    # bounds; per event its packed synapse (6 B) and its accumulate (8 B)
+    bbytes = 500 * nsum * STATE_BYTES + spk * 16 + ev * 14
     res["batched"] = {
         "workload": "4096 networks, N log-uniform [64, 4096], p U(0.01, 0.2), delays 1..8",
-        "networks": len(nets), "neurons": int(sum(w["n"] for w in nets)),
+        "roofline": {"bound": "hbm", "achieved": bbytes / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": bbytes / (ms / 1e3) / 1e9 / peak, "peak_source": src, "kernel": "batch_kernel<SN_F32>",
+                     "note": "per-network timestep latency bounds this kernel (quiet networks, one executor each)"},
+        "networks": len(nets), "neurons": nsum,
         "synapses": int(sum(len(w["pre"]) for w in nets)), "timesteps": 500, "ms": ms,
         "synaptic_events_per_s": ev / (ms / 1e3), "network_timesteps_per_s": len(nets) * 500 / (ms / 1e3),
         "plain_ms": plain_ms, "plain_synaptic_events_per_s": plain_ev / (plain_ms / 1e3),
@@ -544,7 +577,7 @@ def run_reference(args, wl, rank):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--timesteps", type=int, default=TIMESTEPS)
@@ -601,18 +634,21 @@ def main():
         _, spk, ev = S.sn_get_counters(ctx)
         record.append((a.elapsed_time(b), spk, ev))
 
+    clk = Clocks(local).start()
     for _ in range(args.warmup):
         one([])
     res = []
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    with Clocks(local) as clk:
-        w0 = time.perf_counter()
-        for _ in range(args.steps):
-            one(res)
-        torch.cuda.synchronize()
-        wall = time.perf_counter() - w0
+    clk.mark_start()
+    w0 = time.perf_counter()
+    for _ in range(args.steps):
+        one(res)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - w0
+    clk.mark_end()
+    clk.stop()
     if world > 1:
         dist.barrier()
     ms = sum(r[0] for r in res) / len(res)

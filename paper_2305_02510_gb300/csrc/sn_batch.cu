@@ -30,33 +30,53 @@ struct BatchNet {
     unsigned long long key;
 };
 
-// Update of neuron j (local) of network nb at step t.  Returns the spike.
+// Update of neuron j (local) of network nb at step t, in two halves so that a
+// thread can issue the loads of several neurons before it uses any of them:
+// batch_load reads the pending input, state and parameters; batch_finish
+// clears the pending-input slot, adds the external input and applies the LIF
+// rule (Section 2.1 order), storing the state.  Returns the spike.
 template <int MODE>
-__device__ __forceinline__ bool batch_update(const BatchArgs &a, const BatchNet<MODE> &nb, int t, int j,
-                                             typename Tr<MODE>::A *slot, bool global_ring,
-                                             bool &overflow) {
+struct NeuronIn {
+    typename Tr<MODE>::A raw;
+    typename Tr<MODE>::V v, th, lk, rs;
+    int rr, R;
+};
+
+template <int MODE>
+__device__ __forceinline__ void batch_load(const BatchArgs &a, const BatchNet<MODE> &nb, int j,
+                                           const typename Tr<MODE>::A *slot, bool global_ring, NeuronIn<MODE> &in) {
     using V = typename Tr<MODE>::V;
-    using A = typename Tr<MODE>::A;
     const int g = nb.off + j;
-    A raw = global_ring ? __ldcg(slot + j) : slot[j];
+    in.raw = global_ring ? __ldcg(slot + j) : slot[j];
+    in.v = ((const V *)a.V)[g];
+    in.rr = a.r[g];
+    in.th = __ldg((const V *)a.th + g);
+    in.lk = __ldg((const V *)a.lk + g);
+    in.rs = __ldg((const V *)a.rs + g);
+    in.R = __ldg(a.R + g);
+}
+
+template <int MODE>
+__device__ __forceinline__ bool batch_finish(const BatchArgs &a, const BatchNet<MODE> &nb, int t, int j,
+                                             typename Tr<MODE>::A *slot, NeuronIn<MODE> &in, bool &overflow) {
+    using V = typename Tr<MODE>::V;
+    const int g = nb.off + j;
     slot[j] = 0;
-    const V acc = Tr<MODE>::from_acc(raw);
+    const V acc = Tr<MODE>::from_acc(in.raw);
     const V ext = external_input_at<MODE>(a.ev_off, a.ev_nsteps, a.ev_neuron, a.ev_val, a.prate, a.pamp,
                                           nb.key, t, g, j);
-    V *Vp = (V *)a.V;
-    V v = Vp[g];
-    int rr = a.r[g];
     bool fire;
     if constexpr (MODE == SN_F32)
-        fire = lif_update_f32(v, rr, acc, ext, __ldg((const float *)a.th + g), __ldg((const float *)a.lk + g),
-                              __ldg((const float *)a.rs + g), __ldg(a.R + g));
+        fire = lif_update_f32(in.v, in.rr, acc, ext, in.th, in.lk, in.rs, in.R);
     else
-        fire = lif_update_i32(v, rr, acc, ext, __ldg((const int *)a.th + g), __ldg((const int *)a.lk + g),
-                              __ldg((const int *)a.rs + g), __ldg(a.R + g), overflow);
-    Vp[g] = v;
-    a.r[g] = rr;
+        fire = lif_update_i32(in.v, in.rr, acc, ext, in.th, in.lk, in.rs, in.R, overflow);
+    ((V *)a.V)[g] = in.v;
+    a.r[g] = in.rr;
     return fire;
 }
+
+// Neurons whose loads one thread issues together in the update phase.
+constexpr int kUpdAhead = 2;
 
 // Push of spiker i (local) of network nb: lanes stride the CSR row.
 template <int MODE>
@@ -119,17 +139,28 @@ __global__ void __launch_bounds__(kBatchBlock) batch_kernel(BatchArgs a) {
             unsigned *rrow = a.raster + (size_t)(t % a.cap) * a.total_words + nb.woff;
             if (threadIdx.x == 0) s_cnt = 0;
             __syncthreads();
-            for (int jb = 0; jb < nb.n; jb += blockDim.x) {
-                const int j = jb + threadIdx.x;
-                const bool fire = j < nb.n && batch_update<MODE>(a, nb, t, j, slot, !in_smem, overflow);
-                const unsigned ball = __ballot_sync(0xffffffffu, fire);
-                const int wb = jb + warp * 32;
-                if (lane == 0 && wb < nb.n) rrow[wb >> 5] = ball;
-                if (ball) {
-                    int base = 0;
-                    if (lane == 0) base = atomicAdd(&s_cnt, __popc(ball));
-                    base = __shfl_sync(0xffffffffu, base, 0);
-                    if (fire) lists[base + __popc(ball & ((1u << lane) - 1u))] = j;
+            for (int jb0 = 0; jb0 < nb.n; jb0 += kUpdAhead * blockDim.x) {
+                NeuronIn<MODE> in[kUpdAhead];
+#pragma unroll
+                for (int u = 0; u < kUpdAhead; ++u) {
+                    const int j = jb0 + u * blockDim.x + threadIdx.x;
+                    if (j < nb.n) batch_load<MODE>(a, nb, j, slot, !in_smem, in[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < kUpdAhead; ++u) {
+                    const int jb = jb0 + u * blockDim.x;
+                    if (jb >= nb.n) break;
+                    const int j = jb + threadIdx.x;
+                    const bool fire = j < nb.n && batch_finish<MODE>(a, nb, t, j, slot, in[u], overflow);
+                    const unsigned ball = __ballot_sync(0xffffffffu, fire);
+                    const int wb = jb + warp * 32;
+                    if (lane == 0 && wb < nb.n) rrow[wb >> 5] = ball;
+                    if (ball) {
+                        int base = 0;
+                        if (lane == 0) base = atomicAdd(&s_cnt, __popc(ball));
+                        base = __shfl_sync(0xffffffffu, base, 0);
+                        if (fire) lists[base + __popc(ball & ((1u << lane) - 1u))] = j;
+                    }
                 }
             }
             __syncthreads();
@@ -169,13 +200,24 @@ __global__ void __launch_bounds__(kBatchBlock) batch_kernel(BatchArgs a) {
             A *slot = ring + (size_t)cur * nb.n;
             unsigned *rrow = a.raster + (size_t)(t % a.cap) * a.total_words + nb.woff;
             int cnt = 0;
-            for (int jb = 0; jb < nb.n; jb += 32) {
-                const int j = jb + lane;
-                const bool fire = j < nb.n && batch_update<MODE>(a, nb, t, j, slot, !in_smem, overflow);
-                const unsigned ball = __ballot_sync(0xffffffffu, fire);
-                if (lane == 0) rrow[jb >> 5] = ball;
-                if (fire) wlist[cnt + __popc(ball & ((1u << lane) - 1u))] = j;
-                cnt += __popc(ball);
+            for (int jb0 = 0; jb0 < nb.n; jb0 += kUpdAhead * 32) {
+                NeuronIn<MODE> in[kUpdAhead];
+#pragma unroll
+                for (int u = 0; u < kUpdAhead; ++u) {
+                    const int j = jb0 + u * 32 + lane;
+                    if (j < nb.n) batch_load<MODE>(a, nb, j, slot, !in_smem, in[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < kUpdAhead; ++u) {
+                    const int jb = jb0 + u * 32;
+                    if (jb >= nb.n) break;
+                    const int j = jb + lane;
+                    const bool fire = j < nb.n && batch_finish<MODE>(a, nb, t, j, slot, in[u], overflow);
+                    const unsigned ball = __ballot_sync(0xffffffffu, fire);
+                    if (lane == 0) rrow[jb >> 5] = ball;
+                    if (fire) wlist[cnt + __popc(ball & ((1u << lane) - 1u))] = j;
+                    cnt += __popc(ball);
+                }
             }
             __syncwarp();
             if (lane == 0) my_spikes += (unsigned long long)cnt;
