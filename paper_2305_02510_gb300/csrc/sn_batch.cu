@@ -76,7 +76,7 @@ __device__ __forceinline__ bool batch_finish(const BatchArgs &a, const BatchNet<
 }
 
 // Neurons whose loads one thread issues together in the update phase.
-constexpr int kUpdAhead = 2;
+constexpr int kUpdAhead = 8;
 
 // Push of spiker i (local) of network nb: lanes stride the CSR row.
 template <int MODE>
@@ -105,7 +105,7 @@ __device__ BatchNet<MODE> load_net(const BatchArgs &a, int b) {
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kBatchBlock) batch_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(kBatchBlock, 2) batch_kernel(BatchArgs a) {
     using A = typename Tr<MODE>::A;
     extern __shared__ __align__(16) unsigned char smem[];
     A *arena = (A *)smem;                                  // ring arena

@@ -13,10 +13,10 @@
 // Tile = 128 trains x 128 post-neurons, accumulated in TMEM over the K = n
 // pre-neurons in 128-byte stages loaded by TMA (128B swizzle, 6 stages).
 // Warp 0 lane 0 issues TMA, warp 1 lane 0 issues the MMAs; meanwhile warps
-// 2..7 draw the tile's Poisson input of step t (one bit per train and neuron)
+// 2..15 draw the tile's Poisson input of step t (one bit per train and neuron)
 // and stage the tile's neuron parameters in shared memory.  Afterwards the
-// eight warps read the accumulator rows (tcgen05.ld: warps w and w+4 share TMEM
-// lane quarter w, each taking half of the columns) and apply the integer LIF
+// sixteen warps read the accumulator rows (tcgen05.ld: warps w, w+4, w+8 and
+// w+12 share TMEM lane quarter w, each taking 32 columns) and apply the integer LIF
 // rule (Section 2.1 order).  The state is neuron-major ([n][B]: lane = train,
 // so every load and store of V and r is one 128-byte line per warp); the
 // spike bytes that are the next step's A operand go through a shared-memory
@@ -41,7 +41,10 @@ constexpr int kTK = 128;                       // bytes of K per stage (one 128B
 constexpr int kStages = 6;
 constexpr int kStageA = kTM * kTK;             // 16 KiB
 constexpr int kStageBytes = (kTM + kTN) * kTK; // 32 KiB
-constexpr int kShThreads = 256;
+constexpr int kShThreads = 512;
+constexpr int kEpiParts = kShThreads / 128;        // warps per TMEM lane quarter
+constexpr int kEpiCols = kTN / kEpiParts;          // accumulator columns per epilogue warp
+constexpr int kSub = 4;                      // state columns loaded together
 // epilogue staging after the pipeline stages: spike bytes [128][kSaPitch],
 // raster words and Poisson bits [128][4], parameters [5][128]
 constexpr int kSaPitch = 144;                  // 128 B + 16: conflict-free 16-byte stores
@@ -161,43 +164,44 @@ shared_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ 
                 }
             }
             __syncwarp();
-            // epilogue: warps w and w+4 own TMEM lanes (tile rows) 32(w%4) ..,
-            // each taking half of the 128 columns
+            // epilogue: warps w, w+4, ... own TMEM lanes (tile rows) 32(w%4) ..,
+            // each taking kEpiCols of the 128 columns
             const bool ok = mbar_wait(smem_addr(&accbar), tiles_done & 1u, a.ctl);
             ++tiles_done;
             if (!ok) s_abort = 1;
             __syncthreads();                   // Poisson bits and parameters staged
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const int quarter = warp & 3, half = warp >> 2;
+            const int quarter = warp & 3, part = warp >> 2;
             const int bl = quarter * 32 + lane;            // tile row = TMEM lane
             const int b = m0 + bl;
-            for (int cc = 0; cc < 2; ++cc) {
-                const int c0 = half * 64 + cc * 32;        // tile column of register 0
+            for (int cc = 0; cc < kEpiCols / 32; ++cc) {
+                const int c0 = part * kEpiCols + cc * 32;  // tile column of register 0
                 uint32_t v[32];
                 tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
                 if (!ok) continue;
                 const int j0 = n0 + c0;
-                // column q of this train at V[(j0 + q) * B + b]: two halves of
-                // 16 columns, loads of a half issued together
+                // column q of this train at V[(j0 + q) * B + b], in groups of kSub
+                // columns whose loads are issued together
                 int *Vp = a.V + (size_t)j0 * a.B + b;
                 int *rp = a.r + (size_t)j0 * a.B + b;
                 const unsigned pb = sP[bl * 4 + (c0 >> 5)];
                 unsigned bits = 0;
                 uint32_t outw[8];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    int vin[16], rin[16];
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        vin[q] = __ldcg(Vp + (unsigned)((h * 16 + q) * a.B));
-                        rin[q] = __ldcg(rp + (unsigned)((h * 16 + q) * a.B));
+                for (int h = 0; h < 32 / kSub; ++h) {
+                    int vin[kSub], rin[kSub];
+#pragma unroll
+                    for (int q = 0; q < kSub; ++q) {
+                        vin[q] = __ldcg(Vp + (unsigned)((h * kSub + q) * a.B));
+                        rin[q] = __ldcg(rp + (unsigned)((h * kSub + q) * a.B));
                     }
 #pragma unroll
-                    for (int q4 = 0; q4 < 4; ++q4) {
+                    for (int q4 = 0; q4 < kSub / 4; ++q4) {
                         uint32_t bytes = 0;
 #pragma unroll
                         for (int e = 0; e < 4; ++e) {
-                            const int qq = q4 * 4 + e, q = h * 16 + qq, c = c0 + q;
+                            const int qq = q4 * 4 + e, q = h * kSub + qq, c = c0 + q;
                             const int acc = __float2int_rn(__uint_as_float(v[q]));
                             const int ext = ((pb >> q) & 1u) ? sAmp[c] : 0;
                             const bool fire = lif_update_i32(vin[qq], rin[qq], acc, ext, sTh[c], sLk[c], sRs[c],
@@ -205,12 +209,12 @@ shared_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ 
                             bits |= (unsigned)fire << q;
                             bytes |= (fire ? 0x38u : 0u) << (8 * e);      // E4M3 1.0
                         }
-                        outw[h * 4 + q4] = bytes;
+                        outw[h * (kSub / 4) + q4] = bytes;
                     }
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) {
-                        __stcg(Vp + (unsigned)((h * 16 + q) * a.B), vin[q]);
-                        __stcg(rp + (unsigned)((h * 16 + q) * a.B), rin[q]);
+                    for (int q = 0; q < kSub; ++q) {
+                        __stcg(Vp + (unsigned)((h * kSub + q) * a.B), vin[q]);
+                        __stcg(rp + (unsigned)((h * kSub + q) * a.B), rin[q]);
                     }
                 }
                 uint4 *dst = (uint4 *)(sA + bl * kSaPitch + c0);
