@@ -39,8 +39,8 @@ sn_status bf16_map(sn_ctx *c, CUtensorMap *out, const void *base, long long rows
 bool use_tc(const sn_ctx *c) { return c->ff_tc_ok && c->ff_engine != SN_FF_SIMT; }
 
 // Synaptic input of layer l for all rows, I[r][j] = sum_d sum_i S[r - dB][i] W_d[i][j]:
-// 4 delays x 3 exact BF16 weight parts = 12 passes, accumulated block by block
-// (ff_tc_forward).  Unpacks the previous layer's spikes, and their transpose
+// 4 delays x 3 exact BF16 weight parts (4 passes of 3 parts each), accumulated
+// block by block (ff_tc_forward).  Unpacks the previous layer's spikes, and their transpose
 // when the weight gradient will need it.
 sn_status tc_forward(sn_ctx *c, int l, bool want_st) {
     const int B = c->ff_batch, rows = B * c->ff_steps;
@@ -57,13 +57,15 @@ sn_status tc_forward(sn_ctx *c, int l, bool want_st) {
     if ((s = bf16_map(c, &maps.m[0], c->ff_Sbf, rows, nin_p)) ||
         (s = bf16_map(c, &maps.m[1], c->ff_Wf[l - 1], 12LL * rows_out, nin_p)))
         return s;
-    for (int d = 1; d <= 4; ++d)
-        for (int p = 0; p < 3; ++p) {
-            FfTcPass &ps = a.pass[a.npass++];
-            ps.amap = 0; ps.a_y = -d * B; ps.a_x = 0;
-            ps.bmap = 1; ps.b_y = ((d - 1) * 3 + p) * rows_out; ps.b_x = 0;
-            ps.kblocks = nin_p / 64; ps.acc = 0;
-        }
+    // one pass per delay; the kernel multiplies its spike tile by the three
+    // weight parts, rows_out apart in the map
+    for (int d = 1; d <= 4; ++d) {
+        FfTcPass &ps = a.pass[a.npass++];
+        ps.amap = 0; ps.a_y = -d * B; ps.a_x = 0;
+        ps.bmap = 1; ps.b_y = (d - 1) * 3 * rows_out; ps.b_x = 0;
+        ps.kblocks = nin_p / 64; ps.acc = 0;
+    }
+    a.part_stride = rows_out;
     a.M = rows; a.N = nout;
     a.tiles_m = (rows + 127) / 128; a.tiles_n = (nout + 127) / 128; a.ksplit = 1;
     a.nacc = 1; a.mode = 0; a.C = c->ff_I; a.ldc = nout; a.cstride = 0; a.ctl = c->ctl;

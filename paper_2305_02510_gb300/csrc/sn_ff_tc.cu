@@ -14,14 +14,12 @@
 // FP32 (relative error near 2^-16 per product).
 //
 // The forward synaptic input I[r][j] = sum_d sum_i S[r - dB][i] W_d[i][j] runs
-// as 12 passes (4 delays x the three BF16 parts hi + mid + lo of each weight,
-// an exact split) over 0/1 spikes, so every product is exact.  Accumulating a
-// whole K loop in TMEM drifts: the tensor cores' FP32 accumulation lost enough
-// that 100-step membrane checkpoints left the state tolerance.  The forward
-// kernel therefore accumulates one 64-input block of all 12 passes at a time
-// in TMEM (double-buffered) and adds each block's partial sums in FP32 (round
-// to nearest) in registers of dedicated drain warps, as a sequential sum over
-// input blocks.
+// as 4 passes (one per delay), each multiplying a 0/1 spike tile by the three
+// BF16 parts hi + mid + lo of every weight (an exact split), so every product
+// is exact.  The forward kernel accumulates one 64-input block of all passes
+// at a time in TMEM (double-buffered) and adds each block's partial sums in
+// FP32 (round to nearest) in registers of dedicated drain warps: a sequential
+// sum over input blocks, so only 48 MMA steps ever accumulate in TMEM.
 //
 // One kernel runs a list of passes, each a K loop of 64-element (128-byte)
 // blocks of an A and a B tensor map at given coordinate offsets, into one of
@@ -216,14 +214,20 @@ __global__ void __launch_bounds__(kThreads, 1) ff_tc_kernel(const __grid_constan
 // it to accf[buf]; warps 4..11 (warp w: TMEM lane quarter w % 4, columns
 // 64 * ((w - 4) / 4) ..+63) add each block's partial into FP32 registers and
 // release the buffer through acce[buf] (8 arrivals).  Every pass has the
-// same number of K blocks; a.C[m][n] = the sum (mode 0 layout).
+// same number of K blocks; a.C[m][n] = the sum (mode 0 layout).  A pass
+// multiplies its A tile by kFwdParts B tiles (rows b_y + s * a.part_stride,
+// s = 0 .. kFwdParts-1: the parts of one weight split), so a stage holds one
+// A tile and kFwdParts B tiles and A is read once for all parts.
 constexpr int kFwdTcThreads = 384;
+constexpr int kFwdParts = 3;
+constexpr int kFwdStageBytes = (1 + kFwdParts) * kStageA;   // 64 KiB
+constexpr int kFwdSt = 3;
 
 __global__ void __launch_bounds__(kFwdTcThreads, 1) ff_tc_fwd_kernel(const __grid_constant__ FfTcMaps maps,
                                                                      FfTcArgs a) {
     extern __shared__ unsigned char smem_raw[];
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    __shared__ __align__(8) uint64_t full[kSt], empty[kSt], accf[2], acce[2];
+    __shared__ __align__(8) uint64_t full[kFwdSt], empty[kFwdSt], accf[2], acce[2];
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -231,7 +235,7 @@ __global__ void __launch_bounds__(kFwdTcThreads, 1) ff_tc_fwd_kernel(const __gri
     constexpr unsigned ncols = 256;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kSt; ++s) {
+        for (int s = 0; s < kFwdSt; ++s) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(smem_addr(&full[s])));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" :: "r"(smem_addr(&empty[s])));
         }
@@ -263,18 +267,21 @@ __global__ void __launch_bounds__(kFwdTcThreads, 1) ff_tc_fwd_kernel(const __gri
             for (int kb = 0; kb < KB && !s_abort; ++kb)
                 for (int p = 0; p < a.npass; ++p, ++g_prod) {
                     const FfTcPass &ps = a.pass[p];
-                    const int st = g_prod % kSt;
-                    const unsigned round = g_prod / kSt;
+                    const int st = g_prod % kFwdSt;
+                    const unsigned round = g_prod / kFwdSt;
                     if (round > 0 && !mbar_wait(smem_addr(&empty[st]), (round - 1) & 1u, a.ctl)) {
                         s_abort = 1;
                         break;
                     }
                     const uint32_t fb = smem_addr(&full[st]);
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
-                                 :: "r"(fb), "r"(kStageBytes) : "memory");
-                    const uint32_t dA = sbase + st * kStageBytes;
+                                 :: "r"(fb), "r"(kFwdStageBytes) : "memory");
+                    const uint32_t dA = sbase + st * kFwdStageBytes;
                     tma_load_2d(dA, &maps.m[ps.amap], ps.a_x + kb * kKB, ps.a_y + tm * kT, fb);
-                    tma_load_2d(dA + kStageA, &maps.m[ps.bmap], ps.b_x + kb * kKB, ps.b_y + tn * kT, fb);
+#pragma unroll
+                    for (int q = 0; q < kFwdParts; ++q)
+                        tma_load_2d(dA + (1 + q) * kStageA, &maps.m[ps.bmap], ps.b_x + kb * kKB,
+                                    ps.b_y + q * a.part_stride + tn * kT, fb);
                 }
         }
     } else if (warp == 1 && lane == 0) {
@@ -286,15 +293,18 @@ __global__ void __launch_bounds__(kFwdTcThreads, 1) ff_tc_fwd_kernel(const __gri
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 const uint32_t tacc = tmem + buf * kT;
                 for (int p = 0; p < a.npass; ++p, ++g_mma) {
-                    const int st = g_mma % kSt;
-                    const unsigned round = g_mma / kSt;
+                    const int st = g_mma % kFwdSt;
+                    const unsigned round = g_mma / kFwdSt;
                     if (!mbar_wait(smem_addr(&full[st]), round & 1u, a.ctl)) { s_abort = 1; break; }
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-                    const uint32_t dA = sbase + st * kStageBytes;
+                    const uint32_t dA = sbase + st * kFwdStageBytes;
 #pragma unroll
-                    for (int kk = 0; kk < 128 / 32; ++kk)
-                        mma_bf16(tacc, umma_desc_sw128(dA + kk * 32), umma_desc_sw128(dA + kStageA + kk * 32), idesc,
-                                 (p > 0) | (kk > 0));
+                    for (int q = 0; q < kFwdParts; ++q)
+#pragma unroll
+                        for (int kk = 0; kk < 128 / 32; ++kk)
+                            mma_bf16(tacc, umma_desc_sw128(dA + kk * 32),
+                                     umma_desc_sw128(dA + (1 + q) * kStageA + kk * 32), idesc,
+                                     (p > 0) | (q > 0) | (kk > 0));
                     mma_commit(smem_addr(&empty[st]));
                 }
                 mma_commit(smem_addr(&accf[buf]));
@@ -348,12 +358,12 @@ __global__ void __launch_bounds__(kFwdTcThreads, 1) ff_tc_fwd_kernel(const __gri
     // drain: copies issued and MMAs committed complete before shared memory and
     // TMEM go away (bounded waits; no-ops when the phases have completed)
     if (warp == 0 && lane == 0) {
-        for (unsigned i = g_prod > kSt ? g_prod - kSt : 0; i < g_prod; ++i)
-            mbar_wait(smem_addr(&full[i % kSt]), (i / kSt) & 1u, a.ctl);
+        for (unsigned i = g_prod > kFwdSt ? g_prod - kFwdSt : 0; i < g_prod; ++i)
+            mbar_wait(smem_addr(&full[i % kFwdSt]), (i / kFwdSt) & 1u, a.ctl);
     }
     if (warp == 1 && lane == 0) {
-        for (unsigned i = g_mma > kSt ? g_mma - kSt : 0; i < g_mma; ++i)
-            mbar_wait(smem_addr(&empty[i % kSt]), (i / kSt) & 1u, a.ctl);
+        for (unsigned i = g_mma > kFwdSt ? g_mma - kFwdSt : 0; i < g_mma; ++i)
+            mbar_wait(smem_addr(&empty[i % kFwdSt]), (i / kFwdSt) & 1u, a.ctl);
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
@@ -486,7 +496,7 @@ cudaError_t ff_tc_forward(const FfTcMaps &maps, const FfTcArgs &args, cudaStream
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     for (int p = 1; p < args.npass; ++p)
         if (args.pass[p].kblocks != args.pass[0].kblocks) return cudaErrorInvalidValue;
-    const size_t smem = ff_tc_smem_bytes();
+    const size_t smem = (size_t)kFwdSt * kFwdStageBytes + 1024;
     if ((e = cudaFuncSetAttribute((const void *)ff_tc_fwd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem)) != cudaSuccess)
         return e;

@@ -176,6 +176,7 @@ struct FfTcPass {
 };
 struct FfTcArgs {
     int M, N, tiles_m, tiles_n, ksplit, npass, nacc, mode;
+    int part_stride;                  // forward kernel: rows between the B parts of a pass
     FfTcPass pass[kFfTcMaxPasses];
     float *C;
     long long ldc, cstride;
