@@ -287,8 +287,9 @@ sn_status sn_get_weights(sn_ctx *ctx, float *w, int32_t on_device);
  * synapse weights).  on_device = 1: `w` is a device pointer, copied on the
  * stream without validation; 0: host memory (NaN rejected with SN_EINVAL),
  * copied before the call returns.  Delays and the state are kept.  A spike
- * delivered at step t uses the weight in place at t (as in the oracle's
- * delay registers): for a sparse context the call rebuilds the input of
+ * delivered at step t uses the weight in place at t (Section 2.2's delay
+ * registers carry the spike; the weight applies on delivery): for a sparse
+ * context the call rebuilds the input of
  * spikes still in flight from the raster, which must then hold the last
  * max_delay steps (record_steps >= max_delay, else SN_EUNSUPPORTED); a dense
  * context accepts new weights only at step 0 (after creation, sn_reset or an
