@@ -90,13 +90,14 @@ sn_status tc_weight_grad(sn_ctx *c, int l, float *dW) {
         (s = bf16_map(c, &maps.m[1], GT, nout, rows_p)) ||
         (s = bf16_map(c, &maps.m[2], GT + (size_t)nout * rows_p, nout, rows_p)))
         return s;
-    for (int d = 1; d <= 4; ++d)
-        for (int p = 0; p < 2; ++p) {
-            FfTcPass &ps = a.pass[a.npass++];
-            ps.amap = 0; ps.a_y = 0; ps.a_x = -d * B;
-            ps.bmap = 1 + p; ps.b_y = 0; ps.b_x = 0;
-            ps.kblocks = rows_p / 64; ps.acc = d - 1;
-        }
+    // one pass per delay: the shifted spike tile times both gradient parts
+    for (int d = 1; d <= 4; ++d) {
+        FfTcPass &ps = a.pass[a.npass++];
+        ps.amap = 0; ps.a_y = 0; ps.a_x = -d * B;
+        ps.bmap = 1; ps.b_y = 0; ps.b_x = 0;
+        ps.nb = 2; ps.bmap2 = 2; ps.b_y2 = 0;
+        ps.kblocks = rows_p / 64; ps.acc = d - 1;
+    }
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -132,14 +133,19 @@ sn_status tc_spike_grad(sn_ctx *c, int l) {
         (s = bf16_map(c, &maps.m[1], G + (size_t)rows * nout_p, rows, nout_p)) ||
         (s = bf16_map(c, &maps.m[2], c->ff_Wb[l - 1], 8LL * rows_in, nout_p)))
         return s;
-    static const int ga[3] = {0, 0, 1}, wb[3] = {0, 1, 0};   // (gradient part, weight part)
-    for (int d = 1; d <= 4; ++d)
-        for (int p = 0; p < 3; ++p) {
-            FfTcPass &ps = a.pass[a.npass++];
-            ps.amap = ga[p]; ps.a_y = d * B; ps.a_x = 0;
-            ps.bmap = 2; ps.b_y = ((d - 1) * 2 + wb[p]) * rows_in; ps.b_x = 0;
-            ps.kblocks = nout_p / 64; ps.acc = 0;
-        }
+    // per delay: hi gradient part times both weight parts, mid part times hi
+    for (int d = 1; d <= 4; ++d) {
+        FfTcPass &ps = a.pass[a.npass++];
+        ps.amap = 0; ps.a_y = d * B; ps.a_x = 0;
+        ps.bmap = 2; ps.b_y = (d - 1) * 2 * rows_in; ps.b_x = 0;
+        ps.nb = 2; ps.bmap2 = 2; ps.b_y2 = ((d - 1) * 2 + 1) * rows_in;
+        ps.kblocks = nout_p / 64; ps.acc = 0;
+        FfTcPass &pl = a.pass[a.npass++];
+        pl.amap = 1; pl.a_y = d * B; pl.a_x = 0;
+        pl.bmap = 2; pl.b_y = (d - 1) * 2 * rows_in; pl.b_x = 0;
+        pl.nb = 1;
+        pl.kblocks = nout_p / 64; pl.acc = 0;
+    }
     a.M = rows; a.N = nin;
     a.tiles_m = (rows + 127) / 128; a.tiles_n = (nin + 127) / 128; a.ksplit = 1;
     a.nacc = 1; a.mode = 0; a.C = c->ff_gS; a.ldc = nin; a.cstride = 0; a.ctl = c->ctl;

@@ -22,7 +22,8 @@
 // sum over input blocks, so only 48 MMA steps ever accumulate in TMEM.
 //
 // One kernel runs a list of passes, each a K loop of 64-element (128-byte)
-// blocks of an A and a B tensor map at given coordinate offsets, into one of
+// blocks of an A and one or two B tensor maps at given coordinate offsets
+// (both B tiles multiply the same A tile, which is loaded once), into one of
 // up to four TMEM accumulators of a 128 x 128 output tile.  The structure is
 // that of sn_shared.cu: warp 0 lane 0 issues TMA into a 6-stage ring, warp 1
 // lane 0 issues the MMAs, then all eight warps drain the accumulators through
@@ -43,9 +44,9 @@ namespace {
 
 constexpr int kT = 128;                         // tile rows (M) and columns (N)
 constexpr int kKB = 64;                         // BF16 elements of K per stage (128 bytes)
-constexpr int kSt = 6;
+constexpr int kSt = 4;
 constexpr int kStageA = kT * 128;               // 16 KiB
-constexpr int kStageBytes = 2 * kStageA;        // 32 KiB
+constexpr int kStageBytes = 3 * kStageA;        // A and up to two B tiles: 48 KiB
 constexpr int kThreads = 256;
 constexpr int kCPitch = kT + 4;                 // floats per staged output row
 
@@ -100,10 +101,12 @@ __global__ void __launch_bounds__(kThreads, 1) ff_tc_kernel(const __grid_constan
                     }
                     const uint32_t fb = smem_addr(&full[st]);
                     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n"
-                                 :: "r"(fb), "r"(kStageBytes) : "memory");
+                                 :: "r"(fb), "r"((1 + ps.nb) * kStageA) : "memory");
                     const uint32_t dA = sbase + st * kStageBytes;
                     tma_load_2d(dA, &maps.m[ps.amap], ps.a_x + kb * kKB, ps.a_y + tm * kT, fb);
                     tma_load_2d(dA + kStageA, &maps.m[ps.bmap], ps.b_x + kb * kKB, ps.b_y + tn * kT, fb);
+                    if (ps.nb > 1)
+                        tma_load_2d(dA + 2 * kStageA, &maps.m[ps.bmap2], ps.b_x + kb * kKB, ps.b_y2 + tn * kT, fb);
                 }
             }
         } else if (warp == 1 && lane == 0) {
@@ -120,11 +123,13 @@ __global__ void __launch_bounds__(kThreads, 1) ff_tc_kernel(const __grid_constan
                     if (!mbar_wait(smem_addr(&full[st]), round & 1u, a.ctl)) { s_abort = 1; break; }
                     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                     const uint32_t dA = sbase + st * kStageBytes;
+                    for (int q = 0; q < ps.nb; ++q) {
 #pragma unroll
-                    for (int kk = 0; kk < 128 / 32; ++kk) {
-                        const int on = ((started >> ps.acc) & 1) | (kk > 0);
-                        mma_bf16(tacc, umma_desc_sw128(dA + kk * 32), umma_desc_sw128(dA + kStageA + kk * 32),
-                                 idesc, on);
+                        for (int kk = 0; kk < 128 / 32; ++kk) {
+                            const int on = ((started >> ps.acc) & 1) | (q > 0) | (kk > 0);
+                            mma_bf16(tacc, umma_desc_sw128(dA + kk * 32),
+                                     umma_desc_sw128(dA + (1 + q) * kStageA + kk * 32), idesc, on);
+                        }
                     }
                     started |= 1 << ps.acc;
                     mma_commit(smem_addr(&empty[st]));
@@ -479,6 +484,8 @@ cudaError_t ff_tc_gemm(const FfTcMaps &maps, const FfTcArgs &args, cudaStream_t 
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    for (int p = 0; p < args.npass; ++p)
+        if (args.pass[p].nb < 1 || args.pass[p].nb > 2) return cudaErrorInvalidValue;
     const size_t smem = ff_tc_smem_bytes();
     if ((e = cudaFuncSetAttribute((const void *)ff_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem)) != cudaSuccess)

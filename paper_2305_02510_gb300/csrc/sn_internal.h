@@ -16,10 +16,10 @@ namespace sn {
 enum Kind { KIND_SPARSE = 0, KIND_DENSE = 1, KIND_BATCH = 2, KIND_SHARED_I8 = 3, KIND_FF = 4 };
 
 // Grid barrier state (one per context): the arrival count of the running
-// launch (zeroed before every launch that uses it); gen is unused padding.
+// launch, zeroed before every launch that uses it.
 struct GridBarrier {
     unsigned int count;
-    unsigned int gen;
+    unsigned int pad;
 };
 
 // Device-side control block: latched status word and run counters.
@@ -162,7 +162,8 @@ cudaError_t ff_dw(const float *gI, const unsigned *sprev, int words_in, const ui
 // Tensor-core contractions of the feedforward network (sn_ff_tc.cu).  A pass
 // is a K loop over `kblocks` 64-element blocks: A tile rows a_y + 128 * tm,
 // K a_x + 64 * kb of map amap; B tile rows b_y + 128 * tn, K b_x + 64 * kb of
-// map bmap; into accumulator acc.  mode 0: C[m][n] = acc 0; mode 1: C[m][n] =
+// map bmap (and, with nb = 2, a second B tile from bmap2 at rows b_y2 + 128 *
+// tn, multiplying the same A tile); into accumulator acc.  mode 0: C[m][n] = acc 0; mode 1: C[m][n] =
 // acc (D[m][n] - 1) (delay-selected weight gradient).  With ksplit > 1 the
 // work item of split ks covers its share of every pass's K blocks and writes
 // C + ks * cstride.
@@ -173,6 +174,7 @@ struct FfTcMaps {
 };
 struct FfTcPass {
     int amap, bmap, a_y, a_x, b_y, b_x, kblocks, acc;
+    int nb, bmap2, b_y2;              // B tiles per stage (1, or 2: the second from bmap2 at rows b_y2)
 };
 struct FfTcArgs {
     int M, N, tiles_m, tiles_n, ksplit, npass, nacc, mode;
