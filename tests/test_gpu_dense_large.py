@@ -30,8 +30,10 @@ def sample(n, rng, k=384):
     return np.unique(J[(J >= 0) & (J < n)])
 
 
-@pytest.mark.parametrize("n", [20000, 40000, 100000])
+@pytest.mark.parametrize("n", [20000, 20002, 40000, 40002, 60002, 100000])
 def test_huge_dense_sampled_teacher_forced(n):
+    """Column slabs of 64 (20,000), 128 (40,000) and 256 (60,002, 100,000)
+    columns; n % 4 != 0 takes the scalar gather."""
     from paper_2305_02510_gb300 import sn as S
     wl = W.huge_dense(n=n, steps=64)
     w = W.dense_weights_on_device(wl, torch)
@@ -107,3 +109,29 @@ def test_set_weights_then_run(prop):
     assert np.array_equal(np.asarray(v, np.float64), st.v)
     assert np.array_equal(np.asarray(r), st.r)
     assert want2.sum() > 0
+
+
+def test_dense_weights_change_only_at_step_zero():
+    from paper_2305_02510_gb300 import sn as S
+    wl = W.large_dense(n=64, steps=4)
+    ctx = S.from_workload(wl)
+    S.sn_run(ctx, 2)
+    with pytest.raises(S.SnError) as e:
+        S.sn_set_weights(ctx, np.zeros(64 * 64, np.float32))
+    assert e.value.status == S.SN_ESTATE
+    S.sn_reset(ctx)
+    S.sn_set_weights(ctx, np.zeros(64 * 64, np.float32))
+
+
+def test_ff_engine_choice():
+    from paper_2305_02510_gb300 import sn as S
+    task = W.bptt_task(batch=3, sizes=(20, 10), steps=5, seed=1)
+    from paper_2305_02510_gb300 import bptt
+    net = bptt.FFNet.from_task(task)
+    with pytest.raises(S.SnError) as e:             # batch 3: not a multiple of 8
+        S.sn_ff_set_engine(net.ctx, S.SN_FF_TENSOR)
+    assert e.value.status == S.SN_EUNSUPPORTED
+    with pytest.raises(S.SnError) as e:
+        S.sn_ff_set_engine(net.ctx, 7)
+    assert e.value.status == S.SN_EINVAL
+    S.sn_ff_set_engine(net.ctx, S.SN_FF_SIMT)
