@@ -94,3 +94,27 @@ def test_version_and_null_handles(S):
     assert L.sn_set_propagation(None, S.SN_PULL) == S.SN_EINVAL
     assert L.sn_get_propagation(None, None) == S.SN_EINVAL
     L.sn_destroy(None)
+
+
+def test_new_entry_points_reject_bad_arguments(S):
+    """sn_set_weights, sn_ff_set_engine and sn_create_axonal validate their
+    arguments before any CUDA call."""
+    L = S.lib()
+    assert L.sn_set_weights(None, None, 0) == S.SN_EINVAL
+    assert L.sn_ff_set_engine(None, S.SN_FF_TENSOR) == S.SN_EINVAL
+    keep = []
+    n = 4
+    nr, _ = _neurons(S, n, keep)
+    pre, post = np.array([0, 1], np.int32), np.array([1, 2], np.int32)
+    w, d = np.array([1.0, 1.0], np.float32), np.array([1, 2], np.int32)
+    sy = S.sn_synapses()
+    sy.m = 2
+    sy.pre, sy.post, sy.weight, sy.delay = pre.ctypes.data, post.ctypes.data, w.ctypes.data, d.ctypes.data
+    cfg = S.sn_config()
+    cfg.dtype, cfg.max_delay, cfg.flags, cfg.record_steps = 0, 3, 0, 0
+    h = C.c_void_p()
+    for ax, frag in (([0, 2, 0, 0], "axonal"), ([-1, 0, 0, 0], "axonal"), ([3, 0, 0, 0], "axonal")):
+        a = np.array(ax, np.int32)
+        st = L.sn_create_axonal(C.byref(cfg), C.byref(nr), C.byref(sy), a.ctypes.data, C.byref(h))
+        assert st == S.SN_EINVAL, ax
+        assert frag in L.sn_last_error(None).decode()
