@@ -17,7 +17,11 @@
 // and stage the tile's neuron parameters in shared memory.  Afterwards the
 // sixteen warps read the accumulator rows (tcgen05.ld: warps w, w+4, w+8 and
 // w+12 share TMEM lane quarter w, each taking 32 columns) and apply the integer LIF
-// rule (Section 2.1 order).  The state is neuron-major ([n][B]: lane = train,
+// rule (Section 2.1 order).  When every block holds one tile for the whole
+// launch (tiles <= blocks), the tile's V and r stay in TMEM next to the
+// accumulator (columns 128.. and 256..), read from global memory at the
+// launch's start and written back at its end; otherwise they make the round
+// trip every step.  The global state is neuron-major ([n][B]: lane = train,
 // so every load and store of V and r is one 128-byte line per warp); the
 // spike bytes that are the next step's A operand go through a shared-memory
 // transpose and leave as whole 128-byte rows.  A persistent cooperative
@@ -50,6 +54,11 @@ constexpr int kSub = 4;                      // state columns loaded together
 constexpr int kSaPitch = 144;                  // 128 B + 16: conflict-free 16-byte stores
 constexpr int kEpiBytes = kTM * kSaPitch + 2 * kTM * 4 * 4 + 5 * kTN * 4;
 constexpr unsigned kTmemCols = 128;
+// When every block holds one tile for the whole launch, the tile's state
+// stays in TMEM between steps: V at columns kVCol + c, r at kRCol + c of the
+// train's lane (512 columns allocated: the accumulator's 128 and 256 of state).
+constexpr unsigned kTmemColsRes = 512;
+constexpr uint32_t kVCol = 128, kRCol = 256;
 
 struct SharedArgs {
     int n, B, t0, steps, cap, words;
@@ -64,6 +73,7 @@ struct SharedArgs {
     Control *ctl;
 };
 
+template <bool kRes>
 __global__ void __launch_bounds__(kShThreads, 1)
 shared_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ CUtensorMap tmA1,
               const __grid_constant__ CUtensorMap tmW, SharedArgs a) {
@@ -90,15 +100,35 @@ shared_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ 
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         s_abort = 0;
     }
+    constexpr unsigned kCols = kRes ? kTmemColsRes : kTmemCols;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n"
-                     :: "r"(smem_addr(&s_tmem)), "r"(kTmemCols));
+                     :: "r"(smem_addr(&s_tmem)), "r"(kCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     const uint32_t tmem = s_tmem;
+    const int quarter = warp & 3, part = warp >> 2;
+    const int bl = quarter * 32 + lane;                // tile row = TMEM lane
+    const uint32_t trow = tmem + ((uint32_t)(quarter * 32) << 16);   // this warp's lane quarter
+    if (kRes && blockIdx.x < a.tiles) {
+        // the block's one tile: its state into TMEM for the whole launch
+        const int m0 = (blockIdx.x % a.tiles_m) * kTM, n0 = (blockIdx.x / a.tiles_m) * kTN;
+        for (int h = 0; h < kEpiCols / 16; ++h) {
+            const int c0 = part * kEpiCols + h * 16;
+            const int *Vp = a.V + (size_t)(n0 + c0) * a.B + m0 + bl;
+            const int *rp = a.r + (size_t)(n0 + c0) * a.B + m0 + bl;
+            uint32_t vv[16], rr[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                vv[q] = (uint32_t)__ldcg(Vp + (size_t)q * a.B);
+                rr[q] = (uint32_t)__ldcg(rp + (size_t)q * a.B);
+            }
+            tmem_st16x2(trow + kVCol + c0, trow + kRCol + c0, vv, rr);
+        }
+    }
     const int kblocks = a.n / kTK;
     constexpr uint32_t idesc = idesc_e4m3_f32(kTM, kTN);
     unsigned g_prod = 0, g_mma = 0, tiles_done = 0;
@@ -171,50 +201,81 @@ shared_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ 
             if (!ok) s_abort = 1;
             __syncthreads();                   // Poisson bits and parameters staged
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-            const int quarter = warp & 3, part = warp >> 2;
-            const int bl = quarter * 32 + lane;            // tile row = TMEM lane
             const int b = m0 + bl;
             for (int cc = 0; cc < kEpiCols / 32; ++cc) {
                 const int c0 = part * kEpiCols + cc * 32;  // tile column of register 0
-                uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0, v);
-                if (!ok) continue;
-                const int j0 = n0 + c0;
-                // column q of this train at V[(j0 + q) * B + b], in groups of kSub
-                // columns whose loads are issued together
-                int *Vp = a.V + (size_t)j0 * a.B + b;
-                int *rp = a.r + (size_t)j0 * a.B + b;
                 const unsigned pb = sP[bl * 4 + (c0 >> 5)];
                 unsigned bits = 0;
                 uint32_t outw[8];
+                if constexpr (kRes) {
+                    // accumulator and state from TMEM, state back, 16
+                    // columns at a time (the stores run even after a failed
+                    // wait: tcgen05.st is warp-collective)
 #pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const uint32_t col = (uint32_t)(c0 + 16 * h);
+                        uint32_t v[16], vv[16], rr[16];
+                        tmem_ld16x3(trow + col, trow + kVCol + col, trow + kRCol + col, v, vv, rr);
+                        if (ok) {
 #pragma unroll
-                for (int h = 0; h < 32 / kSub; ++h) {
-                    int vin[kSub], rin[kSub];
+                            for (int q4 = 0; q4 < 4; ++q4) {
+                                uint32_t bytes = 0;
 #pragma unroll
-                    for (int q = 0; q < kSub; ++q) {
-                        vin[q] = __ldcg(Vp + (unsigned)((h * kSub + q) * a.B));
-                        rin[q] = __ldcg(rp + (unsigned)((h * kSub + q) * a.B));
-                    }
-#pragma unroll
-                    for (int q4 = 0; q4 < kSub / 4; ++q4) {
-                        uint32_t bytes = 0;
-#pragma unroll
-                        for (int e = 0; e < 4; ++e) {
-                            const int qq = q4 * 4 + e, q = h * kSub + qq, c = c0 + q;
-                            const int acc = __float2int_rn(__uint_as_float(v[q]));
-                            const int ext = ((pb >> q) & 1u) ? sAmp[c] : 0;
-                            const bool fire = lif_update_i32(vin[qq], rin[qq], acc, ext, sTh[c], sLk[c], sRs[c],
-                                                             sRf[c], overflow);
-                            bits |= (unsigned)fire << q;
-                            bytes |= (fire ? 0x38u : 0u) << (8 * e);      // E4M3 1.0
+                                for (int e = 0; e < 4; ++e) {
+                                    const int qq = q4 * 4 + e, q = h * 16 + qq, c = c0 + q;
+                                    const int acc = __float2int_rn(__uint_as_float(v[qq]));
+                                    const int ext = ((pb >> q) & 1u) ? sAmp[c] : 0;
+                                    int vq = (int)vv[qq], rq = (int)rr[qq];
+                                    const bool fire = lif_update_i32(vq, rq, acc, ext, sTh[c], sLk[c], sRs[c],
+                                                                     sRf[c], overflow);
+                                    vv[qq] = (uint32_t)vq;
+                                    rr[qq] = (uint32_t)rq;
+                                    bits |= (unsigned)fire << q;
+                                    bytes |= (fire ? 0x38u : 0u) << (8 * e);      // E4M3 1.0
+                                }
+                                outw[h * 4 + q4] = bytes;
+                            }
                         }
-                        outw[h * (kSub / 4) + q4] = bytes;
+                        tmem_st16x2(trow + kVCol + col, trow + kRCol + col, vv, rr);
                     }
+                    if (!ok) continue;
+                } else {
+                    uint32_t v[32];
+                    tmem_ld32(trow + (uint32_t)c0, v);
+                    if (!ok) continue;
+                    const int j0 = n0 + c0;
+                    // column q of this train at V[(j0 + q) * B + b], in groups of kSub
+                    // columns whose loads are issued together
+                    int *Vp = a.V + (size_t)j0 * a.B + b;
+                    int *rp = a.r + (size_t)j0 * a.B + b;
 #pragma unroll
-                    for (int q = 0; q < kSub; ++q) {
-                        __stcg(Vp + (unsigned)((h * kSub + q) * a.B), vin[q]);
-                        __stcg(rp + (unsigned)((h * kSub + q) * a.B), rin[q]);
+                    for (int h = 0; h < 32 / kSub; ++h) {
+                        int vin[kSub], rin[kSub];
+#pragma unroll
+                        for (int q = 0; q < kSub; ++q) {
+                            vin[q] = __ldcg(Vp + (unsigned)((h * kSub + q) * a.B));
+                            rin[q] = __ldcg(rp + (unsigned)((h * kSub + q) * a.B));
+                        }
+#pragma unroll
+                        for (int q4 = 0; q4 < kSub / 4; ++q4) {
+                            uint32_t bytes = 0;
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                const int qq = q4 * 4 + e, q = h * kSub + qq, c = c0 + q;
+                                const int acc = __float2int_rn(__uint_as_float(v[q]));
+                                const int ext = ((pb >> q) & 1u) ? sAmp[c] : 0;
+                                const bool fire = lif_update_i32(vin[qq], rin[qq], acc, ext, sTh[c], sLk[c], sRs[c],
+                                                                 sRf[c], overflow);
+                                bits |= (unsigned)fire << q;
+                                bytes |= (fire ? 0x38u : 0u) << (8 * e);      // E4M3 1.0
+                            }
+                            outw[h * (kSub / 4) + q4] = bytes;
+                        }
+#pragma unroll
+                        for (int q = 0; q < kSub; ++q) {
+                            __stcg(Vp + (unsigned)((h * kSub + q) * a.B), vin[q]);
+                            __stcg(rp + (unsigned)((h * kSub + q) * a.B), rin[q]);
+                        }
                     }
                 }
                 uint4 *dst = (uint4 *)(sA + bl * kSaPitch + c0);
@@ -262,7 +323,26 @@ shared_kernel(const __grid_constant__ CUtensorMap tmA0, const __grid_constant__ 
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(tmem), "r"(kTmemCols));
+    if (kRes && blockIdx.x < a.tiles) {
+        // the tile's state back to its neuron-major arrays
+        const int m0 = (blockIdx.x % a.tiles_m) * kTM, n0 = (blockIdx.x / a.tiles_m) * kTN;
+        for (int h = 0; h < kEpiCols / 16; ++h) {
+            const int c0 = part * kEpiCols + h * 16;
+            int *Vp = a.V + (size_t)(n0 + c0) * a.B + m0 + bl;
+            int *rp = a.r + (size_t)(n0 + c0) * a.B + m0 + bl;
+            uint32_t vv[16], rr[16];
+            tmem_ld16x2(trow + kVCol + c0, trow + kRCol + c0, vv, rr);
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                __stcg(Vp + (size_t)q * a.B, (int)vv[q]);
+                __stcg(rp + (size_t)q * a.B, (int)rr[q]);
+            }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    }
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" :: "r"(tmem), "r"(kCols));
     if (overflow) atomicCAS(&a.ctl->status, 0, (int)SN_EOVERFLOW);
     if (my_spikes) {
         atomicAdd(&a.ctl->spikes, my_spikes);
@@ -292,10 +372,11 @@ cudaError_t max_grid_shared(int *grid) {
     if (e != cudaSuccess) return e;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute((const void *)shared_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)shared_smem_bytes());
-    if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void *)shared_kernel, kShThreads,
+    for (const void *f : {(const void *)shared_kernel<false>, (const void *)shared_kernel<true>}) {
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shared_smem_bytes());
+        if (e != cudaSuccess) return e;
+    }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, (const void *)shared_kernel<false>, kShThreads,
                                                       shared_smem_bytes());
     if (e != cudaSuccess) return e;
     // one block per SM: TMEM columns and the 128 KiB pipeline are per block
@@ -317,8 +398,9 @@ cudaError_t launch_shared(const void *tmaps, const SharedHostArgs &h, int grid, 
     // the grid barrier's arrival count starts every launch at zero
     cudaError_t e = cudaMemsetAsync(&h.ctl->bar, 0, sizeof(GridBarrier), s);
     if (e != cudaSuccess) return e;
-    return cudaLaunchCooperativeKernel((const void *)shared_kernel, dim3(g), dim3(kShThreads), args,
-                                       shared_smem_bytes(), s);
+    // one tile per block for the whole launch: the state stays in TMEM
+    const void *f = g == a.tiles ? (const void *)shared_kernel<true> : (const void *)shared_kernel<false>;
+    return cudaLaunchCooperativeKernel(f, dim3(g), dim3(kShThreads), args, shared_smem_bytes(), s);
 }
 
 }  // namespace sn

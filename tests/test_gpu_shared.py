@@ -42,7 +42,10 @@ def train_raster(bits, n, b):
 
 
 @pytest.mark.parametrize("n,B,T,trains", [(256, 128, 60, range(128)), (384, 256, 40, range(0, 256, 9)),
-                                           (1024, 128, 30, range(0, 128, 17))])
+                                           (1024, 128, 30, range(0, 128, 17)),
+                                           # 160 tiles of 128 x 128: more tiles than blocks, so the
+                                           # state goes through global memory between steps
+                                           (2048, 1280, 20, range(0, 1280, 97))])
 def test_shared_bit_exact(n, B, T, trains):
     wl = W.shared_dense_i8(n=n, batch=B, steps=T)
     _, bits, v, r = run(wl, T)
