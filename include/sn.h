@@ -308,7 +308,12 @@ sn_status sn_get_counters(sn_ctx *ctx, int64_t *steps, int64_t *spikes, int64_t 
  * are due, STDP traces, weights, counters) into
  * buf.  sn_load restores it into a context created with the same network.
  * A run of T steps equals a run of T1 steps, save, load into a fresh
- * context, and a run of T - T1 steps. */
+ * context, and a run of T - T1 steps.  Single sparse and dense networks,
+ * batched networks (state and pending input of every network; the synapses
+ * never change) and the shared dense network (every train's state and the
+ * previous step's spikes); feedforward contexts return SN_ESTATE.  sn_load
+ * returns SN_EINVAL for a checkpoint of another kind, dtype, size, synapse
+ * count, delay range, network count or train count. */
 sn_status sn_save(sn_ctx *ctx, void *buf, size_t *size);
 sn_status sn_load(sn_ctx *ctx, const void *buf, size_t size);
 

@@ -825,23 +825,41 @@ sn_status sn_get_counters(sn_ctx *c, int64_t *steps, int64_t *spikes, int64_t *e
 // deliveries may be due), counters in the header.
 struct SaveHeader {
     char magic[8];
-    int kind, dtype, n, D1, S, has_trace, has_hist, pad;
+    int kind, dtype, n, D1, S, has_trace, has_hist;
+    int count;                // batched: networks; shared: input trains; else 0
     long long m, step;
     unsigned long long spikes, events;
 };
 
+static int save_count(const sn_ctx *c) {
+    return c->kind == KIND_BATCH ? c->nets : c->kind == KIND_SHARED_I8 ? c->sh_B : 0;
+}
+
+// Checkpoint layout after the header, by kind:
+//   sparse:  V, r, ring, synapse store, [traces], [spike history]
+//   dense:   V, r, ring, spike words, W, [traces]
+//   batched: V, r, ring (the synapses never change)
+//   shared:  V, r ([n][trains]), both spike operands (the weights never change)
 static size_t save_size(const sn_ctx *c, bool has_trace, bool has_hist) {
+    if (c->kind == KIND_SHARED_I8) {
+        const size_t bn = (size_t)c->sh_B * c->n;
+        return sizeof(SaveHeader) + bn * 8 + bn * 2;
+    }
     size_t s = sizeof(SaveHeader) + (size_t)c->n * 8 + c->ring_bytes;
     if (c->kind == KIND_DENSE) s += (size_t)2 * c->words * 4 + (size_t)c->n * c->n * 4;
-    else s += (size_t)(c->m > 0 ? c->m : 0) * 8;
+    else if (c->kind == KIND_SPARSE) s += (size_t)(c->m > 0 ? c->m : 0) * 8;
     if (has_trace) s += (size_t)3 * c->n * 4;
     if (has_hist) s += (size_t)c->D * c->words * 4;
     return s;
 }
 
+static bool can_save(const sn_ctx *c) {
+    return c->kind == KIND_SPARSE || c->kind == KIND_DENSE || c->kind == KIND_BATCH || c->kind == KIND_SHARED_I8;
+}
+
 sn_status sn_save(sn_ctx *c, void *buf, size_t *size) {
     if (!c || !size) return fail(c, SN_EINVAL, "NULL argument");
-    if (c->kind != KIND_SPARSE && c->kind != KIND_DENSE) return fail(c, SN_ESTATE, "wrong context kind");
+    if (!can_save(c)) return fail(c, SN_ESTATE, "wrong context kind");
     const bool has_hist = c->kind == KIND_SPARSE && c->hist_live;
     const size_t need = save_size(c, c->trace != nullptr, has_hist);
     if (!buf) { *size = need; return SN_OK; }
@@ -856,6 +874,7 @@ sn_status sn_save(sn_ctx *c, void *buf, size_t *size) {
     memcpy(hd.magic, "SNCKPT2", 8);
     hd.kind = c->kind; hd.dtype = c->dtype; hd.n = c->n; hd.D1 = c->D1; hd.S = c->S;
     hd.has_trace = c->trace != nullptr; hd.has_hist = has_hist; hd.m = c->m; hd.step = c->step;
+    hd.count = save_count(c);
     hd.spikes = h.spikes; hd.events = h.events;
     uint8_t *p = (uint8_t *)buf;
     memcpy(p, &hd, sizeof(hd)); p += sizeof(hd);
@@ -865,12 +884,19 @@ sn_status sn_save(sn_ctx *c, void *buf, size_t *size) {
         return e;
     };
     cudaError_t e;
+    if (c->kind == KIND_SHARED_I8) {
+        const size_t bn = (size_t)c->sh_B * c->n;
+        if ((e = get(c->V, bn * 4)) || (e = get(c->r, bn * 4)) || (e = get(c->sh_A0, bn)) || (e = get(c->sh_A1, bn)))
+            return cuda_fail(c, e, "save");
+        *size = need;
+        return SN_OK;
+    }
     if ((e = get(c->V, (size_t)c->n * 4)) || (e = get(c->r, (size_t)c->n * 4)) || (e = get(c->ring, c->ring_bytes)))
         return cuda_fail(c, e, "save");
     if (c->kind == KIND_DENSE) {
         if ((e = get(c->spk, (size_t)2 * c->words * 4)) || (e = get(c->W, (size_t)c->n * c->n * 4)))
             return cuda_fail(c, e, "save");
-    } else if (c->m > 0 && (e = get(c->syn, (size_t)c->m * 8))) {
+    } else if (c->kind == KIND_SPARSE && c->m > 0 && (e = get(c->syn, (size_t)c->m * 8))) {
         return cuda_fail(c, e, "save");
     }
     if (c->trace && (e = get(c->trace, (size_t)3 * c->n * 4))) return cuda_fail(c, e, "save");
@@ -885,8 +911,10 @@ sn_status sn_load(sn_ctx *c, const void *buf, size_t size) {
     SaveHeader hd;
     memcpy(&hd, buf, sizeof(hd));
     if (memcmp(hd.magic, "SNCKPT2", 8) != 0) return fail(c, SN_EINVAL, "not a checkpoint");
+    if (!can_save(c)) return fail(c, SN_ESTATE, "wrong context kind");
     if (hd.kind != c->kind || hd.dtype != c->dtype || hd.n != c->n || hd.D1 != c->D1 || hd.m != c->m ||
-        hd.S != c->S || (hd.has_hist && c->kind != KIND_SPARSE))
+        hd.S != c->S || hd.count != save_count(c) || (hd.has_hist && c->kind != KIND_SPARSE) ||
+        (hd.has_trace && c->kind != KIND_SPARSE && c->kind != KIND_DENSE))
         return fail(c, SN_EINVAL, "checkpoint is of a different network");
     if (size < save_size(c, hd.has_trace != 0, hd.has_hist != 0)) return fail(c, SN_EINVAL, "checkpoint truncated");
     sn_status s;
@@ -900,12 +928,19 @@ sn_status sn_load(sn_ctx *c, const void *buf, size_t size) {
         return e;
     };
     cudaError_t e;
-    if ((e = put(c->V, (size_t)c->n * 4)) || (e = put(c->r, (size_t)c->n * 4)) || (e = put(c->ring, c->ring_bytes)))
-        return cuda_fail(c, e, "load");
+    if (c->kind == KIND_SHARED_I8) {
+        const size_t bn = (size_t)c->sh_B * c->n;
+        if ((e = put(c->V, bn * 4)) || (e = put(c->r, bn * 4)) || (e = put(c->sh_A0, bn)) || (e = put(c->sh_A1, bn)))
+            return cuda_fail(c, e, "load");
+    } else {
+        if ((e = put(c->V, (size_t)c->n * 4)) || (e = put(c->r, (size_t)c->n * 4)) ||
+            (e = put(c->ring, c->ring_bytes)))
+            return cuda_fail(c, e, "load");
+    }
     if (c->kind == KIND_DENSE) {
         if ((e = put(c->spk, (size_t)2 * c->words * 4)) || (e = put(c->W, (size_t)c->n * c->n * 4)))
             return cuda_fail(c, e, "load");
-    } else if (c->m > 0 && (e = put(c->syn, (size_t)c->m * 8))) {
+    } else if (c->kind == KIND_SPARSE && c->m > 0 && (e = put(c->syn, (size_t)c->m * 8))) {
         return cuda_fail(c, e, "load");
     }
     if (hd.has_trace && (e = put(c->trace, (size_t)3 * c->n * 4))) return cuda_fail(c, e, "load");

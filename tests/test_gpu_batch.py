@@ -123,3 +123,32 @@ def test_batch_full_size_sampled():
         wl = nets[b]
         got = s.unpack_raster(np.ascontiguousarray(bits[:, woff[b]:woff[b + 1]]), wl["n"])
         compare.check_float_run(wl, got, v[off[b]:off[b + 1]], r[off[b]:off[b + 1]], 500, net_index=b)
+
+
+@pytest.mark.parametrize("kind", ["int", "float"])
+def test_batch_checkpoint_resume_bit_exact(kind):
+    """run(T) equals run(T1); save; load into a fresh context; run(T - T1):
+    every network's spikes, state and the counters."""
+    s = S()
+    nets = int_nets(20, seed=3) if kind == "int" else W.batched_nets(count=24, steps=150)
+    T, T1 = 150, 61
+    ctx = s.from_batch_workloads(nets, record_steps=T)
+    s.sn_run(ctx, T)
+    want = s.sn_get_spikes(ctx, 0, T)
+    v_want, r_want = s.sn_get_state(ctx)
+    a = s.from_batch_workloads(nets, record_steps=T)
+    s.sn_run(a, T1)
+    first = s.sn_get_spikes(a, 0, T1)
+    blob = s.sn_save(a)
+    b = s.from_batch_workloads(nets, record_steps=T)
+    s.sn_load(b, blob)
+    s.sn_run(b, T - T1)
+    second = s.sn_get_spikes(b, T1, T)
+    v, r = s.sn_get_state(b)
+    assert np.array_equal(np.concatenate([first, second]), want)
+    assert np.array_equal(v, v_want) and np.array_equal(r, r_want)
+    assert tuple(s.sn_get_counters(b)) == tuple(s.sn_get_counters(ctx))
+    # a checkpoint of another set of networks is refused
+    other = s.from_batch_workloads(nets[:-1], record_steps=T)
+    with pytest.raises(s.SnError):
+        s.sn_load(other, blob)

@@ -75,6 +75,32 @@ def test_shared_equals_plain_dense_path():
         assert np.array_equal(vv.astype(np.int64), v[b].astype(np.int64)) and np.array_equal(rr, r[b])
 
 
+def test_shared_checkpoint_resume_bit_exact():
+    """run(T) equals run(T1); save; load into a fresh context; run(T - T1):
+    every train's spikes, the state and the counters."""
+    s = S()
+    T, T1 = 60, 23
+    wl = W.shared_dense_i8(n=384, batch=256, steps=T)
+    ctx, _, v_want, r_want = run(wl, T)
+    want = s.sn_get_spikes(ctx, 0, T)
+    a = s.from_shared_workload(wl, record_steps=T)
+    s.sn_run(a, T1)
+    first = s.sn_get_spikes(a, 0, T1)
+    blob = s.sn_save(a)
+    b = s.from_shared_workload(wl, record_steps=T)
+    s.sn_load(b, blob)
+    s.sn_run(b, T - T1)
+    second = s.sn_get_spikes(b, T1, T)
+    v, r = s.sn_get_state(b)
+    assert np.array_equal(np.concatenate([first, second]), want)
+    assert np.array_equal(v.reshape(v_want.shape), v_want) and np.array_equal(r.reshape(r_want.shape), r_want)
+    assert tuple(s.sn_get_counters(b)) == tuple(s.sn_get_counters(ctx))
+    # a checkpoint with another number of trains is refused
+    other = s.from_shared_workload(W.shared_dense_i8(n=384, batch=128, steps=T), record_steps=T)
+    with pytest.raises(s.SnError):
+        s.sn_load(other, blob)
+
+
 def test_shared_full_size_sampled():
     """8192 neurons x 256 trains, 500 steps: two trains bit-exact over the
     first 12 steps, then teacher-forced single steps of sampled trains."""
