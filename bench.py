@@ -377,14 +377,14 @@ def bptt_extra(S, W, torch, stream):
     syn = sum(a * b for a, b in zip(sizes[:-1], sizes[1:]))
     # tensor-core work of one step as executed (padded tiles: K to 64, N to 128
     # for the forward and spike gradient, M to 128 for the weight gradient):
-    # forward and its recomputation 12 passes each, spike gradient 12 passes
-    # (layers above the first), weight gradient 8 passes
+    # forward 12 passes (its synaptic input is kept for the backward), spike
+    # gradient 12 passes (layers above the first), weight gradient 8 passes
     rows = task["steps"] * task["batch"]
     up = lambda x, m: (x + m - 1) // m * m
     flop = 0
     for l in range(1, len(sizes)):
         nin, nout = sizes[l - 1], sizes[l]
-        flop += 2 * 12 * 2 * rows * up(nin, 64) * up(nout, 128)
+        flop += 12 * 2 * rows * up(nin, 64) * up(nout, 128)
         if l > 1:
             flop += 12 * 2 * rows * up(nout, 64) * up(nin, 128)
         flop += 8 * 2 * up(nin, 128) * up(nout, 128) * up(rows, 64)

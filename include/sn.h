@@ -81,6 +81,10 @@ typedef enum {
 #define SN_PROP_PULL 4u     /* sn_create only: start with pull propagation (see
                                sn_set_propagation); SN_EUNSUPPORTED if the
                                network does not fit it                             */
+#define SN_FF_RECOMPUTE 8u  /* sn_create_ff only: sn_backward recomputes each
+                               layer's synaptic input instead of keeping it from
+                               the forward (saves steps * batch * sum(sizes[1..])
+                               floats of device memory)                            */
 
 #define SN_MAX_DELAY 64     /* largest supported synaptic delay                    */
 
@@ -350,7 +354,11 @@ typedef struct {
 } sn_ff_params;
 
 /* delays[l] (host, [sizes[l]][sizes[l+1]] bytes for layer l+1) are copied.
- * batch >= 1, steps >= 1; every size in 1..65536. */
+ * batch >= 1, steps >= 1; every size in 1..65536.  By default the forward
+ * keeps every layer's synaptic input [steps * batch][sizes[l]] for the
+ * backward; with SN_FF_RECOMPUTE in cfg->flags (or when that memory cannot
+ * be allocated) the backward recomputes it with the forward's own kernel.
+ * Both give identical results. */
 sn_status sn_create_ff(const sn_config *cfg, int32_t layers, const int32_t *sizes,
                        const uint8_t *const *delays, const sn_ff_params *params, int32_t batch,
                        int32_t steps, sn_ctx **out);

@@ -15,14 +15,17 @@ class FFNet:
     shared neuron parameters are fixed; the weights are passed per call."""
 
     def __init__(self, sizes, delays, *, batch, steps, threshold=1.0, leak=0.05, reset=0.0,
-                 refractory=0, slope=10.0, checkpoint_every=10, device="cuda", engine=None):
+                 refractory=0, slope=10.0, checkpoint_every=10, device="cuda", engine=None,
+                 recompute=False):
         """engine: None or "auto" (tensor cores where the shapes allow), "simt"
-        or "tensor" (sn_ff_set_engine)."""
+        or "tensor" (sn_ff_set_engine).  recompute: the backward recomputes
+        each layer's synaptic input instead of keeping it from the forward."""
         self.device = torch.device(device)
         self.stream = torch.cuda.current_stream(self.device)
         self.ctx = S.sn_create_ff(sizes, delays, threshold=threshold, leak=leak, reset=reset,
                                   refractory=refractory, slope=slope, checkpoint_every=checkpoint_every,
-                                  batch=batch, steps=steps, stream=self.stream.cuda_stream)
+                                  batch=batch, steps=steps, stream=self.stream.cuda_stream,
+                                  recompute=recompute)
         if engine is not None:
             S.sn_ff_set_engine(self.ctx, {"auto": S.SN_FF_AUTO, "simt": S.SN_FF_SIMT,
                                           "tensor": S.SN_FF_TENSOR}[engine])

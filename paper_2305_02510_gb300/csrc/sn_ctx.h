@@ -90,6 +90,7 @@ struct sn_ctx {
     std::vector<void *> ff_DM;         // device delay bit masks per layer
     std::vector<unsigned *> ff_S;      // device spike bits per layer (0 = input)
     std::vector<float *> ff_vck;
+    std::vector<float *> ff_Ik;        // per layer: the forward's synaptic input (empty: recompute)
     std::vector<int *> ff_rck;
     float *ff_I = nullptr, *ff_gI = nullptr, *ff_gS = nullptr, *ff_part = nullptr;
     std::vector<const float *> ff_w;   // weights of the last forward (caller's device memory)

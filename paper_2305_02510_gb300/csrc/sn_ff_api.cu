@@ -42,7 +42,7 @@ bool use_tc(const sn_ctx *c) { return c->ff_tc_ok && c->ff_engine != SN_FF_SIMT;
 // 4 delays x 3 exact BF16 weight parts (4 passes of 3 parts each), accumulated
 // block by block (ff_tc_forward).  Unpacks the previous layer's spikes, and their transpose
 // when the weight gradient will need it.
-sn_status tc_forward(sn_ctx *c, int l, bool want_st) {
+sn_status tc_forward(sn_ctx *c, int l, bool want_st, float *I) {
     const int B = c->ff_batch, rows = B * c->ff_steps;
     const int nin = c->ff_sizes[l - 1], nout = c->ff_sizes[l];
     const int nin_p = up(nin, 64), rows_out = up(nout, 128), rows_p = up(rows, 64);
@@ -68,7 +68,7 @@ sn_status tc_forward(sn_ctx *c, int l, bool want_st) {
     a.part_stride = rows_out;
     a.M = rows; a.N = nout;
     a.tiles_m = (rows + 127) / 128; a.tiles_n = (nout + 127) / 128; a.ksplit = 1;
-    a.nacc = 1; a.mode = 0; a.C = c->ff_I; a.ldc = nout; a.cstride = 0; a.ctl = c->ctl;
+    a.nacc = 1; a.mode = 0; a.C = I; a.ldc = nout; a.cstride = 0; a.ctl = c->ctl;
     if ((e = ff_tc_forward(maps, a, c->stream)) != cudaSuccess) return cuda_fail(c, e, "tensor-core synaptic input");
     return SN_OK;
 }
@@ -295,6 +295,23 @@ sn_status sn_create_ff(const sn_config *cfg, int32_t layers, const int32_t *size
         (s = dalloc(c, &c->ctl, sizeof(Control))))
         return bail(s);
     if (cudaMemset(c->ctl, 0, sizeof(Control)) != cudaSuccess) return bail(SN_ECUDA);
+    // every layer's synaptic input kept for the backward, unless asked not to
+    // or the memory is not there (then the backward recomputes it)
+    if (!(cfg->flags & SN_FF_RECOMPUTE)) {
+        c->ff_Ik.assign(layers + 1, nullptr);
+        for (int l = 1; l <= layers; ++l) {
+            void *q = nullptr;
+            if (cudaMalloc(&q, (size_t)rows * sizes[l] * 4) != cudaSuccess) {
+                (void)cudaGetLastError();
+                for (int u = 1; u < l; ++u) cudaFree(c->ff_Ik[u]);
+                c->ff_Ik.clear();
+                break;
+            }
+            c->ff_Ik[l] = (float *)q;
+        }
+        for (float *q : c->ff_Ik)
+            if (q) c->allocs.push_back(q);
+    }
     c->ff_w.assign(layers, nullptr);
     tc_setup(c);
     c->err.clear();
@@ -316,6 +333,7 @@ sn_status sn_ff_forward(sn_ctx *c, const uint8_t *input, const float *const *w, 
     c->ff_fwd_tc = tc;
     for (int l = 1; l <= L; ++l) {
         const int nin = c->ff_sizes[l - 1], nout = c->ff_sizes[l];
+        float *I = c->ff_Ik.empty() ? c->ff_I : c->ff_Ik[l];
         c->ff_w[l - 1] = w[l - 1];
         if (tc) {
             // weight parts for this forward and the matching backward
@@ -323,13 +341,13 @@ sn_status sn_ff_forward(sn_ctx *c, const uint8_t *input, const float *const *w, 
                                    l > 1 ? c->ff_Wb[l - 1] : nullptr, (nin + 63) / 64 * 64, (nout + 127) / 128 * 128,
                                    c->ff_Wf[l - 1], c->stream)))
                 return cuda_fail(c, e, "weight parts");
-            sn_status st = tc_forward(c, l, false);
+            sn_status st = tc_forward(c, l, false, I);
             if (st) return st;
         } else if ((e = ff_delay_fwd(c->ff_S[l - 1], (nin + 31) / 32, w[l - 1], c->ff_DM[l - 1], nin, nout, B, 0,
-                                     rows, c->ff_I, c->stream))) {
+                                     rows, I, c->stream))) {
             return cuda_fail(c, e, "forward synaptic input");
         }
-        if ((e = ff_scan_fwd(c->ff_I, nout, B, T, c->ff_k, c->ff_theta, c->ff_leak, c->ff_reset, c->ff_refr,
+        if ((e = ff_scan_fwd(I, nout, B, T, c->ff_k, c->ff_theta, c->ff_leak, c->ff_reset, c->ff_refr,
                              c->ff_S[l], c->ff_vck[l], c->ff_rck[l], l == L ? counts : nullptr, c->stream)))
             return cuda_fail(c, e, "forward recurrence");
     }
@@ -352,16 +370,23 @@ sn_status sn_backward(sn_ctx *c, const float *grad_counts, float *const *grad_w,
     for (int l = L; l >= 1; --l) {
         const int nin = c->ff_sizes[l - 1], nout = c->ff_sizes[l];
         const int words_in = (nin + 31) / 32;
-        // recompute the synaptic input (the forward kept only spikes and
-        // checkpoints) with the forward's own kernel, so the states match
-        if (tc) {
-            sn_status st = tc_forward(c, l, true);
+        // the forward's synaptic input: kept, or recomputed with the
+        // forward's own kernel so that the states match; the tensor-core
+        // weight gradient also takes the transposed input spikes
+        float *I = c->ff_I;
+        if (!c->ff_Ik.empty()) {
+            I = c->ff_Ik[l];
+            if (tc && (e = ff_tc_spikes(c->ff_S[l - 1], rows, nin, words_in, up(nin, 64), up(rows, 64), nullptr,
+                                        c->ff_ST, c->stream)))
+                return cuda_fail(c, e, "spike operands");
+        } else if (tc) {
+            sn_status st = tc_forward(c, l, true, I);
             if (st) return st;
         } else if ((e = ff_delay_fwd(c->ff_S[l - 1], words_in, c->ff_w[l - 1], c->ff_DM[l - 1], nin, nout, B, 0,
-                                     rows, c->ff_I, c->stream))) {
+                                     rows, I, c->stream))) {
             return cuda_fail(c, e, "recompute synaptic input");
         }
-        if ((e = ff_scan_bwd(c->ff_I, nout, B, T, c->ff_k, c->ff_theta, c->ff_leak, c->ff_reset, c->ff_refr,
+        if ((e = ff_scan_bwd(I, nout, B, T, c->ff_k, c->ff_theta, c->ff_leak, c->ff_reset, c->ff_refr,
                              c->ff_slope, c->ff_vck[l], c->ff_rck[l], l == L ? nullptr : c->ff_gS,
                              l == L ? grad_counts : nullptr, c->ff_gI, c->stream)))
             return cuda_fail(c, e, "adjoint recurrence");

@@ -19,7 +19,7 @@ from . import build as _build
 
 SN_OK, SN_EINVAL, SN_ENOMEM, SN_ECUDA, SN_ESTATE, SN_ETIMEOUT, SN_EUNSUPPORTED, SN_EOVERFLOW = range(8)
 SN_F32, SN_I32 = 0, 1
-SN_AUTO, SN_EXEC_CTA, SN_EXEC_GRID, SN_PROP_PULL = 0, 1, 2, 4
+SN_AUTO, SN_EXEC_CTA, SN_EXEC_GRID, SN_PROP_PULL, SN_FF_RECOMPUTE = 0, 1, 2, 4, 8
 SN_PUSH, SN_PULL = 0, 1
 SN_FF_AUTO, SN_FF_SIMT, SN_FF_TENSOR = 0, 1, 2
 _NAMES = ["SN_OK", "SN_EINVAL", "SN_ENOMEM", "SN_ECUDA", "SN_ESTATE", "SN_ETIMEOUT",
@@ -435,14 +435,15 @@ def sn_run_dense_noalloc(n, delay, steps, w, threshold, leak, reset, refractory,
 
 
 def sn_create_ff(sizes, delays, *, threshold, leak, reset, refractory, slope, checkpoint_every,
-                 batch, steps, stream=None) -> Ctx:
-    """Feedforward context; delays: list of uint8 arrays [n_in, n_out] (host)."""
+                 batch, steps, stream=None, recompute=False) -> Ctx:
+    """Feedforward context; delays: list of uint8 arrays [n_in, n_out] (host).
+    recompute: SN_FF_RECOMPUTE (the backward recomputes the synaptic input)."""
     sz = np.ascontiguousarray(sizes, np.int32)
     ds = [np.ascontiguousarray(d, np.uint8) for d in delays]
     ptrs = (C.c_void_p * len(ds))(*[_ptr(d) for d in ds])
     p = sn_ff_params(float(threshold), float(leak), float(reset), int(refractory), float(slope),
                      int(checkpoint_every))
-    cfg = _config(SN_F32, 1, 0, 0, stream)
+    cfg = _config(SN_F32, 1, SN_FF_RECOMPUTE if recompute else 0, 0, stream)
     h = _P()
     _check(lib().sn_create_ff(C.byref(cfg), len(ds), _ptr(sz), ptrs, C.byref(p), int(batch), int(steps),
                               C.byref(h)))

@@ -32,9 +32,9 @@ def built():
     g.build()
 
 
-def run_gpu(task, engine=None):
+def run_gpu(task, engine=None, recompute=False):
     from paper_2305_02510_gb300 import bptt, sn as S
-    net = bptt.FFNet.from_task(task, engine=engine)
+    net = bptt.FFNet.from_task(task, engine=engine, recompute=recompute)
     dev = torch.device("cuda")
     x = torch.tensor(task["input"], device=dev)
     ws = [torch.tensor(w, device=dev, requires_grad=True) for w in task["w"]]
@@ -139,6 +139,26 @@ def check_small_free_running(seed, k, sizes, B, T, engine):
     assert np.array_equal(counts, ref_counts.numpy())
     assert abs(loss - float(ref_loss)) < 1e-5
     compare_grads(grads, ref_grads, fp32_level(task, None), near)
+
+
+@pytest.mark.parametrize("engine", ["simt", "tensor"])
+def test_bptt_kept_input_equals_recomputed(engine):
+    """The backward on the synaptic input kept from the forward and on the
+    input recomputed by the forward's own kernel: identical losses, counts,
+    spikes, checkpoints and gradients, bit for bit."""
+    task = W.bptt_task(batch=16, sizes=(130, 200, 20, 7), steps=25, seed=8)
+    task["w"] = [w * 1.5 for w in task["w"]]
+    task["checkpoint_every"] = 5
+    kept = run_gpu(task, engine)
+    again = run_gpu(task, engine, recompute=True)
+    assert kept[0] == again[0] and np.array_equal(kept[1], again[1])
+    for a, b in zip(kept[2], again[2]):
+        assert np.array_equal(a, b)
+    for a, b in zip(kept[3], again[3]):
+        assert np.array_equal(a, b)
+    for a, b in zip(kept[4][1:], again[4][1:]):
+        assert np.array_equal(a, b)
+    assert kept[3][-1].sum() > 0
 
 
 @pytest.mark.parametrize("engine", ["simt", "tensor"])
