@@ -36,15 +36,24 @@ constexpr int kFFDelays = 4;
 // input spikes (bytes) -> bit rows [T*B][words]
 __global__ void ff_pack_kernel(const uint8_t *in, int rows, int n, int words, unsigned *out) {
     const int lane = threadIdx.x & 31;
+    constexpr int kU = 4;                      // words per warp and iteration (loads in flight)
     const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     const long long total = (long long)rows * words;
-    for (long long w = gw; w < total; w += ((long long)gridDim.x * blockDim.x) >> 5) {
-        const long long r = w / words;
-        const int c = (int)(w - r * words);
-        const int i = c * 32 + lane;
-        const bool bit = i < n && in[r * n + i] != 0;
-        const unsigned word = __ballot_sync(0xffffffffu, bit);
-        if (lane == 0) out[w] = word;
+    for (long long w0 = gw * kU; w0 < total; w0 += nw * kU) {
+        bool bit[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const long long w = w0 + u;
+            const long long r = w / words;
+            const int i = (int)(w - r * words) * 32 + lane;
+            bit[u] = w < total && i < n && in[r * n + i] != 0;
+        }
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const unsigned word = __ballot_sync(0xffffffffu, bit[u]);
+            if (lane == 0 && w0 + u < total) out[w0 + u] = word;
+        }
     }
 }
 
@@ -144,8 +153,10 @@ __global__ void ff_scan_fwd_kernel(const float *__restrict__ I, int n, int words
     int r = 0;
     float cnt = 0.0f;
     // the inputs of the next kPre steps are loaded ahead (they do not depend
-    // on the recurrence)
-    constexpr int kPre = 4;
+    // on the recurrence): each thread is a chain of T dependent steps, so the
+    // depth of the prefetch sets how many round trips to memory the chain
+    // waits for (T / kPre)
+    constexpr int kPre = 16;
     const size_t stride = (size_t)B * n;
     const float *Ip = I + (size_t)b * n + j;
     float ahead[kPre];
@@ -181,9 +192,33 @@ __global__ void ff_scan_fwd_kernel(const float *__restrict__ I, int n, int words
 // to the first; each is recomputed from its checkpoint (u kept in registers),
 // then walked backwards.  gs = gradient w.r.t. the layer's spikes: per step
 // ([T][B][n]) or, for the output layer, the count gradient gc [B][n] that
-// every step shares.
+// every step shares.  A segment's loads (checkpoint, inputs, spike
+// gradients) do not depend on the adjoint, so those of segment sg - 1 are in
+// flight while segment sg is computed.
 template <int K>
-__global__ void ff_scan_bwd_kernel(const float *__restrict__ I, int n, int B, int T, FFNeuron p,
+__device__ __forceinline__ void ff_bwd_load(const float *__restrict__ I, const float *__restrict__ vck,
+                                            const int *__restrict__ rck, const float *__restrict__ gs,
+                                            float gcount, int n, int B, int T, int b, int j, int sg,
+                                            float reset, float (&Ix)[K], float (&Gx)[K], float &v0, int &r0) {
+    const int t0 = sg * K;
+    v0 = reset;
+    r0 = 0;
+    if (sg > 0) {
+        const size_t q = ((size_t)(sg - 1) * B + b) * n + j;
+        v0 = __ldg(vck + q);
+        r0 = __ldg(rck + q);
+    }
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+        const int t = t0 + q;
+        const size_t o = ((size_t)t * B + b) * n + j;
+        Ix[q] = t < T ? __ldg(I + o) : 0.0f;
+        Gx[q] = gs ? (t < T ? __ldg(gs + o) : 0.0f) : gcount;
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(128) ff_scan_bwd_kernel(const float *__restrict__ I, int n, int B, int T, FFNeuron p,
                                    const float *__restrict__ vck, const int *__restrict__ rck,
                                    const float *__restrict__ gs, const float *__restrict__ gc,
                                    float *__restrict__ gI) {
@@ -193,15 +228,16 @@ __global__ void ff_scan_bwd_kernel(const float *__restrict__ I, int n, int B, in
     const int segs = (T + K - 1) / K;
     const float gcount = gc ? gc[(size_t)b * n + j] : 0.0f;
     float gv = 0.0f;
+    float Ic[K], Gc[K], vc;
+    int rc;
+    ff_bwd_load<K>(I, vck, rck, gs, gcount, n, B, T, b, j, segs - 1, p.reset, Ic, Gc, vc, rc);
     for (int sg = segs - 1; sg >= 0; --sg) {
         const int t0 = sg * K;
-        float v = p.reset;
-        int r = 0;
-        if (sg > 0) {
-            const size_t q = ((size_t)(sg - 1) * B + b) * n + j;
-            v = vck[q];
-            r = rck[q];
-        }
+        float In[K], Gn[K], vn = p.reset;
+        int rn = 0;
+        if (sg > 0) ff_bwd_load<K>(I, vck, rck, gs, gcount, n, B, T, b, j, sg - 1, p.reset, In, Gn, vn, rn);
+        float v = vc;
+        int r = rc;
         float u[K], vprev[K];
         bool sp[K], mk[K];
 #pragma unroll
@@ -209,7 +245,7 @@ __global__ void ff_scan_bwd_kernel(const float *__restrict__ I, int n, int B, in
             const int t = t0 + q;
             vprev[q] = v;
             if (t < T) {
-                u[q] = __fadd_rn(ff_leak(v, p.leak, p.reset), I[((size_t)t * B + b) * n + j]);
+                u[q] = __fadd_rn(ff_leak(v, p.leak, p.reset), Ic[q]);
                 mk[q] = (r == 0);
                 sp[q] = (u[q] > p.theta) && mk[q];
                 if (sp[q]) { v = p.reset; r = p.refractory; }
@@ -222,15 +258,18 @@ __global__ void ff_scan_bwd_kernel(const float *__restrict__ I, int n, int B, in
         for (int q = K - 1; q >= 0; --q) {
             const int t = t0 + q;
             if (t >= T) continue;
-            const float g_s = gc ? gcount : gs[((size_t)t * B + b) * n + j];
             const float x = fabsf(u[q] - p.theta);
             const float den = 1.0f + p.slope * x;
             const float sur = mk[q] ? 1.0f / (den * den) : 0.0f;
-            const float gu = (sp[q] ? 0.0f : gv) + g_s * sur;
+            const float gu = (sp[q] ? 0.0f : gv) + Gc[q] * sur;
             gI[((size_t)t * B + b) * n + j] = gu;
             const float dv = vprev[q] - p.reset;
             gv = (fabsf(dv) > p.leak) ? gu : 0.0f;
         }
+#pragma unroll
+        for (int q = 0; q < K; ++q) { Ic[q] = In[q]; Gc[q] = Gn[q]; }
+        vc = vn;
+        rc = rn;
     }
 }
 
@@ -437,7 +476,11 @@ static int blocks_for(long long work, int per) {
 
 cudaError_t ff_pack(const uint8_t *in, int rows, int n, int words, unsigned *out, cudaStream_t s) {
     const long long warps = (long long)rows * words;
-    ff_pack_kernel<<<blocks_for(warps * 32, 256), 256, 0, s>>>(in, rows, n, words, out);
+    // a grid-stride loop over at most 2048 blocks (block launches, not
+    // bandwidth, bound one word per warp)
+    int nb = blocks_for(warps * 32 / 4, 256);
+    nb = nb < 2048 ? nb : 2048;
+    ff_pack_kernel<<<nb, 256, 0, s>>>(in, rows, n, words, out);
     return cudaGetLastError();
 }
 
