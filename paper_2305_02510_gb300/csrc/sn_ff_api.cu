@@ -175,9 +175,13 @@ void tc_setup(sn_ctx *c) {
         st_elems = std::max(st_elems, (size_t)nin * rows_p);
         g_elems = std::max(g_elems, (size_t)2 * rows * up(nout, 64));
         gt_elems = std::max(gt_elems, (size_t)2 * nout * rows_p);
-        if (dalloc(c, &c->ff_Wf[l - 1], (size_t)12 * up(nout, 128) * up(nin, 64) * 2) ||
-            dalloc(c, &c->ff_Wb[l - 1], (size_t)8 * up(nin, 128) * up(nout, 64) * 2))
+        const size_t wf = (size_t)12 * up(nout, 128) * up(nin, 64) * 2, wb = (size_t)8 * up(nin, 128) * up(nout, 64) * 2;
+        if (dalloc(c, &c->ff_Wf[l - 1], wf) || dalloc(c, &c->ff_Wb[l - 1], wb))
             return;
+        // the weight parts of the other three delays and the padding stay
+        // zero for the context's lifetime (each forward rewrites only every
+        // weight's own delay slot)
+        if (cudaMemset(c->ff_Wf[l - 1], 0, wf) || cudaMemset(c->ff_Wb[l - 1], 0, wb)) return;
     }
     if (dalloc(c, &c->ff_Sbf, s_elems * 2) || dalloc(c, &c->ff_ST, st_elems * 2) || dalloc(c, &c->ff_G, g_elems * 2) ||
         dalloc(c, &c->ff_GT, gt_elems * 2))

@@ -379,32 +379,53 @@ __global__ void __launch_bounds__(kFwdTcThreads, 1) ff_tc_fwd_kernel(const __gri
 // Weight parts: Wb[(d-1)*2 + s] = part s (hi, mid) of W_d ([rows_in][nout_p],
 // rows_in = n_in rounded up to 128) for the backward; if Wf is given,
 // Wf[(d-1)*3 + s] = part s (hi, mid, lo: hi + mid + lo = w exactly) of W_d
-// transposed ([rows_out][nin_p]) for the forward.  The buffers start zeroed.
-__global__ void ff_tc_weights_kernel(const float *__restrict__ W, const uint8_t *__restrict__ D, int n_in,
-                                     int n_out, int nout_p, int rows_in, int nin_p, int rows_out,
-                                     __nv_bfloat16 *Wb, __nv_bfloat16 *Wf) {
-    const long long cnt = (long long)n_in * n_out;
+// transposed ([rows_out][nin_p]) for the forward.  Only each weight's own
+// delay slot is written: the buffers are zeroed once when the context is
+// set up and the delays never change, so every other slot stays zero.
+// 32 x 32 tiles through shared memory (a grid-stride loop over tiles), so
+// that both outputs leave as 64-byte row pieces.
+__global__ void __launch_bounds__(256) ff_tc_weights_kernel(const float *__restrict__ W,
+                                                            const uint8_t *__restrict__ D, int n_in, int n_out,
+                                                            int nout_p, int rows_in, int nin_p, int rows_out,
+                                                            __nv_bfloat16 *Wb, __nv_bfloat16 *Wf) {
+    __shared__ __nv_bfloat16 sp[3][32][34];
+    __shared__ uint8_t sd[32][33];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;      // 32 x 8
     const size_t bsz = (size_t)rows_in * nout_p, fsz = (size_t)rows_out * nin_p;
-    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < cnt;
-         q += (long long)gridDim.x * blockDim.x) {
-        const int i = (int)(q / n_out), j = (int)(q % n_out);
-        const int d = D[q];
-        const float w = W[q];
-        const __nv_bfloat16 hi = __float2bfloat16_rn(w);
-        const float r1 = __fsub_rn(w, __bfloat162float(hi));
-        const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
-        if (Wb) {
-            const size_t b = (size_t)i * nout_p + j;
-            Wb[(size_t)((d - 1) * 2 + 0) * bsz + b] = hi;
-            Wb[(size_t)((d - 1) * 2 + 1) * bsz + b] = mid;
+    const int ti = (n_in + 31) / 32, tj = (n_out + 31) / 32;
+    const long long ntiles = (long long)ti * tj;
+    for (long long tl = blockIdx.x; tl < ntiles; tl += gridDim.x) {
+        const int i0 = (int)(tl / tj) * 32, j0 = (int)(tl % tj) * 32;
+        for (int y = ty; y < 32; y += 8) {
+            const int i = i0 + y, j = j0 + tx;
+            if (i >= n_in || j >= n_out) continue;
+            const size_t q = (size_t)i * n_out + j;
+            const int d = D[q];
+            const float w = W[q];
+            const __nv_bfloat16 hi = __float2bfloat16_rn(w);
+            const float r1 = __fsub_rn(w, __bfloat162float(hi));
+            const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
+            if (Wb) {
+                const size_t b = (size_t)i * nout_p + j;
+                Wb[(size_t)((d - 1) * 2 + 0) * bsz + b] = hi;
+                Wb[(size_t)((d - 1) * 2 + 1) * bsz + b] = mid;
+            }
+            sp[0][y][tx] = hi;
+            sp[1][y][tx] = mid;
+            sp[2][y][tx] = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(mid)));
+            sd[y][tx] = (uint8_t)d;
         }
-        if (Wf) {
-            const __nv_bfloat16 lo = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(mid)));
+        if (!Wf) continue;
+        __syncthreads();
+        for (int y = ty; y < 32; y += 8) {
+            const int j = j0 + y, i = i0 + tx;
+            if (i >= n_in || j >= n_out) continue;
+            const int d = sd[tx][y];
             const size_t f = (size_t)j * nin_p + i;
-            Wf[(size_t)((d - 1) * 3 + 0) * fsz + f] = hi;
-            Wf[(size_t)((d - 1) * 3 + 1) * fsz + f] = mid;
-            Wf[(size_t)((d - 1) * 3 + 2) * fsz + f] = lo;
+#pragma unroll
+            for (int part = 0; part < 3; ++part) Wf[(size_t)((d - 1) * 3 + part) * fsz + f] = sp[part][tx][y];
         }
+        __syncthreads();
     }
 }
 
@@ -468,9 +489,10 @@ __global__ void __launch_bounds__(256) ff_tc_gsplit_kernel(const float *__restri
     }
 }
 
-int grid_for(long long work) {
-    long long b = (work + 255) / 256;
-    if (b > 8192) b = 8192;
+// Blocks for a grid-stride loop over 32 x 32 tiles: at most 1216 (eight per
+// SM of a 152-SM part).
+static int tile_grid(long long tiles) {
+    const long long b = tiles < 1216 ? tiles : 1216;
     return (int)(b < 1 ? 1 : b);
 }
 
@@ -515,16 +537,14 @@ cudaError_t ff_tc_forward(const FfTcMaps &maps, const FfTcArgs &args, cudaStream
 
 cudaError_t ff_tc_weights(const float *W, const uint8_t *D, int n_in, int n_out, int nout_p, int rows_in,
                           void *Wb, int nin_p, int rows_out, void *Wf, cudaStream_t s) {
-    cudaError_t e;
-    if (Wb && (e = cudaMemsetAsync(Wb, 0, (size_t)8 * rows_in * nout_p * 2, s)) != cudaSuccess) return e;
-    if (Wf && (e = cudaMemsetAsync(Wf, 0, (size_t)12 * rows_out * nin_p * 2, s)) != cudaSuccess) return e;
-    ff_tc_weights_kernel<<<grid_for((long long)n_in * n_out), 256, 0, s>>>(
+    ff_tc_weights_kernel<<<tile_grid((long long)((n_in + 31) / 32) * ((n_out + 31) / 32)), 256, 0, s>>>(
         W, D, n_in, n_out, nout_p, rows_in, nin_p, rows_out, (__nv_bfloat16 *)Wb, (__nv_bfloat16 *)Wf);
     return cudaGetLastError();
 }
 
 cudaError_t ff_tc_spikes(const unsigned *bits, int rows, int n_in, int words, int nin_p, int rows_p, void *S,
                          void *ST, cudaStream_t s) {
+    // one block per tile: a grid-stride loop over tiles measured slower
     const dim3 grid((rows + 31) / 32, (n_in + 31) / 32);
     ff_tc_spikes_kernel<<<grid, 256, 0, s>>>(bits, rows, n_in, words, nin_p, rows_p, (__nv_bfloat16 *)S,
                                             (__nv_bfloat16 *)ST);
