@@ -162,8 +162,9 @@ sn_status sn_create_dense(const sn_config *cfg, const sn_neurons *neurons,
  * sn_get_state concatenates the states, and every raster row holds each
  * network's ceil(n_b/32) words in network order.  sn_run advances all
  * networks by the same number of steps in one persistent kernel launch,
- * replayed from a CUDA graph.  STDP, weights and checkpoints are not
- * available for batched contexts (SN_EUNSUPPORTED / SN_ESTATE). */
+ * replayed from a CUDA graph.  STDP and weight access are not available
+ * for batched contexts (SN_EUNSUPPORTED / SN_ESTATE); sn_save / sn_load
+ * are. */
 sn_status sn_create_batch(const sn_config *cfg, int32_t nets, const sn_neurons *neurons,
                           const sn_synapses *synapses, sn_ctx **out);
 
@@ -177,8 +178,8 @@ sn_status sn_create_batch(const sn_config *cfg, int32_t nets, const sn_neurons *
  * (Section 2.1: previous spike vector times the weight matrix), exact in
  * integers.  State (sn_get_state) is [trains][n]; every raster row holds
  * each train's n/32 words in train order; sn_set_poisson takes neuron
- * indices 0..n-1 and drives that neuron in every train.  Explicit events,
- * STDP and checkpoints are not available. */
+ * indices 0..n-1 and drives that neuron in every train.  Explicit events
+ * and STDP are not available; sn_save / sn_load are. */
 sn_status sn_create_shared_dense_i8(const sn_config *cfg, const sn_neurons *neurons, const int8_t *w,
                                     int32_t trains, sn_ctx **out);
 
