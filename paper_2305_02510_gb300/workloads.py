@@ -302,10 +302,11 @@ def batched_nets(count: int = 4096, seed: int = SEED_BASE + 4, steps: int = 500,
     [nmin, nmax], connection probability U(0.01, 0.2), thresholds U(0.5, 1.5),
     leaks U(0, 0.2), reset 0, refractory U{0..3}, delays U{1..8}, weights
     N(0, 1)/sqrt(p N); Poisson 0.05/step into 10% of each net's neurons with
-    amplitude 2 * max threshold.  Network b is drawn from its own seed
-    sequence, so any subset [first, first + count) is the same networks as in
-    the full batch.  Weights are float32, indices int32.  Returns a list of
-    workload dicts."""
+    amplitude 2 * max threshold.  The sizes and probabilities of networks
+    0 .. first + count - 1 come from one stream (so they depend on
+    first + count); network b then draws its synapses and parameters from its
+    own seed sequence (seed, b).  Weights are float32, indices int32.
+    Returns a list of workload dicts for networks first .. first + count - 1."""
     top = np.random.default_rng(np.random.SeedSequence(int(seed)))
     sizes = np.floor(np.exp(top.uniform(math.log(nmin), math.log(nmax), size=first + count)))
     probs = top.uniform(0.01, 0.2, size=first + count)
