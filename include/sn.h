@@ -453,6 +453,15 @@ typedef struct {
 
 sn_status sn_run_dense_noalloc(const sn_dense_noalloc_args *args);
 
+/* Failure-detection self-test.  Launches on cuda_stream (NULL = default
+ * stream) a kernel of four blocks whose grid barrier one block never
+ * reaches, so that the other blocks' bounded wait runs out (after about 2 s
+ * of wall-clock time); *status receives the status the kernel latched:
+ * SN_ETIMEOUT when the bound works.  Nothing faults or traps, and the CUDA
+ * context stays usable.  Returns SN_OK when the self-test ran, SN_EINVAL for
+ * a NULL status, SN_ENOMEM or SN_ECUDA when it could not run. */
+sn_status sn_selftest_barrier_timeout(void *cuda_stream, int32_t *status);
+
 /* Library version string. */
 const char *sn_version(void);
 

@@ -220,6 +220,26 @@ extern "C" {
 
 const char *sn_version(void) { return "sn-gb300 0.1 (sm_103a)"; }
 
+sn_status sn_selftest_barrier_timeout(void *cuda_stream, int32_t *status) {
+    if (!status) return fail(nullptr, SN_EINVAL, "status is NULL");
+    const cudaStream_t s = (cudaStream_t)cuda_stream;
+    Control *ctl = nullptr;
+    if (cudaMalloc(&ctl, sizeof(Control)) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(nullptr, SN_ENOMEM, "device allocation of the control block failed");
+    }
+    Control h;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(ctl, 0, sizeof(Control), s)) || (e = launch_barrier_selftest(ctl, 4, s)) ||
+        (e = cudaStreamSynchronize(s)) || (e = cudaMemcpy(&h, ctl, sizeof(Control), cudaMemcpyDeviceToHost))) {
+        cudaFree(ctl);
+        return fail(nullptr, SN_ECUDA, std::string("self-test: ") + cudaGetErrorString(e));
+    }
+    cudaFree(ctl);
+    *status = h.status;
+    return SN_OK;
+}
+
 const char *sn_last_error(const sn_ctx *ctx) {
     return ctx ? ctx->err.c_str() : g_create_err.c_str();
 }

@@ -215,5 +215,6 @@ cudaError_t launch_gather_weights(const uint2 *syn, const long long *perm_inv, l
                                   float *out, cudaStream_t s);
 cudaError_t launch_scatter_weights(uint2 *syn, const long long *perm_inv, long long m, const float *w,
                                    cudaStream_t s);
+cudaError_t launch_barrier_selftest(Control *ctl, int blocks, cudaStream_t s);
 
 }  // namespace sn

@@ -751,6 +751,19 @@ __global__ void __launch_bounds__(kBlock, CPL <= 2 ? 4 : 3) dense_kernel(NetArgs
     }
 }
 
+// Failure-detection self-test: block 0 never arrives at the barrier, so the
+// count stays one short of its target and every other block's wait runs out
+// after kBarrierTimeoutNs, latching SN_ETIMEOUT (no fault, no trap).
+__global__ void barrier_selftest_kernel(Control *ctl) {
+    if (blockIdx.x == 0) return;
+    grid_barrier(ctl);
+}
+
+cudaError_t launch_barrier_selftest(Control *ctl, int blocks, cudaStream_t s) {
+    barrier_selftest_kernel<<<blocks, 32, 0, s>>>(ctl);
+    return cudaGetLastError();
+}
+
 // Shared memory of a dense block: spike-count prefix, list chunk, warp
 // partials (the vector path keeps RPI partials per warp: at most 4 * 32 * 4 B
 // per warp for any CPL, as much as CPL = 4's scalar partials).

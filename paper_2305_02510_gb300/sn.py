@@ -113,6 +113,7 @@ def lib():
                 "sn_get_propagation": [_P, C.POINTER(C.c_int32)],
                 "sn_save": [_P, _P, C.POINTER(C.c_size_t)],
                 "sn_load": [_P, _P, C.c_size_t],
+                "sn_selftest_barrier_timeout": [_P, C.POINTER(C.c_int32)],
             }
             for name, args in sig.items():
                 f = getattr(L, name)
@@ -481,6 +482,15 @@ def sn_ff_get_checkpoints(ctx: Ctx, layer: int):
     out = np.zeros((ctx.steps // ctx.k, ctx.batch, n), np.float32)
     _check(lib().sn_ff_get_checkpoints(ctx.handle, int(layer), _ptr(out), 0), ctx)
     return out
+
+
+def sn_selftest_barrier_timeout(stream=None) -> int:
+    """Run the failure-detection self-test (a grid barrier that one block
+    never reaches); returns the status the kernel latched (SN_ETIMEOUT when
+    the wait's bound works)."""
+    st = C.c_int32(-1)
+    _check(lib().sn_selftest_barrier_timeout(stream, C.byref(st)))
+    return st.value
 
 
 def sn_version() -> str:

@@ -93,6 +93,7 @@ def test_version_and_null_handles(S):
     assert L.sn_sync(None) == S.SN_EINVAL
     assert L.sn_set_propagation(None, S.SN_PULL) == S.SN_EINVAL
     assert L.sn_get_propagation(None, None) == S.SN_EINVAL
+    assert L.sn_selftest_barrier_timeout(None, None) == S.SN_EINVAL
     L.sn_destroy(None)
 
 
