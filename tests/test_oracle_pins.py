@@ -11,6 +11,8 @@ mathematics, independent of the oracle's own code.
   * exhaustive brute force on 2-neuron networks
   * hand-computed pair-based STDP updates and clipping
   * the published SplitMix64 test vector and the Poisson source rate
+  * the all-to-all matrix form equals the per-synapse form of the same
+    network (integer and float, with and without STDP)
 """
 
 import math
@@ -381,3 +383,65 @@ def test_fp32_mirror_tracks_fp64():
         t = diff[0]
         j = np.nonzero(r64[t] != r32[t])[0]
         assert np.all(np.abs(s64.ctrace[t, j] - th[j]) < 1e-4 * th[j])
+
+
+def dense_as_synapses(wl, diagonal=True):
+    """The same network in the per-synapse form: one synapse i -> j of the
+    matrix's delay for every entry W[i][j] (row = pre, Section 2.1), listed in
+    row-major order; without the diagonal when it is left out."""
+    n = wl["n"]
+    w = np.asarray(wl["dense_w"] if "dense_w" in wl else wl["dense_w_i8"], np.float64)
+    mask = np.ones((n, n), bool) if diagonal else ~np.eye(n, dtype=bool)
+    i, j = np.nonzero(mask)
+    d = int(wl["dense_delay"])
+    out = {k: v for k, v in wl.items() if k not in ("dense_w", "dense_w_i8", "dense_delay")}
+    out.update(pre=i.astype(np.int32), post=j.astype(np.int32), weight=w[i, j],
+               delay=np.full(i.size, d, np.int32), max_delay=max(int(wl["max_delay"]), d))
+    return out, mask
+
+
+@pytest.mark.parametrize("delay", [1, 3])
+def test_dense_form_equals_synapse_form_int(delay):
+    """The oracle's matrix form (the previous spike vector times W, row =
+    pre, diagonal included) gives the same integer run as the per-synapse
+    form of the same network: a transposed matrix, a dropped diagonal or a
+    wrong delay in the matrix form fails this."""
+    n, T = 48, 80
+    wl = W.shared_dense_i8(n=n, batch=1, steps=T)       # theta 40, Poisson amplitude 41
+    rng = np.random.default_rng(11 + delay)
+    w = rng.integers(-8, 9, size=(n, n)).astype(np.int8)
+    w[np.triu_indices(n, 1)] = np.abs(w[np.triu_indices(n, 1)])   # asymmetric
+    wl.update(dense_w_i8=w, dense_delay=delay, max_delay=delay)
+    a, ra, _ = O.run(wl, O.INT, T)
+    syn, _ = dense_as_synapses(wl)
+    b, rb, _ = O.run(syn, O.INT, T)
+    assert ra.sum() > 0
+    assert np.array_equal(ra, rb)
+    assert np.array_equal(a.v, b.v) and np.array_equal(a.r, b.r)
+    # the transposed matrix is a different network
+    wt = dict(wl, dense_w_i8=np.ascontiguousarray(w.T))
+    _, rt, _ = O.run(wt, O.INT, T)
+    assert not np.array_equal(rt, ra)
+
+
+@pytest.mark.parametrize("mode", [O.F32, O.F64])
+@pytest.mark.parametrize("stdp", [False, True])
+def test_dense_form_equals_synapse_form_float(mode, stdp):
+    """Float runs of the matrix form and the per-synapse form are identical
+    bit for bit (both add a post-neuron's inputs in ascending pre order), and
+    with STDP so are the weights after the run (the matrix form's rule skips
+    the diagonal, which is not a synapse)."""
+    n, T = 64, 60
+    wl = W.large_dense(n=n, stdp=stdp, steps=T)
+    wl["dense_w"] = (wl["dense_w"] * np.float32(10.0)).astype(np.float32)   # N(0, 0.2), W_ii = 0
+    a, ra, _ = O.run(wl, mode, T)
+    syn, mask = dense_as_synapses(wl, diagonal=False)
+    b, rb, _ = O.run(syn, mode, T)
+    assert ra.sum() > 0
+    assert np.array_equal(ra, rb)
+    assert np.array_equal(a.v, b.v) and np.array_equal(a.r, b.r)
+    if stdp:
+        wa = a.w.reshape(n, n)
+        assert np.array_equal(wa[mask], b.w)
+        assert np.all(np.diag(wa) == 0)
+        assert not np.array_equal(wa, np.asarray(wl["dense_w"], np.float64))   # plasticity acted
