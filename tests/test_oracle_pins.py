@@ -13,6 +13,7 @@ mathematics, independent of the oracle's own code.
   * the published SplitMix64 test vector and the Poisson source rate
   * the all-to-all matrix form equals the per-synapse form of the same
     network (integer and float, with and without STDP)
+  * a state rebuilt from outside values continues like the uninterrupted run
 """
 
 import math
@@ -445,3 +446,29 @@ def test_dense_form_equals_synapse_form_float(mode, stdp):
         assert np.array_equal(wa[mask], b.w)
         assert np.all(np.diag(wa) == 0)
         assert not np.array_equal(wa, np.asarray(wl["dense_w"], np.float64))   # plasticity acted
+
+
+@pytest.mark.parametrize("kind", ["sparse", "dense-stdp"])
+def test_state_from_rebuilds_the_run(kind):
+    """A state rebuilt from V, the refractory countdowns, the last D spike
+    rows (oldest first), the traces and the weights continues exactly like
+    the uninterrupted run: the teacher-forced comparisons rest on this."""
+    if kind == "sparse":
+        wl = W.tiny(integer=False, steps=200)          # delays 1..4
+    else:
+        wl = W.large_dense(n=64, stdp=True, steps=200)
+        wl["dense_w"] = (wl["dense_w"] * np.float32(10.0)).astype(np.float32)
+    D, t, k = wl["max_delay"], 120, 60
+    full, raster, _ = O.run(wl, O.F32, t + k)
+    part, r1, _ = O.run(wl, O.F32, t)
+    st = O.state_from(wl, t, part.v, part.r, raster[t - D:t], trace=part.trace, w=part.w)
+    st2, r2, _ = O.run(wl, O.F32, k, state=st)
+    assert raster[t:].sum() > 0
+    assert np.array_equal(r2, raster[t:])
+    assert np.array_equal(st2.v, full.v) and np.array_equal(st2.r, full.r)
+    assert np.array_equal(st2.w, full.w)
+    # the rows in the other order do not give the same continuation
+    if raster[t - D:t].any() and not np.array_equal(raster[t - D:t], raster[t - D:t][::-1]):
+        bad = O.state_from(wl, t, part.v, part.r, raster[t - D:t][::-1], trace=part.trace, w=part.w)
+        _, rb, _ = O.run(wl, O.F32, k, state=bad)
+        assert not np.array_equal(rb, raster[t:])
