@@ -472,3 +472,19 @@ def test_state_from_rebuilds_the_run(kind):
         bad = O.state_from(wl, t, part.v, part.r, raster[t - D:t][::-1], trace=part.trace, w=part.w)
         _, rb, _ = O.run(wl, O.F32, k, state=bad)
         assert not np.array_equal(rb, raster[t:])
+
+
+def test_integer_overflow_is_detected():
+    """Integer mode: a state that leaves the int32 range is an error.  One
+    neuron gets 2^23 - 1 every step with no leak: 256 steps reach
+    2^31 - 256 (fine), the 257th passes 2^31."""
+    n, T = 4, 300
+    wl = W._base(n, "i32", 2.0 ** 31, 0, 0, 0, 1, T)
+    wl.update(pre=np.zeros(0, np.int32), post=np.zeros(0, np.int32), weight=np.zeros(0),
+              delay=np.zeros(0, np.int32))
+    wl["events"] = dict(step=np.arange(T, dtype=np.int32), neuron=np.zeros(T, np.int32),
+                        value=np.full(T, 2.0 ** 23 - 1))
+    st, raster, _ = O.run(wl, O.INT, 256)
+    assert st.v[0] == 256 * (2 ** 23 - 1) and raster.sum() == 0
+    with pytest.raises(RuntimeError):
+        O.run(wl, O.INT, 257)
