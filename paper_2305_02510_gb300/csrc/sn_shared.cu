@@ -48,6 +48,7 @@ constexpr int kStageBytes = (kTM + kTN) * kTK; // 32 KiB
 constexpr int kShThreads = 512;
 constexpr int kEpiParts = kShThreads / 128;        // warps per TMEM lane quarter
 constexpr int kEpiCols = kTN / kEpiParts;          // accumulator columns per epilogue warp
+static_assert(kEpiCols % 32 == 0, "an epilogue warp takes whole 32-column TMEM loads");
 constexpr int kSub = 4;                      // state columns loaded together
 // epilogue staging after the pipeline stages: spike bytes [128][kSaPitch],
 // raster words and Poisson bits [128][4], parameters [5][128]
