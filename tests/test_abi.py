@@ -119,3 +119,88 @@ def test_new_entry_points_reject_bad_arguments(S):
         st = L.sn_create_axonal(C.byref(cfg), C.byref(nr), C.byref(sy), a.ctypes.data, C.byref(h))
         assert st == S.SN_EINVAL, ax
         assert frag in L.sn_last_error(None).decode()
+
+
+def _shared(S, n=128, trains=128, dtype=1, D=1, wval=0):
+    keep = []
+    nr, _ = _neurons(S, n, keep)
+    w = np.full((n, n), wval, np.int8)
+    cfg = S.sn_config()
+    cfg.dtype, cfg.max_delay, cfg.flags, cfg.record_steps = dtype, D, 0, 0
+    h = C.c_void_p()
+    st = S.lib().sn_create_shared_dense_i8(C.byref(cfg), C.byref(nr), w.ctypes.data, trains, C.byref(h))
+    return st, S.lib().sn_last_error(None).decode()
+
+
+@pytest.mark.parametrize("kw,frag", [
+    (dict(n=100), "multiple of 128"),
+    (dict(trains=100), "trains"),
+    (dict(dtype=0), "SN_I32"),
+    (dict(D=2), "delay 1"),
+    (dict(wval=9), "-8 .. 8"),
+    (dict(wval=-9), "-8 .. 8"),
+])
+def test_shared_dense_rejects_bad_arguments(S, kw, frag):
+    st, msg = _shared(S, **kw)
+    assert st == S.SN_EINVAL and frag in msg, msg
+
+
+def _batch(S, sizes=(4, 5), D=2, delay=1, dtype=0):
+    keep = []
+    nrs = (S.sn_neurons * max(1, len(sizes)))()
+    sys_ = (S.sn_synapses * max(1, len(sizes)))()
+    for b, n in enumerate(sizes):
+        nr, _ = _neurons(S, n, keep)
+        nrs[b] = nr
+        pre, post = np.array([0], np.int32), np.array([min(1, n - 1)], np.int32)
+        w, d = np.array([1.0], np.float32), np.array([delay], np.int32)
+        keep += [pre, post, w, d]
+        sy = S.sn_synapses()
+        sy.m = 1
+        sy.pre, sy.post, sy.weight, sy.delay = pre.ctypes.data, post.ctypes.data, w.ctypes.data, d.ctypes.data
+        sys_[b] = sy
+    cfg = S.sn_config()
+    cfg.dtype, cfg.max_delay, cfg.flags, cfg.record_steps = dtype, D, 0, 0
+    h = C.c_void_p()
+    st = S.lib().sn_create_batch(C.byref(cfg), len(sizes), nrs, sys_, C.byref(h))
+    return st, S.lib().sn_last_error(None).decode()
+
+
+@pytest.mark.parametrize("kw,frag", [
+    (dict(sizes=()), "nets"),
+    (dict(sizes=(4, 5000)), "1..4096"),
+    (dict(D=17), "max_delay"),
+    (dict(delay=3), "delay"),
+    (dict(dtype=5), "dtype"),
+])
+def test_batch_rejects_bad_arguments(S, kw, frag):
+    st, msg = _batch(S, **kw)
+    assert st == S.SN_EINVAL and frag in msg, msg
+
+
+def _ff(S, sizes=(3, 4, 2), k=10, batch=2, steps=10, delay=1, layers=None):
+    sz = np.array(sizes, np.int32)
+    L = len(sizes) - 1 if layers is None else layers
+    ds = [np.full((max(1, sizes[l]), max(1, sizes[l + 1])), delay, np.uint8) for l in range(len(sizes) - 1)]
+    ptrs = (C.c_void_p * max(1, len(ds)))(*[d.ctypes.data for d in ds])
+    p = S.sn_ff_params(1.0, 0.05, 0.0, 0, 10.0, k)
+    cfg = S.sn_config()
+    cfg.dtype, cfg.max_delay, cfg.flags, cfg.record_steps = 0, 1, 0, 0
+    h = C.c_void_p()
+    st = S.lib().sn_create_ff(C.byref(cfg), L, sz.ctypes.data, ptrs, C.byref(p), batch, steps, C.byref(h))
+    return st, S.lib().sn_last_error(None).decode()
+
+
+@pytest.mark.parametrize("kw,frag", [
+    (dict(layers=0), "layers"),
+    (dict(layers=17), "layers"),
+    (dict(k=3), "checkpoint_every"),
+    (dict(delay=5), "delays"),
+    (dict(delay=0), "delays"),
+    (dict(batch=0), "batch"),
+    (dict(steps=0), "steps"),
+    (dict(sizes=(3, 0, 2)), "sizes"),
+])
+def test_ff_rejects_bad_arguments(S, kw, frag):
+    st, msg = _ff(S, **kw)
+    assert st == S.SN_EINVAL and frag in msg, msg
