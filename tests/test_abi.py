@@ -204,3 +204,50 @@ def _ff(S, sizes=(3, 4, 2), k=10, batch=2, steps=10, delay=1, layers=None):
 def test_ff_rejects_bad_arguments(S, kw, frag):
     st, msg = _ff(S, **kw)
     assert st == S.SN_EINVAL and frag in msg, msg
+
+
+def _noalloc(S, **kw):
+    a = S.sn_dense_noalloc_args()
+    a.n, a.delay, a.steps = 8, 1, 4
+    for name in ("w", "threshold", "leak", "reset", "refractory", "v", "r", "raster"):
+        setattr(a, name, 256)               # never dereferenced by the checks
+    for k, v in kw.items():
+        setattr(a, k, v)
+    return S.lib().sn_run_dense_noalloc(C.byref(a))
+
+
+@pytest.mark.parametrize("kw", [dict(n=0), dict(n=200001), dict(delay=0), dict(delay=65), dict(steps=-1),
+                                dict(w=None), dict(v=None), dict(raster=None),
+                                dict(poisson_threshold=256), dict(poisson_amplitude=256)])
+def test_noalloc_rejects_bad_arguments(S, kw):
+    assert _noalloc(S, **kw) == S.SN_EINVAL
+
+
+def test_noalloc_zero_steps_is_a_no_op(S):
+    """Zero steps return SN_OK before any CUDA call (and need no raster)."""
+    assert _noalloc(S, steps=0, raster=None) == S.SN_OK
+    assert S.lib().sn_run_dense_noalloc(None) == S.SN_EINVAL
+
+
+def _dense(S, n=4, delay=1, D=2, dtype=0, wval=0.5, flags=0):
+    keep = []
+    nr, _ = _neurons(S, n, keep)
+    w = np.full((max(n, 1), max(n, 1)), wval, np.float32)
+    cfg = S.sn_config()
+    cfg.dtype, cfg.max_delay, cfg.flags, cfg.record_steps = dtype, D, flags, 0
+    h = C.c_void_p()
+    st = S.lib().sn_create_dense(C.byref(cfg), C.byref(nr), w.ctypes.data, delay, C.byref(h))
+    return st, S.lib().sn_last_error(None).decode()
+
+
+@pytest.mark.parametrize("kw,status,frag", [
+    (dict(dtype=1), "SN_EUNSUPPORTED", "SN_F32"),
+    (dict(flags=4), "SN_EUNSUPPORTED", "SN_PROP_PULL"),
+    (dict(n=0), "SN_EINVAL", "dense n"),
+    (dict(delay=0), "SN_EINVAL", "delay"),
+    (dict(delay=3), "SN_EINVAL", "delay"),
+    (dict(wval=float("inf")), "SN_EINVAL", "weight"),
+])
+def test_dense_rejects_bad_arguments(S, kw, status, frag):
+    st, msg = _dense(S, **kw)
+    assert st == getattr(S, status) and frag in msg, (st, msg)
