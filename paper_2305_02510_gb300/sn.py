@@ -178,8 +178,18 @@ def _config(dtype, max_delay, flags, record_steps, stream):
 
 
 def _neurons(threshold, leak, reset, refractory, keep):
+    """Neuron parameter arrays of one size n; a single value is repeated n
+    times (the C side always reads n values of each)."""
     th, lk, rs = _arr(threshold, np.float32), _arr(leak, np.float32), _arr(reset, np.float32)
     rf = _arr(refractory, np.int32)
+    arrs = [th.reshape(-1), lk.reshape(-1), rs.reshape(-1), rf.reshape(-1)]
+    n = max(a.size for a in arrs)
+    for k, a in enumerate(arrs):
+        if a.size == 1 and n > 1:
+            arrs[k] = np.full(n, a[0], a.dtype)
+        elif a.size != n:
+            raise ValueError(f"neuron parameter arrays differ in length ({[x.size for x in arrs]})")
+    th, lk, rs, rf = arrs
     keep += [th, lk, rs, rf]
     nr = sn_neurons()
     nr.n = th.size

@@ -251,3 +251,15 @@ def _dense(S, n=4, delay=1, D=2, dtype=0, wval=0.5, flags=0):
 def test_dense_rejects_bad_arguments(S, kw, status, frag):
     st, msg = _dense(S, **kw)
     assert st == getattr(S, status) and frag in msg, (st, msg)
+
+
+def test_binding_neuron_arrays(S):
+    """The binding repeats a single parameter value n times and refuses
+    arrays of different lengths before any C call."""
+    keep = []
+    nr = S._neurons(np.ones(5), 0.1, [0.0], 2, keep)
+    assert nr.n == 5
+    lk = keep[1]
+    assert lk.size == 5 and np.all(lk == np.float32(0.1)) and np.all(keep[3] == 2)
+    with pytest.raises(ValueError):
+        S._neurons(np.ones(5), np.zeros(4), 0.0, 0, [])
