@@ -177,19 +177,36 @@ def _config(dtype, max_delay, flags, record_steps, stream):
     return cfg
 
 
+def _match(what, n, *arrs):
+    """Arrays of n values each (the C side reads n of each); a single value
+    is repeated n times, any other length raises ValueError."""
+    out = []
+    for a in arrs:
+        a = a.reshape(-1)
+        if a.size == n:
+            out.append(a)
+        elif a.size == 1 and n != 1:
+            out.append(np.full(n, a[0], a.dtype))
+        else:
+            raise ValueError(f"{what}: expected {n} values, got {a.size}")
+    return out
+
+
+def _synapses(pre, post, weight, delay, keep):
+    pre, post = _arr(pre, np.int32).reshape(-1), _arr(post, np.int32).reshape(-1)
+    if pre.size != post.size:
+        raise ValueError(f"synapses: {pre.size} pre and {post.size} post indices")
+    w, d = _match("synapse weights and delays", pre.size, _arr(weight, np.float32), _arr(delay, np.int32))
+    keep += [pre, post, w, d]
+    return pre, post, w, d
+
+
 def _neurons(threshold, leak, reset, refractory, keep):
     """Neuron parameter arrays of one size n; a single value is repeated n
     times (the C side always reads n values of each)."""
-    th, lk, rs = _arr(threshold, np.float32), _arr(leak, np.float32), _arr(reset, np.float32)
-    rf = _arr(refractory, np.int32)
-    arrs = [th.reshape(-1), lk.reshape(-1), rs.reshape(-1), rf.reshape(-1)]
-    n = max(a.size for a in arrs)
-    for k, a in enumerate(arrs):
-        if a.size == 1 and n > 1:
-            arrs[k] = np.full(n, a[0], a.dtype)
-        elif a.size != n:
-            raise ValueError(f"neuron parameter arrays differ in length ({[x.size for x in arrs]})")
-    th, lk, rs, rf = arrs
+    arrs = [_arr(threshold, np.float32), _arr(leak, np.float32), _arr(reset, np.float32),
+            _arr(refractory, np.int32)]
+    th, lk, rs, rf = _match("neuron parameters", max(a.size for a in arrs), *arrs)
     keep += [th, lk, rs, rf]
     nr = sn_neurons()
     nr.n = th.size
@@ -202,9 +219,7 @@ def sn_create(threshold, leak, reset, refractory, pre, post, weight, delay, *, d
     """sn_create, or sn_create_axonal when axonal_delay (n values) is given."""
     keep = []
     nr = _neurons(threshold, leak, reset, refractory, keep)
-    pre, post = _arr(pre, np.int32), _arr(post, np.int32)
-    w, d = _arr(weight, np.float32), _arr(delay, np.int32)
-    keep += [pre, post, w, d]
+    pre, post, w, d = _synapses(pre, post, weight, delay, keep)
     sy = sn_synapses()
     sy.m = pre.size
     sy.pre, sy.post, sy.weight, sy.delay = _ptr(pre), _ptr(post), _ptr(w), _ptr(d)
@@ -228,6 +243,8 @@ def sn_create_dense(threshold, leak, reset, refractory, w, delay=1, *, max_delay
     nr = _neurons(threshold, leak, reset, refractory, keep)
     if w is not None:                  # None: zero weights, set later with sn_set_weights
         w = _arr(w, np.float32)
+        if w.size != nr.n * nr.n:
+            raise ValueError(f"dense weights: expected {nr.n} x {nr.n} values, got {w.size}")
         keep.append(w)
     cfg = _config(SN_F32, max_delay if max_delay is not None else delay, flags, record_steps, stream)
     h = _P()
@@ -247,9 +264,7 @@ def sn_create_batch(nets, *, dtype=SN_F32, max_delay, record_steps=0, stream=Non
     for b, d in enumerate(nets):
         nr = _neurons(d["threshold"], d["leak"], d["reset"], d["refractory"], keep)
         NR[b] = nr
-        pre, post = _arr(d["pre"], np.int32), _arr(d["post"], np.int32)
-        w, dl = _arr(d["weight"], np.float32), _arr(d["delay"], np.int32)
-        keep += [pre, post, w, dl]
+        pre, post, w, dl = _synapses(d["pre"], d["post"], d["weight"], d["delay"], keep)
         SY[b].m = pre.size
         SY[b].pre, SY[b].post = _ptr(pre) if pre.size else None, _ptr(post) if post.size else None
         SY[b].weight, SY[b].delay = _ptr(w) if w.size else None, _ptr(dl) if dl.size else None
@@ -270,6 +285,8 @@ def sn_create_shared_dense_i8(threshold, leak, reset, refractory, w, trains, *, 
     keep = []
     nr = _neurons(threshold, leak, reset, refractory, keep)
     w8 = np.ascontiguousarray(w, np.int8)
+    if w8.size != nr.n * nr.n:
+        raise ValueError(f"shared weights: expected {nr.n} x {nr.n} values, got {w8.size}")
     cfg = _config(SN_I32, 1, 0, record_steps, stream)
     h = _P()
     _check(lib().sn_create_shared_dense_i8(C.byref(cfg), C.byref(nr), _ptr(w8), int(trains), C.byref(h)))
@@ -322,20 +339,25 @@ def split_batch_raster(bits, net_n):
 
 
 def sn_set_input(ctx: Ctx, step, neuron, value):
-    s, j, v = _arr(step, np.int32), _arr(neuron, np.int32), _arr(value, np.float32)
+    s, j = _arr(step, np.int32).reshape(-1), _arr(neuron, np.int32).reshape(-1)
+    if s.size != j.size:
+        raise ValueError(f"input events: {s.size} steps and {j.size} neurons")
+    (v,) = _match("input event values", s.size, _arr(value, np.float32))
     _check(lib().sn_set_input(ctx.handle, s.size, _ptr(s) if s.size else None,
                               _ptr(j) if j.size else None, _ptr(v) if v.size else None), ctx)
 
 
 def sn_set_poisson(ctx: Ctx, neuron, rate, amplitude, seed):
-    j, r, a = _arr(neuron, np.int32), _arr(rate, np.float32), _arr(amplitude, np.float32)
+    j = _arr(neuron, np.int32).reshape(-1)
+    r, a = _match("Poisson rates and amplitudes", j.size, _arr(rate, np.float32), _arr(amplitude, np.float32))
     _check(lib().sn_set_poisson(ctx.handle, j.size, _ptr(j) if j.size else None,
                                 _ptr(r) if r.size else None, _ptr(a) if a.size else None,
                                 int(seed) & (2**64 - 1)), ctx)
 
 
 def sn_set_poisson_stream(ctx: Ctx, neuron, rate, amplitude, seed, net):
-    j, r, a = _arr(neuron, np.int32), _arr(rate, np.float32), _arr(amplitude, np.float32)
+    j = _arr(neuron, np.int32).reshape(-1)
+    r, a = _match("Poisson rates and amplitudes", j.size, _arr(rate, np.float32), _arr(amplitude, np.float32))
     _check(lib().sn_set_poisson_stream(ctx.handle, j.size, _ptr(j) if j.size else None,
                                        _ptr(r) if r.size else None, _ptr(a) if a.size else None,
                                        int(seed) & (2**64 - 1), int(net) & (2**64 - 1)), ctx)

@@ -263,3 +263,24 @@ def test_binding_neuron_arrays(S):
     assert lk.size == 5 and np.all(lk == np.float32(0.1)) and np.all(keep[3] == 2)
     with pytest.raises(ValueError):
         S._neurons(np.ones(5), np.zeros(4), 0.0, 0, [])
+
+
+def test_binding_synapse_and_input_arrays(S):
+    """Synapse, input-event and Poisson arrays: pre and post must pair up,
+    weights and delays (event values, rates, amplitudes) match or are single
+    values; everything is checked before a C call (no GPU needed here)."""
+    keep = []
+    pre, post, w, d = S._synapses([0, 1, 2], [1, 2, 0], 0.5, [1, 2, 3], keep)
+    assert w.tolist() == [0.5] * 3 and d.tolist() == [1, 2, 3]
+    for bad in (([0, 1], [1], 1.0, 1), ([0, 1], [1, 0], [1.0, 2.0, 3.0], 1), ([0, 1], [1, 0], 1.0, [1, 2, 3])):
+        with pytest.raises(ValueError):
+            S._synapses(*bad, [])
+    dummy = S.Ctx(None, 4, 0, 1, "sparse", 0)
+    with pytest.raises(ValueError):
+        S.sn_set_input(dummy, [0, 1], [0], [1.0, 1.0])
+    with pytest.raises(ValueError):
+        S.sn_set_input(dummy, [0, 1], [0, 1], [1.0, 1.0, 1.0])
+    with pytest.raises(ValueError):
+        S.sn_set_poisson(dummy, [0, 1, 2], [0.1, 0.2], 1.0, 7)
+    with pytest.raises(ValueError):
+        S.sn_create_dense(np.ones(3), 0.0, 0.0, 0, np.zeros(8, np.float32))
