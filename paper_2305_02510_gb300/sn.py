@@ -154,6 +154,19 @@ def _is_dev(x):
     return hasattr(x, "is_cuda") and x.is_cuda
 
 
+def _out(x, nbytes, what):
+    """A caller's output buffer (numpy array or torch tensor) must be
+    contiguous and hold at least nbytes: the library writes that many."""
+    if hasattr(x, "data_ptr"):
+        size, contig = x.numel() * x.element_size(), x.is_contiguous()
+    else:
+        size, contig = x.nbytes, x.flags["C_CONTIGUOUS"]
+    if not contig or size < nbytes:
+        raise ValueError(f"{what}: need a contiguous buffer of {nbytes} bytes, got {size}"
+                         f"{'' if contig else ' (not contiguous)'}")
+    return x
+
+
 class Ctx:
     """Owns one sn_ctx handle; n, dtype and kind are kept for output sizing."""
 
@@ -384,6 +397,7 @@ def sn_get_spikes(ctx: Ctx, t0: int, t1: int, out=None):
     tensor of that shape (int32 or uint32 storage) for a device-side copy."""
     if out is None:
         out = np.zeros((t1 - t0, ctx.words), np.uint32)
+    _out(out, max(0, t1 - t0) * ctx.words * 4, "sn_get_spikes")
     _check(lib().sn_get_spikes(ctx.handle, int(t0), int(t1), _ptr(out), int(_is_dev(out))), ctx)
     return out
 
@@ -401,6 +415,8 @@ def sn_get_state(ctx: Ctx, v=None, refractory=None):
         v = np.zeros(ctx.n, vt)
     if refractory is None:
         refractory = np.zeros(ctx.n, np.int32)
+    _out(v, ctx.n * 4, "sn_get_state (v)")
+    _out(refractory, ctx.n * 4, "sn_get_state (refractory)")
     dev = _is_dev(v)
     _check(lib().sn_get_state(ctx.handle, _ptr(v), _ptr(refractory), int(dev)), ctx)
     return v, refractory
@@ -409,6 +425,7 @@ def sn_get_state(ctx: Ctx, v=None, refractory=None):
 def sn_get_trace(ctx: Ctx, out=None):
     if out is None:
         out = np.zeros(ctx.n, np.float32)
+    _out(out, ctx.n * 4, "sn_get_trace")
     _check(lib().sn_get_trace(ctx.handle, _ptr(out), int(_is_dev(out))), ctx)
     return out
 
@@ -416,6 +433,7 @@ def sn_get_trace(ctx: Ctx, out=None):
 def sn_get_weights(ctx: Ctx, out=None):
     if out is None:
         out = np.zeros(ctx.m, np.float32)
+    _out(out, ctx.m * 4, "sn_get_weights")
     _check(lib().sn_get_weights(ctx.handle, _ptr(out), int(_is_dev(out))), ctx)
     return out
 
@@ -424,6 +442,7 @@ def sn_set_weights(ctx: Ctx, w):
     """Replace the weights (same layout as sn_get_weights); w is a host array
     or a device tensor."""
     if _is_dev(w):
+        _out(w, ctx.m * 4, "sn_set_weights")
         _check(lib().sn_set_weights(ctx.handle, _ptr(w), 1), ctx)
         return
     w = np.ascontiguousarray(w, dtype=np.float32).reshape(-1)

@@ -284,3 +284,25 @@ def test_binding_synapse_and_input_arrays(S):
         S.sn_set_poisson(dummy, [0, 1, 2], [0.1, 0.2], 1.0, 7)
     with pytest.raises(ValueError):
         S.sn_create_dense(np.ones(3), 0.0, 0.0, 0, np.zeros(8, np.float32))
+
+
+def test_binding_output_buffers(S):
+    """Caller-provided output buffers must be contiguous and large enough
+    for what the library writes; checked before the C call."""
+    dummy = S.Ctx(None, 40, 0, 2, "sparse", 10)
+    with pytest.raises(ValueError):
+        S.sn_get_spikes(dummy, 0, 5, out=np.zeros((4, 2), np.uint32))
+    with pytest.raises(ValueError):
+        S.sn_get_spikes(dummy, 0, 5, out=np.zeros((5, 4), np.uint32)[:, ::2])
+    with pytest.raises(ValueError):
+        S.sn_get_state(dummy, v=np.zeros(39, np.float32))
+    with pytest.raises(ValueError):
+        S.sn_get_state(dummy, refractory=np.zeros(10, np.int32))
+    with pytest.raises(ValueError):
+        S.sn_get_weights(dummy, out=np.zeros(9, np.float32))
+    with pytest.raises(ValueError):
+        S.sn_get_trace(dummy, out=np.zeros(3, np.float32))
+    torch = pytest.importorskip("torch")
+    with pytest.raises(ValueError):
+        S._out(torch.zeros(3), 16, "x")
+    assert S._out(torch.zeros(4), 16, "x") is not None
