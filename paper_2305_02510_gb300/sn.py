@@ -492,6 +492,11 @@ def sn_create_ff(sizes, delays, *, threshold, leak, reset, refractory, slope, ch
     recompute: SN_FF_RECOMPUTE (the backward recomputes the synaptic input)."""
     sz = np.ascontiguousarray(sizes, np.int32)
     ds = [np.ascontiguousarray(d, np.uint8) for d in delays]
+    if sz.size != len(ds) + 1:
+        raise ValueError(f"{sz.size} layer sizes need {sz.size - 1} delay arrays, got {len(ds)}")
+    for l, d in enumerate(ds):
+        if d.size != int(sz[l]) * int(sz[l + 1]):
+            raise ValueError(f"delays[{l}]: expected {int(sz[l])} x {int(sz[l + 1])} values, got {d.size}")
     ptrs = (C.c_void_p * len(ds))(*[_ptr(d) for d in ds])
     p = sn_ff_params(float(threshold), float(leak), float(reset), int(refractory), float(slope),
                      int(checkpoint_every))
@@ -508,14 +513,37 @@ def sn_ff_set_engine(ctx: Ctx, engine: int):
     _check(lib().sn_ff_set_engine(ctx.handle, int(engine)), ctx)
 
 
+def _dev(t, numel, dtype, what):
+    """A CUDA tensor of `numel` elements of `dtype` ("uint8", "float32"),
+    contiguous: the library reads or writes exactly that many."""
+    if not _is_dev(t):
+        raise ValueError(f"{what}: expected a CUDA tensor")
+    if str(t.dtype) != "torch." + dtype or not t.is_contiguous() or t.numel() != numel:
+        raise ValueError(f"{what}: expected a contiguous {dtype} tensor of {numel} elements, got "
+                         f"{t.dtype} with {t.numel()} (contiguous: {t.is_contiguous()})")
+
+
+def _ff_layers(ctx, tensors, dtype, what):
+    L = len(ctx.sizes) - 1
+    if len(tensors) != L:
+        raise ValueError(f"{what}: expected {L} tensors, got {len(tensors)}")
+    for l, t in enumerate(tensors):
+        _dev(t, ctx.sizes[l] * ctx.sizes[l + 1], dtype, f"{what}[{l}]")
+
+
 def sn_ff_forward(ctx: Ctx, input_spikes, weights, counts):
     """input_spikes: CUDA uint8 [steps, batch, n0]; weights: CUDA float32
     tensors [n_in, n_out]; counts: CUDA float32 [batch, n_out] (written)."""
+    _dev(input_spikes, ctx.steps * ctx.batch * ctx.sizes[0], "uint8", "input spikes")
+    _ff_layers(ctx, weights, "float32", "weights")
+    _dev(counts, ctx.batch * ctx.sizes[-1], "float32", "counts")
     ptrs = (C.c_void_p * len(weights))(*[_ptr(w) for w in weights])
     _check(lib().sn_ff_forward(ctx.handle, _ptr(input_spikes), ptrs, _ptr(counts)), ctx)
 
 
 def sn_backward(ctx: Ctx, grad_counts, grad_weights):
+    _dev(grad_counts, ctx.batch * ctx.sizes[-1], "float32", "count gradient")
+    _ff_layers(ctx, grad_weights, "float32", "weight gradients")
     ptrs = (C.c_void_p * len(grad_weights))(*[_ptr(g) for g in grad_weights])
     _check(lib().sn_backward(ctx.handle, _ptr(grad_counts), ptrs, 1), ctx)
 

@@ -306,3 +306,23 @@ def test_binding_output_buffers(S):
     with pytest.raises(ValueError):
         S._out(torch.zeros(3), 16, "x")
     assert S._out(torch.zeros(4), 16, "x") is not None
+
+
+def test_binding_ff_arguments(S):
+    """Feedforward contexts: one delay array of n_in x n_out per layer at
+    creation, and CUDA tensors of the exact sizes and dtypes for the forward
+    and backward, checked before any C call."""
+    with pytest.raises(ValueError):
+        S.sn_create_ff([3, 4, 2], [np.ones((3, 4), np.uint8)], threshold=1, leak=0, reset=0, refractory=0,
+                       slope=10, checkpoint_every=10, batch=2, steps=10)
+    with pytest.raises(ValueError):
+        S.sn_create_ff([3, 4], [np.ones((3, 5), np.uint8)], threshold=1, leak=0, reset=0, refractory=0,
+                       slope=10, checkpoint_every=10, batch=2, steps=10)
+    dummy = S.Ctx(None, 2, 0, 0, "ff", 0)
+    dummy.sizes, dummy.batch, dummy.steps, dummy.k = [3, 4, 2], 2, 10, 10
+    with pytest.raises(ValueError):                     # host arrays are not CUDA tensors
+        S.sn_ff_forward(dummy, np.zeros((10, 2, 3), np.uint8), [np.zeros((3, 4), np.float32)] * 2,
+                        np.zeros((2, 2), np.float32))
+    torch = pytest.importorskip("torch")
+    with pytest.raises(ValueError):
+        S._dev(torch.zeros(6), 6, "float32", "x")      # a CPU tensor
