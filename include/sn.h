@@ -33,7 +33,13 @@
  *   - The context owns all device memory it allocates; sn_destroy frees it.
  *   - Work is issued on the context's CUDA stream (sn_config.cuda_stream, or
  *     the legacy default stream when NULL).  sn_run returns once the work is
- *     queued; sn_sync waits for it.  Host-buffer getters synchronise.
+ *     queued; sn_sync waits for it.  Host-buffer getters synchronise.  Calls
+ *     that replace device-side inputs or tables (sn_set_input,
+ *     sn_set_poisson, sn_stdp, sn_set_propagation, sn_set_weights of a
+ *     sparse network, sn_batch_config) first wait for the work queued on the
+ *     context's stream, so a run already queued (also on a
+ *     cudaStreamNonBlocking stream) sees the old values and the next run the
+ *     new ones.
  *   - No exception crosses the ABI.  Each call returns an sn_status;
  *     sn_last_error gives a message for the last failure of a context.
  *     Device-side failures (a timed-out grid barrier, an integer overflow)
@@ -400,15 +406,14 @@ sn_status sn_ff_get_checkpoints(sn_ctx *ctx, int32_t layer, float *v, int32_t on
 
 /* ------------------------------------------------------------------------
  * Dense run without allocation.  The paper has no counterpart: this entry
- * point exists for callers that cannot allocate device memory, for example
- * code running while a CUDA stream is being captured into a graph (where
- * cudaMalloc is not allowed), or a host application whose device memory is
- * fully reserved by its own pool allocator.
+ * point exists for callers that cannot allocate device memory, for example a
+ * host application whose device memory is all reserved by its own pool
+ * allocator, or a plug-in whose host process does not let it allocate.
  *
  * It simulates `steps` timesteps (steps 0 .. steps-1) of an all-to-all
- * network exactly as sn_create_dense + sn_run would, on buffers the caller
- * owns, starting from the caller's state with no synaptic input pending and
- * no explicit events.  Every pointer below is a device pointer:
+ * network exactly as sn_create_dense + sn_run would (bit for bit), on buffers
+ * the caller owns, starting from the caller's state with no synaptic input
+ * pending and no explicit events.  Every pointer below is a device pointer:
  *   w                  [n*n] row-major weights (row = pre), read only
  *   threshold, leak, reset [n] float; refractory [n] int32
  *   poisson_threshold  [n] uint32 = floor(rate * 2^32) per neuron (0: none),
@@ -420,15 +425,17 @@ sn_status sn_ff_get_checkpoints(sn_ctx *ctx, int32_t layer, float *v, int32_t on
  * The kernel's scratch (spike bits of the last two steps, pending-input
  * ring, control block) lives in one static device array of
  * SN_NOALLOC_SCRATCH_BYTES, held by every device that loads the library until
- * the process exits.  A network whose scratch does not fit is rejected with
- * SN_EINVAL; the need is about 4 * (delay + 2) * n bytes, so every network up
- * to the 200,000-neuron dense limit fits while delay <= 18.  The first call
- * on a device
- * looks up the array's device address with that device current; make that
- * first call before any stream capture.  Every call shares the array and
- * clears it first, so calls whose work overlaps on the GPU (two streams,
- * two threads) race and must not be issued.  The call waits for its work and
- * returns the device status (SN_ETIMEOUT if a grid barrier gave up).
+ * the process exits.  A network needs
+ *   256 + 256-rounded(8 * ceil(n/32)) + 256-rounded(4 * (delay + 1) * n)
+ *       + 256-rounded(4 * n) bytes
+ * of it (so every network up to the 200,000-neuron dense limit fits while
+ * delay <= 18); a larger need is rejected with SN_EINVAL before any CUDA
+ * call, with the sizes in sn_last_error(NULL).  The first call on a device
+ * looks up the array's device address with that device current.  Every call
+ * shares the array and clears it first, so calls whose work overlaps on the
+ * GPU (two streams, two threads) race and must not be issued.  The call
+ * waits for its work to finish and returns the device status (SN_ETIMEOUT if
+ * a grid barrier gave up); messages of failures go to sn_last_error(NULL).
  * ------------------------------------------------------------------------ */
 #define SN_NOALLOC_SCRATCH_BYTES (16u << 20)
 

@@ -142,6 +142,7 @@ sn_status select_pull(sn_ctx *c) {
                         "memory and at most 1024 neurons per SM");
     }
     sn_status s;
+    if ((s = quiesce(c))) return s;            // a queued push run may still read the ring
     if (!c->hist) {
         if ((s = dalloc(c, &c->hist, (size_t)c->D * c->words * 4))) return s;
         SN_CUDA(c, cudaMemset(c->hist, 0, (size_t)c->D * c->words * 4));
@@ -438,6 +439,7 @@ sn_status sn_set_input(sn_ctx *c, int64_t nev, const int32_t *step, const int32_
         vi.push_back((int)si);
     }
     for (int t = 0; t <= max_step; ++t) off[t + 1] += off[t];
+    if (sn_status q = quiesce(c)) return q;   // a queued run may read the old events
     dfree(c, c->ev_off); dfree(c, c->ev_neuron); dfree(c, c->ev_val);
     c->ev_off = c->ev_neuron = nullptr;
     c->ev_val = nullptr;
@@ -481,6 +483,7 @@ sn_status sn_set_poisson(sn_ctx *c, int32_t nsrc, const int32_t *neuron, const f
         af[j] = amp[k];
         ai[j] = (int)amp[k];
     }
+    if (sn_status q = quiesce(c)) return q;   // a queued run may read the old sources
     SN_CUDA(c, cudaMemcpy(c->prate, thr.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
     SN_CUDA(c, cudaMemcpy(c->pamp, c->dtype == SN_F32 ? (const void *)af.data() : (const void *)ai.data(),
                           (size_t)n * 4, cudaMemcpyHostToDevice));
@@ -508,6 +511,7 @@ sn_status sn_stdp(sn_ctx *c, float decay, float a_plus, float a_minus, float wmi
     if (!(std::isfinite(decay) && std::isfinite(a_plus) && std::isfinite(a_minus) && std::isfinite(wmin) &&
           std::isfinite(wmax) && wmin <= wmax))
         return fail(c, SN_EINVAL, "bad STDP parameters");
+    if (sn_status q = quiesce(c)) return q;   // queued runs use the current rule and weights
     if (!c->trace) {
         sn_status s = dalloc(c, &c->trace, (size_t)3 * c->n * 4);
         if (s) return s;
@@ -805,6 +809,7 @@ sn_status sn_set_weights(sn_ctx *c, const float *w, int32_t on_device) {
     if (c->kind != KIND_SPARSE) return fail(c, SN_ESTATE, "wrong context kind");
     if (c->dtype != SN_F32) return fail(c, SN_EUNSUPPORTED, "weights of SN_I32 networks are fixed at creation");
     if (c->m == 0) return SN_OK;
+    if (sn_status q = quiesce(c)) return q;    // queued runs read the current weights
     if (!c->perm_inv) {
         sn_status s = dalloc(c, &c->perm_inv, (size_t)c->m * 8);
         if (s) return s;

@@ -121,6 +121,7 @@ sn_status batch_set_poisson(sn_ctx *c, int32_t nsrc, const int32_t *neuron, cons
     }
     std::vector<unsigned long long> keys(c->nets);
     for (int b = 0; b < c->nets; ++b) keys[b] = host_splitmix64(seed ^ host_splitmix64((unsigned long long)b));
+    if (sn_status q = quiesce(c)) return q;   // a queued run may read the old sources
     SN_CUDA(c, cudaMemcpy(c->prate, thr.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
     SN_CUDA(c, cudaMemcpy(c->pamp, c->dtype == SN_F32 ? (const void *)af.data() : (const void *)ai.data(),
                           (size_t)n * 4, cudaMemcpyHostToDevice));
@@ -308,6 +309,7 @@ sn_status sn_batch_config(sn_ctx *c, int32_t warp_max_n, int32_t ring_smem_bytes
     if (warp_max_n < 0 || warp_max_n > 512) return fail(c, SN_EINVAL, "warp_max_n must be in 0..512");
     if (ring_smem_bytes < 0 || ring_smem_bytes > 192 * 1024 || ring_smem_bytes % 1024)
         return fail(c, SN_EINVAL, "ring_smem_bytes must be a multiple of 1024 in 0..196608");
+    if (sn_status q = quiesce(c)) return q;   // a queued run reads the work queues
     c->warp_max_n = warp_max_n;
     c->ring_smem = ring_smem_bytes;
     sn_status s;

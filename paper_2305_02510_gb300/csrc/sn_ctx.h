@@ -125,6 +125,16 @@ inline sn_status cuda_fail(sn_ctx *c, cudaError_t e, const char *what) {
     return fail(c, SN_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// Wait for the work queued on the context's stream.  Host calls that rewrite
+// device buffers with blocking copies (setters, mode switches) call this
+// first: a blocking cudaMemcpy orders itself after the legacy default stream
+// but not after a cudaStreamNonBlocking stream, where a queued run may still
+// be reading the buffer.
+inline sn_status quiesce(sn_ctx *c) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    return e == cudaSuccess ? SN_OK : cuda_fail(c, e, "waiting for the context's queued work");
+}
+
 #define SN_CUDA(ctx, call)                                           \
     do {                                                             \
         cudaError_t e_ = (call);                                     \

@@ -1,6 +1,7 @@
 // Tensor-core (tcgen05, BF16 operands, FP32 accumulation in TMEM) contractions
-// of the feedforward network's backward pass (sn_ff.cu has the forward, the
-// recurrences and the SIMT forms of these contractions).
+// of the feedforward network: the forward synaptic input (ff_tc_fwd_kernel)
+// and the backward's spike and weight gradients (ff_tc_kernel).  sn_ff.cu has
+// the recurrences and the SIMT forms of these contractions.
 //
 // A delay-shifted contraction is a sum of plain GEMMs, one per delay d, with
 // the weights restricted to the synapses of delay d (W_d = W masked by
@@ -25,7 +26,7 @@
 // blocks of an A and one or two B tensor maps at given coordinate offsets
 // (both B tiles multiply the same A tile, which is loaded once), into one of
 // up to four TMEM accumulators of a 128 x 128 output tile.  The structure is
-// that of sn_shared.cu: warp 0 lane 0 issues TMA into a 6-stage ring, warp 1
+// that of sn_shared.cu: warp 0 lane 0 issues TMA into a 4-stage ring, warp 1
 // lane 0 issues the MMAs, then all eight warps drain the accumulators through
 // shared memory into coalesced FP32 rows.  Work items are (tile, K split)
 // pairs taken by a persistent grid; every wait is bounded.

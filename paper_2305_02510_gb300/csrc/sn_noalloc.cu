@@ -1,8 +1,10 @@
 // sn_run_dense_noalloc: the dense simulation for callers that cannot allocate
-// device memory.  It launches the same dense kernel as sn_run on a dense
-// context, but every buffer comes from the caller except the kernel's scratch
-// (spike bits of the last two steps, pending-input ring, zero Poisson table,
-// control block), which lives in one fixed file-scope device array.  No cudaMalloc, cudaFree or
+// device memory (an application whose device memory is all owned by its own
+// pool allocator, or a plug-in whose host forbids it to allocate).  It launches
+// the same dense kernel as sn_run on a dense context, but every buffer comes
+// from the caller except the kernel's scratch (spike bits of the last two
+// steps, pending-input ring, zero Poisson table, control block), which lives
+// in one fixed file-scope device array.  No cudaMalloc, cudaFree or
 // allocating library routine is called on this path.
 
 #include <cuda_runtime.h>
@@ -12,6 +14,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include "sn_ctx.h"
 #include "sn_internal.h"
 
 namespace {
@@ -44,43 +47,66 @@ sn_status scratch_address(int dev, void **out) {
 
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Bytes of scratch a network of n neurons with synaptic delay `delay` needs:
+// control | spike bits [2][words] | ring [delay + 1][n] | zero Poisson table [n].
+struct ScratchLayout {
+    size_t off_spk, off_ring, off_zero, need;
+};
+
+ScratchLayout scratch_layout(int n, int delay) {
+    const size_t words = ((size_t)n + 31) / 32;
+    ScratchLayout L;
+    L.off_spk = align256(sizeof(sn::Control));
+    L.off_ring = L.off_spk + align256(2 * words * 4);
+    L.off_zero = L.off_ring + align256((size_t)(delay + 1) * n * 4);
+    L.need = L.off_zero + align256((size_t)n * 4);
+    return L;
+}
+
 }  // namespace
 
 extern "C" sn_status sn_run_dense_noalloc(const sn_dense_noalloc_args *p) {
     using namespace sn;
-    if (!p) return SN_EINVAL;
+    if (!p) return fail(nullptr, SN_EINVAL, "sn_run_dense_noalloc: NULL arguments");
     const int n = p->n;
-    if (n < 1 || n > 200000 || p->steps < 0 || p->delay < 1 || p->delay > SN_MAX_DELAY) return SN_EINVAL;
+    if (n < 1 || n > 200000) return fail(nullptr, SN_EINVAL, "sn_run_dense_noalloc: n outside 1..200000");
+    if (p->steps < 0) return fail(nullptr, SN_EINVAL, "sn_run_dense_noalloc: steps < 0");
+    if (p->delay < 1 || p->delay > SN_MAX_DELAY)
+        return fail(nullptr, SN_EINVAL, "sn_run_dense_noalloc: delay outside 1..64");
     if (!p->w || !p->threshold || !p->leak || !p->reset || !p->refractory || !p->v || !p->r ||
         (p->steps > 0 && !p->raster))
-        return SN_EINVAL;
-    if ((p->poisson_threshold == nullptr) != (p->poisson_amplitude == nullptr)) return SN_EINVAL;
+        return fail(nullptr, SN_EINVAL, "sn_run_dense_noalloc: a required pointer is NULL");
+    if ((p->poisson_threshold == nullptr) != (p->poisson_amplitude == nullptr))
+        return fail(nullptr, SN_EINVAL,
+                    "sn_run_dense_noalloc: poisson_threshold and poisson_amplitude must both be given or both NULL");
+    // the scratch check needs only n and delay, so it comes before any CUDA call
+    const ScratchLayout lay = scratch_layout(n, p->delay);
+    if (lay.need > kScratchBytes)
+        return fail(nullptr, SN_EINVAL,
+                    "sn_run_dense_noalloc: the network needs " + std::to_string(lay.need) +
+                        " bytes of scratch, more than the fixed " + std::to_string(kScratchBytes));
     if (p->steps == 0) return SN_OK;
     cudaStream_t stream = (cudaStream_t)p->cuda_stream;
 
     // executor sizing, the same rule as a dense context
     const int words = (n + 31) / 32;
     int grid = 0, chunk = 0;
-    if (plan_dense(n, &grid, &chunk) != cudaSuccess) return SN_ECUDA;
-    if (grid < 1) return SN_EUNSUPPORTED;
+    cudaError_t ce = plan_dense(n, &grid, &chunk);
+    if (ce != cudaSuccess) return cuda_fail(nullptr, ce, "sn_run_dense_noalloc: executor sizing");
+    if (grid < 1) return fail(nullptr, SN_EUNSUPPORTED, "sn_run_dense_noalloc: no co-resident grid for this n");
     const int D1 = p->delay + 1;
-
-    // scratch layout: control | spike bits [2][words] | ring [D1][n] | zero Poisson table [n]
-    const size_t off_spk = align256(sizeof(Control));
-    const size_t off_ring = off_spk + align256((size_t)2 * words * 4);
-    const size_t off_zero = off_ring + align256((size_t)D1 * n * 4);
-    const size_t need = off_zero + align256((size_t)n * 4);
-    if (need > kScratchBytes) return SN_EINVAL;   // beyond the fixed scratch
+    const size_t off_spk = lay.off_spk, off_ring = lay.off_ring, off_zero = lay.off_zero, need = lay.need;
 
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return SN_ECUDA;
     void *base = nullptr;
     sn_status st = scratch_address(dev, &base);
-    if (st != SN_OK) return st;
+    if (st != SN_OK) return fail(nullptr, st, "sn_run_dense_noalloc: scratch address lookup failed");
     unsigned char *b = (unsigned char *)base;
 
     // zero what must start at zero: control block, spike bits, ring, table
-    if (cudaMemsetAsync(b, 0, need, stream) != cudaSuccess) return SN_ECUDA;
+    ce = cudaMemsetAsync(b, 0, need, stream);
+    if (ce != cudaSuccess) return cuda_fail(nullptr, ce, "sn_run_dense_noalloc: clearing the scratch");
 
     NetArgs a;
     memset(&a, 0, sizeof(a));
@@ -107,11 +133,15 @@ extern "C" sn_status sn_run_dense_noalloc(const sn_dense_noalloc_args *p) {
     a.ring = b + off_ring;
     a.raster = p->raster;
     a.ctl = (Control *)b;
-    if (launch_dense(a, grid, 256, stream) != cudaSuccess) return SN_ECUDA;
+    ce = launch_dense(a, grid, 256, stream);
+    if (ce != cudaSuccess) return cuda_fail(nullptr, ce, "sn_run_dense_noalloc: launch");
 
     // wait, then read the device status word (no allocation involved)
-    if (cudaStreamSynchronize(stream) != cudaSuccess) return SN_ECUDA;
+    ce = cudaStreamSynchronize(stream);
+    if (ce != cudaSuccess) return cuda_fail(nullptr, ce, "sn_run_dense_noalloc: synchronize");
     int status = 0;
-    if (cudaMemcpy(&status, b, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SN_ECUDA;
-    return (sn_status)status;
+    ce = cudaMemcpy(&status, b, sizeof(int), cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess) return cuda_fail(nullptr, ce, "sn_run_dense_noalloc: status read");
+    if (status != SN_OK) return fail(nullptr, (sn_status)status, "sn_run_dense_noalloc: the kernel latched a failure");
+    return SN_OK;
 }

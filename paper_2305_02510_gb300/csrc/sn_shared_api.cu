@@ -95,6 +95,7 @@ sn_status shared_set_poisson(sn_ctx *c, int32_t nsrc, const int32_t *neuron, con
     }
     std::vector<unsigned long long> keys(c->sh_B);
     for (int b = 0; b < c->sh_B; ++b) keys[b] = host_splitmix64(seed ^ host_splitmix64((unsigned long long)b));
+    if (sn_status q = quiesce(c)) return q;   // a queued run may read the old sources
     SN_CUDA(c, cudaMemcpy(c->prate, thr.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
     SN_CUDA(c, cudaMemcpy(c->pamp, ai.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
     SN_CUDA(c, cudaMemcpy(c->pkeys, keys.data(), keys.size() * 8, cudaMemcpyHostToDevice));

@@ -469,21 +469,60 @@ def sn_load(ctx: Ctx, blob: bytes):
     _check(lib().sn_load(ctx.handle, blob, len(blob)), ctx)
 
 
+def _noalloc_arg(t, numel, dtypes, what, device, at_least=False):
+    """A CUDA tensor on `device`, contiguous, of one of `dtypes`, holding
+    exactly (or, for outputs, at least) `numel` elements: the kernel reads or
+    writes that many through the raw pointer."""
+    if not _is_dev(t):
+        raise ValueError(f"{what}: expected a CUDA tensor, got {type(t).__name__}")
+    if t.device != device:
+        raise ValueError(f"{what}: on {t.device}, expected {device} (the weights' device)")
+    if str(t.dtype).replace("torch.", "") not in dtypes:
+        raise ValueError(f"{what}: dtype {t.dtype}, expected one of {dtypes}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what}: not contiguous")
+    if (t.numel() < numel) if at_least else (t.numel() != numel):
+        raise ValueError(f"{what}: {t.numel()} elements, expected {'at least ' if at_least else ''}{numel}")
+
+
 def sn_run_dense_noalloc(n, delay, steps, w, threshold, leak, reset, refractory, v, r, raster,
                          poisson_threshold=None, poisson_amplitude=None, seed=0, stream=None):
-    """Dense run on caller-owned device tensors (torch CUDA tensors); the
-    library allocates nothing.  Raises SnError on a non-OK status."""
+    """Dense run on caller-owned device tensors (torch CUDA tensors, all on
+    the current device); the library allocates nothing.  w float32 [n*n];
+    threshold, leak, reset, v float32 [n]; refractory, r int32 [n]; raster
+    int32 or uint32, at least steps * ceil(n/32) words; poisson_threshold
+    int32 or uint32 [n] and poisson_amplitude float32 [n], both or neither.
+    Every argument is checked before the C call (ValueError); a non-OK status
+    raises SnError."""
+    import torch
+    n, delay, steps = int(n), int(delay), int(steps)
+    if n < 1 or steps < 0:
+        raise ValueError(f"n = {n} and steps = {steps}: need n >= 1, steps >= 0")
+    if (poisson_threshold is None) != (poisson_amplitude is None):
+        raise ValueError("poisson_threshold and poisson_amplitude: give both or neither")
+    if not _is_dev(w):
+        raise ValueError("w: expected a CUDA tensor")
+    device = torch.device("cuda", torch.cuda.current_device())
+    words = (n + 31) // 32
+    _noalloc_arg(w, n * n, ("float32",), "w", device)
+    for t, what in ((threshold, "threshold"), (leak, "leak"), (reset, "reset"), (v, "v")):
+        _noalloc_arg(t, n, ("float32",), what, device)
+    for t, what in ((refractory, "refractory"), (r, "r")):
+        _noalloc_arg(t, n, ("int32",), what, device)
+    if steps > 0:
+        _noalloc_arg(raster, steps * words, ("int32", "uint32"), "raster", device, at_least=True)
+    if poisson_threshold is not None:
+        _noalloc_arg(poisson_threshold, n, ("int32", "uint32"), "poisson_threshold", device)
+        _noalloc_arg(poisson_amplitude, n, ("float32",), "poisson_amplitude", device)
     a = sn_dense_noalloc_args()
-    a.n, a.delay, a.steps = int(n), int(delay), int(steps)
+    a.n, a.delay, a.steps = n, delay, steps
     a.w, a.threshold, a.leak, a.reset = _ptr(w), _ptr(threshold), _ptr(leak), _ptr(reset)
     a.refractory = _ptr(refractory)
     a.poisson_threshold, a.poisson_amplitude = _ptr(poisson_threshold), _ptr(poisson_amplitude)
     a.seed = int(seed) & (2**64 - 1)
-    a.v, a.r, a.raster = _ptr(v), _ptr(r), _ptr(raster)
+    a.v, a.r, a.raster = _ptr(v), _ptr(r), _ptr(raster) if steps > 0 else None
     a.cuda_stream = stream
-    st = lib().sn_run_dense_noalloc(C.byref(a))
-    if st != SN_OK:
-        raise SnError(st, "sn_run_dense_noalloc failed")
+    _check(lib().sn_run_dense_noalloc(C.byref(a)))
 
 
 def sn_create_ff(sizes, delays, *, threshold, leak, reset, refractory, slope, checkpoint_every,

@@ -229,6 +229,31 @@ def test_noalloc_zero_steps_is_a_no_op(S):
     assert S.lib().sn_run_dense_noalloc(None) == S.SN_EINVAL
 
 
+def test_noalloc_rejects_oversized_scratch_before_any_cuda_call(S):
+    """The scratch need depends only on n and delay, so a network beyond the
+    fixed array is refused (with the sizes in the message) before any CUDA
+    call: here with dummy pointers and no GPU."""
+    # 70,000 neurons at delay 64: about 65 * 4 * 70000 bytes of ring, over 16 MiB
+    assert _noalloc(S, n=70000, delay=64) == S.SN_EINVAL
+    msg = S.lib().sn_last_error(None).decode()
+    assert "scratch" in msg and str(16 << 20) in msg, msg
+    # the largest delay that fits 200,000 neurons is accepted by the check
+    # (zero steps: nothing runs)
+    assert _noalloc(S, n=200000, delay=18, steps=0, raster=None) == S.SN_OK
+    assert _noalloc(S, n=200000, delay=19, steps=0, raster=None) == S.SN_EINVAL
+
+
+def test_noalloc_binding_rejects_host_arrays(S):
+    """The binding wants CUDA tensors: numpy arrays (host pointers the kernel
+    would dereference) raise ValueError before the C call."""
+    n = 8
+    z = np.zeros(n, np.float32)
+    zi = np.zeros(n, np.int32)
+    with pytest.raises(ValueError):
+        S.sn_run_dense_noalloc(n, 1, 2, np.zeros(n * n, np.float32), z, z, z, zi, z.copy(), zi.copy(),
+                               np.zeros(2, np.int32))
+
+
 def _dense(S, n=4, delay=1, D=2, dtype=0, wval=0.5, flags=0):
     keep = []
     nr, _ = _neurons(S, n, keep)
