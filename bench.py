@@ -39,9 +39,80 @@ TIMESTEPS = 1000
 STATE_BYTES = 56
 # the pull kernel touches the same state without the pending-input slot
 STATE_BYTES_PULL = 40
-# DRAM bytes (read + write) of one 1000-timestep launch, from the ncu capture
-# of the current kernel version (absent: none taken for that kernel)
-NCU_TRAFFIC_BYTES = {"sparse_pull_kernel<SN_F32>": 2.30e9 + 3.80e6}
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch per
+# kernel, as measured by ncu, with a hash of the sources that kernel is built
+# from when it was measured; a figure whose sources changed since is stale and
+# not reported (bench.py --record-traffic writes this file from an ncu CSV)
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+CSRC = os.path.join(ROOT, "paper_2305_02510_gb300", "csrc")
+KERNEL_SOURCES = {
+    "sparse_pull_kernel": ["sn_pull.cu", "sn_device.cuh", "sn_internal.h"],
+    "sparse_reg_kernel": ["sn_kernels.cu", "sn_device.cuh", "sn_internal.h"],
+    "dense_kernel": ["sn_kernels.cu", "sn_device.cuh", "sn_internal.h"],
+    "batch_kernel": ["sn_batch.cu", "sn_device.cuh", "sn_internal.h"],
+    "shared_kernel": ["sn_shared.cu", "sn_tc.cuh", "sn_device.cuh", "sn_internal.h"],
+}
+
+
+def kernel_source_hash(kernel):
+    """sha256 (first 16 hex digits) of the source files a kernel is built from."""
+    import hashlib
+    base = kernel.split("<")[0]
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES[base]:
+        with open(os.path.join(CSRC, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, workload):
+    """DRAM bytes per launch of `kernel` on `workload` from TRAFFIC_FILE, or
+    (None, reason) when none was recorded or the kernel's sources changed."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            rows = [ln.split("\t") for ln in f.read().splitlines() if ln and not ln.startswith("#")]
+    except OSError:
+        return None, "no ncu traffic recorded"
+    for r in rows:
+        if len(r) >= 5 and r[0] == kernel and r[1] == workload:
+            if r[2] != kernel_source_hash(kernel):
+                return None, "kernel changed since its ncu capture"
+            return float(r[3]), f"ncu dram__bytes_read.sum + dram__bytes_write.sum, commit {r[4]}"
+    return None, "no ncu traffic recorded for this kernel and workload"
+
+
+def record_traffic(csv_path, kernel, workload, launches_per_unit=1):
+    """Add (or replace) the TRAFFIC_FILE line of `kernel` on `workload` from an
+    ncu --csv capture with dram__bytes_read.sum and dram__bytes_write.sum: the
+    mean over the captured launches of that kernel, in bytes."""
+    import csv
+    unit = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9}
+    per = {}
+    with open(csv_path) as f:
+        lines = [ln for ln in f if ln.startswith('"')]
+    for row in csv.DictReader(lines):
+        if not row.get("Kernel Name", "").startswith(kernel.split("<")[0]):
+            continue
+        if row.get("Metric Name") not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            continue
+        v = float(row["Metric Value"].replace(",", "")) * unit.get(row.get("Metric Unit", "byte"), 1)
+        per.setdefault(row["ID"], 0.0)
+        per[row["ID"]] += v
+    if not per:
+        raise SystemExit(f"no dram__bytes rows for {kernel} in {csv_path}")
+    value = launches_per_unit * sum(per.values()) / len(per)
+    commit = subprocess.run(["git", "-C", ROOT, "rev-parse", "--short", "HEAD"], capture_output=True,
+                            text=True).stdout.strip() or "unknown"
+    keep = []
+    if os.path.exists(TRAFFIC_FILE):
+        with open(TRAFFIC_FILE) as f:
+            keep = [ln for ln in f.read().splitlines()
+                    if ln and not ln.startswith("#") and ln.split("\t")[:2] != [kernel, workload]]
+    with open(TRAFFIC_FILE, "w") as f:
+        f.write("# kernel\tworkload\tsource sha256 (16)\tDRAM bytes per launch\tcommit measured\n")
+        for ln in keep + [f"{kernel}\t{workload}\t{kernel_source_hash(kernel)}\t{value:.6g}\t{commit}"]:
+            f.write(ln + "\n")
+    print(f"{kernel} on {workload}: {value:.4g} B per launch ({len(per)} launches)")
 
 
 def replica_seed(seed, rank):
@@ -161,20 +232,48 @@ def algorithmic_bytes_pull(n, m, timesteps):
     return timesteps * (m * 8 + n * STATE_BYTES_PULL + n / 8)
 
 
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
 def oracle_sample(wl, warm=40, timed=60):
-    """The CPU oracle as it stands, single-threaded, on a bounded sample of the
-    workload: `warm` untimed timesteps from the initial state (past the start-up
-    transient), then `timed` timed timesteps.  Returns (events/s, timesteps/s,
-    sample text)."""
+    """The CPU oracle as it stands on a bounded sample of the workload: `warm`
+    untimed timesteps from the initial state (past the start-up transient),
+    then `timed` timesteps timed single-threaded and again on every host core
+    (the per-neuron loop split over threads; identical results).  Returns a
+    dict per thread count: events/s, timesteps/s, threads, sample text."""
     from oracle import oracle as O
     deg = np.bincount(np.asarray(wl["pre"]), minlength=wl["n"]).astype(np.int64)
-    st, _, _ = O.run(wl, O.F32, warm)
-    t0 = time.perf_counter()
-    st, raster, _ = O.run(wl, O.F32, timed, state=st)
-    dt = time.perf_counter() - t0
-    ev = int((raster.astype(np.int64) * deg[None, :]).sum())
-    return ev / dt, timed / dt, f"timesteps {warm}..{warm + timed - 1} of {wl['name']} (N={wl['n']}, " \
-                                f"M={len(wl['pre'])}), single-threaded C oracle, float32 mirror"
+    cores = host_cores()
+    O.set_threads(cores)
+    try:
+        base, _, _ = O.run(wl, O.F32, warm)
+        out = {}
+        for k in (1, cores):
+            O.set_threads(k)
+            t0 = time.perf_counter()
+            st, raster, _ = O.run(wl, O.F32, timed, state=base.copy())
+            dt = time.perf_counter() - t0
+            ev = int((raster.astype(np.int64) * deg[None, :]).sum())
+            out[k] = {"value": ev / dt, "timesteps_per_s": timed / dt, "cores": k,
+                      "sample": f"timesteps {warm}..{warm + timed - 1} of {wl['name']} (N={wl['n']}, "
+                                f"M={len(wl['pre'])}), C oracle (float32 mirror) on {k} thread(s) "
+                                f"of {cores} host cores"}
+    finally:
+        O.set_threads(1)
+    return out
+
+
+def event_bytes(n, timesteps, spikes, events, state_bytes=STATE_BYTES):
+    """The method's own bytes per launch, proportional to its events: per
+    spike its CSR row bounds (16 B), per event its synapse (8 B) and one
+    accumulate into the target's pending input (8 B), per neuron and timestep
+    the update's state traffic and its raster bit.  This is the event-driven
+    work whichever propagation form runs."""
+    return spikes * 16 + events * 16 + timesteps * n * (state_bytes + 1 / 8)
 
 
 def timed_runs(S, torch, stream, flush, ctx, steps, reps, warm=1):
@@ -393,12 +492,19 @@ def bptt_extra(S, W, torch, stream):
             bf16, src = float(json.load(f)["bf16_tflops"]), "measured bf16 burst"
     except Exception:
         bf16, src = 1900.0, "fallback bf16"
+    # the method's own work of one training step, dense-equivalent: forward
+    # synaptic input 2*B*T*sum(n_in*n_out); spike gradients of the layers above
+    # the first 2*B*T*sum_{l>1}(n_in*n_out); weight gradients as the forward
+    alg = 2 * rows * syn + 2 * rows * sum(a * b for a, b in zip(sizes[1:-1], sizes[2:])) + 2 * rows * syn
     return {"workload": "700-1024-1024-20 LIF, per-synapse delays 1..4, batch 128, 100 steps, "
                         "checkpoint every 10", "synapses": syn, "ms_per_training_step": ms,
-            "roofline": {"bound": "tensor", "achieved": flop / (ms / 1e3) / 1e12, "peak": bf16, "unit": "TFLOP/s",
-                         "frac": flop / (ms / 1e3) / 1e12 / bf16, "peak_source": src,
-                         "kernel": "ff_tc_fwd_kernel + ff_tc_kernel (whole step's tensor work over the step time)",
-                         "tensor_flop_per_step": flop},
+            "roofline": {"bound": "tensor", "achieved": alg / (ms / 1e3) / 1e12, "peak": bf16, "unit": "TFLOP/s",
+                         "frac": alg / (ms / 1e3) / 1e12 / bf16, "peak_source": src,
+                         "kernel": "ff_tc_fwd_kernel + ff_tc_kernel (whole step's work over the step time)",
+                         "algorithmic_flop_per_step": alg,
+                         "executed_tensor_flop_per_step": flop,
+                         "executed_frac": flop / (ms / 1e3) / 1e12 / bf16,
+                         "note": "executed work counts every delay pass, weight part and padded tile"},
             "engine": "tcgen05 BF16 contractions (forward: exact three-part weight split, block-wise FP32 sums)",
             "simt_engine_ms_per_training_step": simt_ms,
             "plain_torch_ms_per_training_step": plain_ms, "speedup_vs_plain_torch": plain_ms / ms}
@@ -547,8 +653,10 @@ def run_reference(args, wl, rank):
         return
     from oracle import oracle as O
     deg = np.bincount(np.asarray(wl["pre"]), minlength=wl["n"]).astype(np.int64)
+    cores = host_cores()
+    O.set_threads(cores)
     base, _, _ = O.run(wl, O.F32, 40)
-    per = 8
+    per = 16
     times, evs = [], []
     for k in range(args.warmup + args.steps):
         st = base.copy()
@@ -558,8 +666,9 @@ def run_reference(args, wl, rank):
         if k >= args.warmup:
             times.append(dt)
             evs.append(int((raster.astype(np.int64) * deg[None, :]).sum()))
+    O.set_threads(1)
     value = sum(evs) / sum(times)
-    sample = f"{per} timesteps (40..{40 + per - 1}) of {wl['name']} per step, single-threaded C oracle"
+    sample = f"{per} timesteps (40..{40 + per - 1}) of {wl['name']} per step, C oracle on {cores} threads"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
@@ -568,7 +677,7 @@ def run_reference(args, wl, rank):
         "config": {"workload": "large-sparse", "neurons": wl["n"], "synapses": int(len(wl["pre"])),
                    "max_delay": 16, "timesteps_per_step": per, "parallelism": "replicas"},
         "timesteps_per_s": per * len(times) / sum(times),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -584,7 +693,13 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the dense, STDP and batched measurements beside the headline")
+    ap.add_argument("--record-traffic", nargs=3, metavar=("CSV", "KERNEL", "WORKLOAD"),
+                    help="write the DRAM traffic of KERNEL on WORKLOAD from an ncu CSV into "
+                         "profiles/dram_traffic.txt and exit")
     args = ap.parse_args()
+    if args.record_traffic:
+        record_traffic(*args.record_traffic)
+        return
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local = int(os.environ.get("LOCAL_RANK", 0))
@@ -676,9 +791,13 @@ def main():
 
     if rank == 0:
         peak, src = peaks()
-        abytes = algorithmic_bytes_pull(n, m, T) if pull else algorithmic_bytes(n, T, spikes, events)
+        # the method's event-proportional bytes; pull also streams every
+        # synapse every step, which is reported beside it
+        abytes = event_bytes(n, T, spikes, events)
+        form_bytes = algorithmic_bytes_pull(n, m, T) if pull else algorithmic_bytes(n, T, spikes, events)
         kernel = "sparse_pull_kernel<SN_F32>" if pull else "sparse_reg_kernel<SN_F32>"
         achieved = abytes / (ms / 1e3) / 1e9
+        traffic, traffic_src = recorded_traffic(kernel, f"large-sparse T={T}")
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True, "scaling": "weak",
@@ -693,9 +812,20 @@ def main():
             "wall_ms_per_step": 1e3 * wall / args.steps,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": src,
-                         "traffic": NCU_TRAFFIC_BYTES.get(kernel) if T == TIMESTEPS else None,
+                         "traffic": traffic, "traffic_source": traffic_src,
                          "kernel": kernel,
-                         "algorithmic_bytes_per_launch": abytes},
+                         "algorithmic_bytes_per_launch": abytes,
+                         "bytes_model": "event-proportional: 16 B per spike (row bounds), 16 B per synaptic "
+                                        "event (synapse + accumulate), 56 B state and a raster bit per "
+                                        "neuron and timestep",
+                         "kernel_bound": ("l2+barrier: the 80 MB synapse store stays in the 129 MB L2; each "
+                                          "timestep streams it from L2 once, then one grid barrier")
+                                         if pull else "l2 atomics: scattered accumulates into the pending-input "
+                                                      "ring, L2-resident",
+                         "form_bytes_per_launch": form_bytes,
+                         "frac_form_bytes": form_bytes / (ms / 1e3) / 1e9 / peak,
+                         "form_bytes_model": "pull: 8 B per synapse every timestep + 40 B state and a raster "
+                                             "bit per neuron and timestep" if pull else "push: as above"},
             "e2e": {"value": e2e_ev_all / e2e_all, "unit": UNIT,
                     "h2d_bytes_per_step": 8 * n,
                     "d2h_bytes_per_step": T * ctx.words * 4 + 32},
@@ -717,9 +847,14 @@ def main():
             line["extra"] = {"large_sparse_other_propagation": alt}
             line["extra"].update(extras(S, W, torch, stream, flush))
         if not args.no_cpu_baseline:
-            ev_s, ts_s, sample = oracle_sample(wl)
-            line["cpu_baseline"] = {"value": ev_s, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                    "sample": sample, "timesteps_per_s": ts_s}
+            samp = oracle_sample(wl)
+            many = samp[max(samp)]
+            line["cpu_baseline"] = {"value": many["value"], "unit": UNIT, "cores": many["cores"],
+                                    "kind": "oracle", "sample": many["sample"],
+                                    "timesteps_per_s": many["timesteps_per_s"],
+                                    "host_cores": host_cores(),
+                                    "single_thread": {"value": samp[1]["value"], "unit": UNIT, "cores": 1,
+                                                      "timesteps_per_s": samp[1]["timesteps_per_s"]}}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

@@ -92,13 +92,25 @@ typedef enum {
                                the forward (saves steps * batch * sum(sizes[1..])
                                floats of device memory)                            */
 
+#define SN_DENSE_SLAB(k) ((uint32_t)(k) << 8)
+                            /* sn_create_dense only: each block owns a slab of
+                               32 * k weight columns, k = 1, 2, 4 or 8, instead
+                               of the narrowest slab whose grid is co-resident
+                               (k = 1 up to about 19,000 neurons).  k changes
+                               only the order of the float additions of each
+                               neuron's synaptic input; it lets a small network
+                               run the wide-slab code of large ones (tests,
+                               tuning).  SN_EUNSUPPORTED if that grid is not
+                               co-resident                                        */
+#define SN_DENSE_SLAB_MASK 0xF00u
+
 #define SN_MAX_DELAY 64     /* largest supported synaptic delay                    */
 
 typedef struct {
     int32_t dtype;          /* sn_dtype                                            */
     int32_t max_delay;      /* D: every synaptic delay lies in 1..D, D <= 64       */
     uint32_t flags;         /* SN_AUTO or one SN_EXEC_* value, optionally with
-                               SN_PROP_PULL                                        */
+                               SN_PROP_PULL or SN_DENSE_SLAB(k)                    */
     int32_t record_steps;   /* spike-raster capacity in steps (a ring); sn_get_spikes
                                can return any of the last record_steps steps; 0
                                means 1                                              */

@@ -34,7 +34,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < os.path.getmtime(SRC):
         tmp = LIB + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-std=c99", "-ffp-contract=off",
-                               "-fno-fast-math", "-fPIC", "-shared", SRC, "-o", tmp, "-lm"])
+                               "-fno-fast-math", "-fopenmp", "-fPIC", "-shared", SRC, "-o", tmp, "-lm"])
         os.replace(tmp, LIB)
     return LIB
 
@@ -69,7 +69,16 @@ def lib():
             _lib.orc_poisson_u32.restype = C.c_uint32
             _lib.orc_splitmix64.argtypes = [C.c_uint64]
             _lib.orc_splitmix64.restype = C.c_uint64
+            _lib.orc_set_threads.argtypes = [C.c_int]
+            _lib.orc_set_threads.restype = C.c_int
     return _lib
+
+
+def set_threads(k: int) -> int:
+    """Threads for the per-neuron loop of each oracle step (1 by default).
+    Each neuron's step depends only on earlier steps and its own state, so
+    the results do not depend on k."""
+    return int(lib().orc_set_threads(int(k)))
 
 
 def splitmix64(x: int) -> int:

@@ -37,7 +37,11 @@
  * External input of (t, j): the explicit events of (t, j) in the order given,
  * then the Poisson source of j (if any), summed into ext starting from 0.
  *
- * Build: gcc -O2 -ffp-contract=off -fPIC -shared (no fused multiply-add).
+ * Build: gcc -O2 -ffp-contract=off -fopenmp -fPIC -shared (no fused
+ * multiply-add).  The per-neuron loop of a step may run on several threads
+ * (orc_set_threads; 1 by default): each neuron's sum, update and spike depend
+ * only on earlier steps and on its own state, so the result is the same bit
+ * for bit on any number of threads.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -102,6 +106,14 @@ uint32_t orc_poisson_u32(uint64_t seed, uint64_t net, uint32_t t, uint32_t j)
 
 /* ---------------------------------------------------------------------- */
 static int g_mode;
+static int g_threads = 1;
+
+/* Threads for the per-neuron loop of each step (k >= 1); returns the count. */
+int orc_set_threads(int k)
+{
+    g_threads = k < 1 ? 1 : k;
+    return g_threads;
+}
 
 static double R(double x)
 {
@@ -248,6 +260,8 @@ int orc_run(const orc_net *net, int64_t t0, int32_t steps,
                 if (u < net->src_rate_u32[k]) ext[j] = R(ext[j] + net->src_amp[k]);
             }
 
+        int overflow = 0;
+#pragma omp parallel for schedule(static) num_threads(g_threads) reduction(| : overflow)
         for (int j = 0; j < n; ++j) {
             /* synaptic input: spikes of t-d reach j at t */
             double acc = 0.0;
@@ -269,7 +283,7 @@ int orc_run(const orc_net *net, int64_t t0, int32_t steps,
             vj = R(vj + ext[j]);
             if (ctrace) ctrace[(size_t)s * n + j] = vj;
             /* integer mode: the integrated state must fit int32 */
-            if (net->mode == ORC_INT && fabs(vj) >= 2147483648.0) status = ORC_EOVERFLOW;
+            if (net->mode == ORC_INT && fabs(vj) >= 2147483648.0) overflow = 1;
             /* threshold (strict), refractory mask, reset */
             int fire = (vj > net->threshold[j]) && (r[j] == 0);
             if (fire) {
@@ -281,6 +295,7 @@ int orc_run(const orc_net *net, int64_t t0, int32_t steps,
             v[j] = vj;
             cur[j] = (uint8_t)fire;
         }
+        if (overflow) status = ORC_EOVERFLOW;
 
         if (net->stdp) {
             for (int j = 0; j < n; ++j) xold[j] = trace[j];

@@ -29,7 +29,8 @@ sn_status check_config(const sn_config *cfg) {
     if (cfg->max_delay < 1 || cfg->max_delay > SN_MAX_DELAY)
         return fail(nullptr, SN_EINVAL, "max_delay must be in 1..64");
     if (cfg->record_steps < 0) return fail(nullptr, SN_EINVAL, "record_steps < 0");
-    if (cfg->flags & ~(SN_EXEC_CTA | SN_EXEC_GRID | SN_PROP_PULL)) return fail(nullptr, SN_EINVAL, "unknown flags");
+    if (cfg->flags & ~(SN_EXEC_CTA | SN_EXEC_GRID | SN_PROP_PULL | SN_DENSE_SLAB_MASK))
+        return fail(nullptr, SN_EINVAL, "unknown flags");
     if ((cfg->flags & SN_EXEC_CTA) && (cfg->flags & SN_EXEC_GRID))
         return fail(nullptr, SN_EINVAL, "SN_EXEC_CTA and SN_EXEC_GRID are exclusive");
     return SN_OK;
@@ -357,6 +358,9 @@ sn_status sn_create_dense(const sn_config *cfg, const sn_neurons *nr, const floa
     const int n = nr->n;
     if (n < 1 || n > 200000) return fail(nullptr, SN_EINVAL, "dense n must be in 1 .. 200000");
     if (delay < 1 || delay > cfg->max_delay) return fail(nullptr, SN_EINVAL, "delay outside 1..max_delay");
+    const int force_cpl = (int)((cfg->flags & SN_DENSE_SLAB_MASK) >> 8);
+    if (force_cpl != 0 && force_cpl != 1 && force_cpl != 2 && force_cpl != 4 && force_cpl != 8)
+        return fail(nullptr, SN_EINVAL, "SN_DENSE_SLAB(k) takes k = 1, 2, 4 or 8");
     const size_t nn = (size_t)n * n;
     for (size_t q = 0; w && q < nn; ++q)
         if (!std::isfinite(w[q]) || std::fabs(w[q]) > 1e9f) return fail(nullptr, SN_EINVAL, "weight not finite");
@@ -379,9 +383,13 @@ sn_status sn_create_dense(const sn_config *cfg, const sn_neurons *nr, const floa
     // executor: column slabs of 32 * cpl columns, one block each, co-resident
     c->block = 256;
     int grid = 0, chunk = 0;
-    cudaError_t e = plan_dense(n, &grid, &chunk);
+    cudaError_t e = plan_dense(n, &grid, &chunk, force_cpl);
     if (e != cudaSuccess) { c->err = std::string("dense executor: ") + cudaGetErrorString(e); return bail(SN_ECUDA); }
-    if (grid < 1) { c->err = "dense network too large for a co-resident grid"; return bail(SN_EUNSUPPORTED); }
+    if (grid < 1) {
+        c->err = force_cpl ? "the forced column slab gives no co-resident grid for this n"
+                           : "dense network too large for a co-resident grid";
+        return bail(SN_EUNSUPPORTED);
+    }
     c->grid = grid;
     c->chunk = chunk;
     c->S = 1;

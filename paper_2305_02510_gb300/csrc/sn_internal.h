@@ -202,7 +202,7 @@ cudaError_t max_grid_sparse(int dtype, int stdp, int block, int *grid);
 cudaError_t max_grid_sparse_reg(int *grid);
 cudaError_t launch_sparse_reg(const NetArgs &a, int dtype, int grid, cudaStream_t s);
 constexpr int kSparseRegBlock = 512;
-cudaError_t plan_dense(int n, int *grid, int *chunk);
+cudaError_t plan_dense(int n, int *grid, int *chunk, int force_cpl = 0);
 // Pull propagation (sn_pull.cu).  plan_pull sets *grid = 0 when the network
 // does not fit the executor (a window of max_delay spike rows above a block's
 // shared memory, or more than one neuron per thread).  Synapse words of the

@@ -805,8 +805,9 @@ cudaError_t launch_dense(const NetArgs &a, int grid, int block, cudaStream_t s) 
 
 // Executor plan of a dense network: the smallest columns-per-lane (1, 2, 4,
 // 8) whose grid of ceil(n / (32 * cpl)) blocks is co-resident; a network of
-// at most 128 neurons runs as one block (no grid barrier).
-cudaError_t plan_dense(int n, int *grid, int *chunk) {
+// at most 128 neurons runs as one block (no grid barrier).  force_cpl (1, 2,
+// 4 or 8; 0 = choose) takes that slab width if its grid is co-resident.
+cudaError_t plan_dense(int n, int *grid, int *chunk, int force_cpl) {
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -814,7 +815,7 @@ cudaError_t plan_dense(int n, int *grid, int *chunk) {
     if (e != cudaSuccess) return e;
     const int words = (n + 31) / 32;
     for (int cpl : {1, 2, 4, 8}) {
-        if (n <= 128 && 32 * cpl < n) continue;
+        if (force_cpl ? cpl != force_cpl : (n <= 128 && 32 * cpl < n)) continue;
         const size_t smem = dense_smem(words, cpl);
         int per = 1 << 30;
         for (int v = 0; v < 3; ++v) {

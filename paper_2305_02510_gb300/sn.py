@@ -21,6 +21,12 @@ SN_OK, SN_EINVAL, SN_ENOMEM, SN_ECUDA, SN_ESTATE, SN_ETIMEOUT, SN_EUNSUPPORTED, 
 SN_F32, SN_I32 = 0, 1
 SN_AUTO, SN_EXEC_CTA, SN_EXEC_GRID, SN_PROP_PULL, SN_FF_RECOMPUTE = 0, 1, 2, 4, 8
 SN_PUSH, SN_PULL = 0, 1
+
+
+def SN_DENSE_SLAB(k: int) -> int:
+    """sn_create_dense flag: column slabs of 32 * k columns per block (k = 1, 2, 4, 8)."""
+    return int(k) << 8
+
 SN_FF_AUTO, SN_FF_SIMT, SN_FF_TENSOR = 0, 1, 2
 _NAMES = ["SN_OK", "SN_EINVAL", "SN_ENOMEM", "SN_ECUDA", "SN_ESTATE", "SN_ETIMEOUT",
           "SN_EUNSUPPORTED", "SN_EOVERFLOW"]

@@ -197,14 +197,53 @@ def huge_dense(n: int = 100_000, seed: int = SEED_BASE + 7, steps: int = 1000):
     return wl
 
 
+def dense_integer_valued(n: int, seed: int = SEED_BASE + 8, steps: int = 1000, on_device: bool = False):
+    """All-to-all network whose float32 weights are the integers -1, 0, +1
+    (each nonzero with probability 500 / n, W_ii = 0), theta 8, leak 1,
+    reset 0, refractory 1, delay 1; Poisson 0.02/step into every neuron at
+    amplitude 9.  Every partial sum of a step's synaptic input is an integer
+    far below 2^24, so float32 arithmetic is exact in any order of addition
+    and a run must equal the oracle bit for bit whatever the kernel's blocking.
+    About 15% of the neurons fire per step, most of them through synaptic
+    input.  on_device: the weights are drawn on the device by
+    dense_weights_on_device (for sizes beyond a host copy)."""
+    q = min(0.5, 500.0 / n)
+    wl = _base(n, "f32", 8.0, 1.0, 0.0, 1, 1, steps)
+    if on_device:
+        wl.update(dense_w_device=dict(seed=int(seed), int_q=q), dense_delay=1)
+    else:
+        rng = _rng(seed)
+        w = np.empty((n, n), dtype=np.float32)
+        rows = max(1, (1 << 24) // n)
+        for r0 in range(0, n, rows):
+            r1 = min(n, r0 + rows)
+            u = rng.random((r1 - r0, n))
+            w[r0:r1] = (u < q).astype(np.float32) - (u >= 1.0 - q).astype(np.float32)
+        np.fill_diagonal(w, 0.0)
+        wl.update(dense_w=w, dense_delay=1)
+    wl["poisson"] = _poisson(np.arange(n), 0.02, 9.0, seed * 7 + 3)
+    wl["name"] = f"dense-integer-valued-n{n}"
+    return wl
+
+
 def dense_weights_on_device(wl, torch, device="cuda"):
-    """Device tensor [n, n] float32 with the weights of a huge_dense workload,
-    drawn by a seeded torch generator on the device (W_ii = 0)."""
+    """Device tensor [n, n] float32 with the weights of a huge_dense (or an
+    on-device dense_integer_valued) workload, drawn by a seeded torch
+    generator on the device (W_ii = 0)."""
     spec, n = wl["dense_w_device"], wl["n"]
     g = torch.Generator(device=device)
     g.manual_seed(spec["seed"])
     w = torch.empty((n, n), dtype=torch.float32, device=device)
-    w.normal_(0.0, spec["sigma"], generator=g)
+    if "int_q" in spec:
+        # dense_integer_valued: -1, 0, +1 with P(+1) = P(-1) = q, row block by row block
+        q = float(spec["int_q"])
+        rows = max(1, (1 << 28) // n)
+        for r0 in range(0, n, rows):
+            blk = w[r0:r0 + rows]
+            blk.uniform_(0.0, 1.0, generator=g)
+            blk.copy_((blk < q).float() - (blk >= 1.0 - q).float())
+    else:
+        w.normal_(0.0, spec["sigma"], generator=g)
     w.fill_diagonal_(0.0)
     return w
 

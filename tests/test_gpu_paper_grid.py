@@ -67,3 +67,27 @@ def test_paper_grid_exact(n, p, how):
     deg = np.full(n, n) if how == "dense" else np.bincount(wl["pre"], minlength=n)
     assert ev == int((want.astype(np.int64) * deg).sum())
     assert want[-1].sum() > 0
+
+
+_BIG = {}
+
+
+@pytest.mark.parametrize("how", ["dense", "push", "pull"])
+@pytest.mark.parametrize("p", [0.25, 1.0])
+def test_paper_grid_n10000_exact(p, how):
+    """The largest networks of Table 2 (N = 10,000: 25M and 100M synapses),
+    which the benchmark times beside the paper's numbers: 12 steps (two input
+    rounds; from step 2 on every neuron fires every step), bit for bit."""
+    n, steps = 10_000, 12
+    if p not in _BIG:
+        wl = W.paper_grid(n, p, steps=steps)
+        st, want, _ = O.run(wl, O.F32, steps)
+        _BIG[p] = (wl, st, want)
+    wl, st, want = _BIG[p]
+    raster, v, r, ev = run(wl, steps, how)
+    assert np.array_equal(raster, want), f"first differing step {np.nonzero((raster != want).any(1))[0][:1]}"
+    assert np.array_equal(np.asarray(v, np.float64), st.v)
+    assert np.array_equal(np.asarray(r), st.r)
+    deg = np.full(n, n) if how == "dense" else np.bincount(wl["pre"], minlength=n)
+    assert ev == int((want.astype(np.int64) * deg).sum())
+    assert want[-1].sum() == n

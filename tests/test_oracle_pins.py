@@ -488,3 +488,48 @@ def test_integer_overflow_is_detected():
     assert st.v[0] == 256 * (2 ** 23 - 1) and raster.sum() == 0
     with pytest.raises(RuntimeError):
         O.run(wl, O.INT, 257)
+
+
+@pytest.mark.parametrize("kind", ["sparse-float", "sparse-int", "dense-stdp"])
+def test_threads_do_not_change_results(kind):
+    """The per-neuron loop on several threads (the CPU baseline's
+    multi-threaded timing) gives the single-threaded run bit for bit."""
+    if kind == "sparse-float":
+        wl = W.large_sparse(integer=False, n=3000, k=40, steps=60)
+    elif kind == "sparse-int":
+        wl = W.large_sparse(integer=True, n=3000, k=40, steps=60)
+    else:
+        wl = W.large_dense(n=300, stdp=True, steps=60)
+    mode = O.INT if wl["dtype"] == "i32" else O.F32
+    out = []
+    for k in (1, 4):
+        O.set_threads(k)
+        try:
+            st, raster, _ = O.run(wl, mode, 60, record_v=True)
+        finally:
+            O.set_threads(1)
+        out.append((st, raster))
+    (a, ra), (b, rb) = out
+    assert ra.sum() > 0 and np.array_equal(ra, rb)
+    assert np.array_equal(a.v, b.v) and np.array_equal(a.r, b.r)
+    assert np.array_equal(a.ctrace, b.ctrace) and np.array_equal(a.w, b.w)
+
+
+def test_integer_overflow_is_detected_on_threads():
+    """As above, with the growing neuron in the middle of a 64-neuron loop
+    split over three threads: steps 0..255 stay in range, step 256 is an
+    error."""
+    n, T = 64, 300
+    wl = W._base(n, "i32", 2.0 ** 31, 0, 0, 0, 1, T)
+    wl.update(pre=np.zeros(0, np.int32), post=np.zeros(0, np.int32), weight=np.zeros(0),
+              delay=np.zeros(0, np.int32))
+    wl["events"] = dict(step=np.arange(T, dtype=np.int32), neuron=np.full(T, 37, np.int32),
+                        value=np.full(T, 2.0 ** 23 - 1))
+    O.set_threads(3)
+    try:
+        st, raster, _ = O.run(wl, O.INT, 256)
+        assert st.v[37] == 256 * (2 ** 23 - 1) and raster.sum() == 0
+        with pytest.raises(RuntimeError):
+            O.run(wl, O.INT, 257)
+    finally:
+        O.set_threads(1)
