@@ -235,10 +235,14 @@ sn_status sn_set_input(sn_ctx *ctx, int64_t nev, const int32_t *step,
 sn_status sn_set_poisson(sn_ctx *ctx, int32_t nsrc, const int32_t *neuron,
                          const float *rate, const float *amplitude, uint64_t seed);
 
-/* sn_set_poisson with the stream's network index given explicitly: the
- * sources of a single network use key = SplitMix64(seed ^ SplitMix64(net)),
- * so a single context can reproduce network `net` of a batched context.
- * Single networks only (SN_ESTATE otherwise). */
+/* sn_set_poisson with the stream's network index given explicitly.  A single
+ * network uses key = SplitMix64(seed ^ SplitMix64(net)), so a single context
+ * can reproduce network `net` of a batched context.  A batched or shared
+ * dense context takes `net` as the global index of its first network or
+ * train: network (train) b uses net + b.  A context holding networks
+ * [k, k + nets) of a larger family (one shard of it, on one GPU of several)
+ * then draws exactly the input those networks get in a context holding the
+ * whole family.  Feedforward contexts: SN_ESTATE. */
 sn_status sn_set_poisson_stream(sn_ctx *ctx, int32_t nsrc, const int32_t *neuron, const float *rate,
                                 const float *amplitude, uint64_t seed, uint64_t net);
 

@@ -472,8 +472,8 @@ sn_status sn_set_poisson(sn_ctx *c, int32_t nsrc, const int32_t *neuron, const f
     if (c->kind != KIND_SPARSE && c->kind != KIND_DENSE && c->kind != KIND_BATCH && c->kind != KIND_SHARED_I8)
         return fail(c, SN_ESTATE, "wrong context kind");
     if (nsrc < 0 || (nsrc > 0 && (!neuron || !rate || !amp))) return fail(c, SN_EINVAL, "bad source arrays");
-    if (c->kind == KIND_BATCH) return batch_set_poisson(c, nsrc, neuron, rate, amp, seed);
-    if (c->kind == KIND_SHARED_I8) return shared_set_poisson(c, nsrc, neuron, rate, amp, seed);
+    if (c->kind == KIND_BATCH) return batch_set_poisson(c, nsrc, neuron, rate, amp, seed, 0);
+    if (c->kind == KIND_SHARED_I8) return shared_set_poisson(c, nsrc, neuron, rate, amp, seed, 0);
     const int n = c->n;
     std::vector<unsigned> thr(n, 0u);
     std::vector<float> af(n, 0.0f);
@@ -502,7 +502,12 @@ sn_status sn_set_poisson(sn_ctx *c, int32_t nsrc, const int32_t *neuron, const f
 sn_status sn_set_poisson_stream(sn_ctx *c, int32_t nsrc, const int32_t *neuron, const float *rate,
                                 const float *amp, uint64_t seed, uint64_t net) {
     if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
-    if (c->kind != KIND_SPARSE && c->kind != KIND_DENSE) return fail(c, SN_ESTATE, "single networks only");
+    if (c->kind == KIND_BATCH || c->kind == KIND_SHARED_I8) {
+        if (nsrc < 0 || (nsrc > 0 && (!neuron || !rate || !amp))) return fail(c, SN_EINVAL, "bad source arrays");
+        return c->kind == KIND_BATCH ? batch_set_poisson(c, nsrc, neuron, rate, amp, seed, net)
+                                     : shared_set_poisson(c, nsrc, neuron, rate, amp, seed, net);
+    }
+    if (c->kind != KIND_SPARSE && c->kind != KIND_DENSE) return fail(c, SN_ESTATE, "wrong context kind");
     sn_status s = sn_set_poisson(c, nsrc, neuron, rate, amp, seed);
     if (s) return s;
     c->pkey = host_splitmix64(seed ^ host_splitmix64(net));

@@ -101,7 +101,7 @@ static sn_status batch_size_grid(sn_ctx *c) {
 }
 
 sn_status batch_set_poisson(sn_ctx *c, int32_t nsrc, const int32_t *neuron, const float *rate,
-                            const float *amp, uint64_t seed) {
+                            const float *amp, uint64_t seed, uint64_t net0) {
     const int n = c->n;
     std::vector<unsigned> thr(n, 0u);
     std::vector<float> af(n, 0.0f);
@@ -120,7 +120,7 @@ sn_status batch_set_poisson(sn_ctx *c, int32_t nsrc, const int32_t *neuron, cons
         ai[j] = (int)amp[k];
     }
     std::vector<unsigned long long> keys(c->nets);
-    for (int b = 0; b < c->nets; ++b) keys[b] = host_splitmix64(seed ^ host_splitmix64((unsigned long long)b));
+    for (int b = 0; b < c->nets; ++b) keys[b] = host_splitmix64(seed ^ host_splitmix64(net0 + (unsigned long long)b));
     if (sn_status q = quiesce(c)) return q;   // a queued run may read the old sources
     SN_CUDA(c, cudaMemcpy(c->prate, thr.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
     SN_CUDA(c, cudaMemcpy(c->pamp, c->dtype == SN_F32 ? (const void *)af.data() : (const void *)ai.data(),

@@ -187,9 +187,9 @@ sn_status sparse_autotune(sn_ctx *c, int trial_steps, float *best_ms);
 sn_status shared_run(sn_ctx *c, int steps);
 sn_status shared_get_state(sn_ctx *c, void *v, int32_t *refr, int32_t on_device);
 sn_status shared_set_poisson(sn_ctx *c, int32_t nsrc, const int32_t *neuron, const float *rate,
-                             const float *amp, uint64_t seed);
+                             const float *amp, uint64_t seed, uint64_t net0);
 inline long long state_elems(const sn_ctx *c) { return c->kind == KIND_SHARED_I8 ? (long long)c->sh_B * c->n : c->n; }
 sn_status batch_set_poisson(sn_ctx *c, int32_t nsrc, const int32_t *neuron, const float *rate,
-                            const float *amp, uint64_t seed);
+                            const float *amp, uint64_t seed, uint64_t net0);
 
 }  // namespace sn

@@ -78,7 +78,7 @@ sn_status shared_get_state(sn_ctx *c, void *v, int32_t *refr, int32_t on_device)
 }
 
 sn_status shared_set_poisson(sn_ctx *c, int32_t nsrc, const int32_t *neuron, const float *rate,
-                             const float *amp, uint64_t seed) {
+                             const float *amp, uint64_t seed, uint64_t net0) {
     const int n = c->n;
     std::vector<unsigned> thr(n, 0u);
     std::vector<int> ai(n, 0);
@@ -94,7 +94,7 @@ sn_status shared_set_poisson(sn_ctx *c, int32_t nsrc, const int32_t *neuron, con
         ai[j] = (int)amp[k];
     }
     std::vector<unsigned long long> keys(c->sh_B);
-    for (int b = 0; b < c->sh_B; ++b) keys[b] = host_splitmix64(seed ^ host_splitmix64((unsigned long long)b));
+    for (int b = 0; b < c->sh_B; ++b) keys[b] = host_splitmix64(seed ^ host_splitmix64(net0 + (unsigned long long)b));
     if (sn_status q = quiesce(c)) return q;   // a queued run may read the old sources
     SN_CUDA(c, cudaMemcpy(c->prate, thr.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
     SN_CUDA(c, cudaMemcpy(c->pamp, ai.data(), (size_t)n * 4, cudaMemcpyHostToDevice));

@@ -314,13 +314,18 @@ def sn_create_shared_dense_i8(threshold, leak, reset, refractory, w, trains, *, 
     return ctx
 
 
-def from_shared_workload(wl, *, record_steps=None, stream=None) -> Ctx:
+def from_shared_workload(wl, *, record_steps=None, stream=None, first_train=0, trains=None) -> Ctx:
+    """Shared dense context for a shared_dense_i8 workload.  first_train and
+    trains select the trains [first_train, first_train + trains) of the
+    workload's family (one shard of it); their Poisson streams keep their
+    global train indices."""
     rec = wl["steps"] if record_steps is None else record_steps
+    B = wl["batch"] if trains is None else int(trains)
     ctx = sn_create_shared_dense_i8(wl["threshold"], wl["leak"], wl["reset"], wl["refractory"],
-                                    wl["dense_w_i8"], wl["batch"], record_steps=rec, stream=stream)
+                                    wl["dense_w_i8"], B, record_steps=rec, stream=stream)
     po = wl["poisson"]
     if len(po["neuron"]):
-        sn_set_poisson(ctx, po["neuron"], po["rate"], po["amplitude"], po["seed"])
+        sn_set_poisson_stream(ctx, po["neuron"], po["rate"], po["amplitude"], po["seed"], int(first_train))
     return ctx
 
 
@@ -664,18 +669,21 @@ def from_workload(wl, *, record_steps=None, flags=SN_AUTO, stream=None, w_device
     return ctx
 
 
-def from_batch_workloads(nets, *, record_steps=None, stream=None) -> Ctx:
+def from_batch_workloads(nets, *, record_steps=None, stream=None, first=0) -> Ctx:
     """Batched context for a list of workload dicts (all sparse, same dtype);
-    network b of the list is stream b of the batch's Poisson input, whose
-    seed is taken from the first network."""
+    network b of the list is stream first + b of the batch's Poisson input
+    (first: the global index of the list's first network when the list is
+    one shard of a larger family), whose seed is taken from the first
+    network."""
     rec = nets[0]["steps"] if record_steps is None else record_steps
     D = max(int(w["max_delay"]) for w in nets)
     ctx = sn_create_batch(nets, dtype=nets[0]["dtype"], max_delay=D, record_steps=rec, stream=stream)
     off = np.cumsum([0] + [w["n"] for w in nets])
     nj = [np.asarray(w["poisson"]["neuron"], np.int64) + off[b] for b, w in enumerate(nets)]
     if sum(x.size for x in nj):
-        sn_set_poisson(ctx, np.concatenate(nj), np.concatenate([w["poisson"]["rate"] for w in nets]),
-                       np.concatenate([w["poisson"]["amplitude"] for w in nets]), nets[0]["poisson"]["seed"])
+        sn_set_poisson_stream(ctx, np.concatenate(nj), np.concatenate([w["poisson"]["rate"] for w in nets]),
+                              np.concatenate([w["poisson"]["amplitude"] for w in nets]),
+                              nets[0]["poisson"]["seed"], int(first))
     evs = [(np.asarray(w["events"]["step"]), np.asarray(w["events"]["neuron"]) + off[b],
             np.asarray(w["events"]["value"])) for b, w in enumerate(nets)]
     if sum(e[0].size for e in evs):
