@@ -91,7 +91,7 @@ def record_traffic(csv_path, kernel, workload, launches_per_unit=1):
     with open(csv_path) as f:
         lines = [ln for ln in f if ln.startswith('"')]
     for row in csv.DictReader(lines):
-        if not row.get("Kernel Name", "").startswith(kernel.split("<")[0]):
+        if kernel.split("<")[0] + "<" not in row.get("Kernel Name", ""):
             continue
         if row.get("Metric Name") not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
             continue

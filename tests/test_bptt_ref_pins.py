@@ -97,3 +97,29 @@ def test_leak_derivative_rule():
     assert torch.allclose(out.detach(), torch.tensor([0.25, 0.0, 0.0, -0.15, 0.0], dtype=torch.float64))
     out.sum().backward()
     assert v.grad.tolist() == [1.0, 0.0, 0.0, 1.0, 0.0]
+
+
+def test_float32_itself_exceeds_the_state_bound_at_full_size():
+    """The reading behind the full-size BPTT state tolerance: over the 100
+    integrated steps of the 700-1024-1024-20, batch-128 network, a plain
+    float32 evaluation of the reference (same spikes as float64) already
+    deviates from float64 by more than 1e-5 * max(|V|, theta) in the first
+    hidden layer (about 1.09 of it), so no float32 evaluation can be held to
+    the bound itself; the kernels are held to a multiple of this level."""
+    task = W.bptt_task()
+    T, k = task["steps"], task["checkpoint_every"]
+    ws = [torch.tensor(w, dtype=torch.float64) for w in task["w"]]
+    _, sp, pre = R.forward(task, ws, record=True)
+    given = [[sp[l + 1][t].float() for t in range(T)] for l in range(len(ws))]
+    w32 = [torch.tensor(w, dtype=torch.float32) for w in task["w"]]
+    _, _, pre32 = R.forward(task, w32, dtype=torch.float32, given=given, record=True)
+    th = task["threshold"]
+    u = torch.stack([pre[0][t] for t in range(T)]).numpy()
+    s = torch.stack([sp[1][t] for t in range(T)]).numpy().astype(bool)
+    v = np.where(s, task["reset"], u)[k - 1::k]
+    v32 = np.where(s, task["reset"], torch.stack([pre32[0][t] for t in range(T)]).double().numpy())[k - 1::k]
+    ratio = np.abs(v32 - v) / (1e-5 * np.maximum(np.abs(v), th))
+    assert ratio.max() > 1.0, ratio.max()
+    # almost all states are well inside it: the excess is float32 rounding at
+    # the largest sums, not a wrong term
+    assert np.quantile(ratio, 0.999) < 0.5

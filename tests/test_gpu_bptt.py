@@ -204,11 +204,15 @@ def test_bptt_full_size_teacher_forced(engine):
         worst = float((np.abs(ck[l + 1] - v) / tol).max())
         assert worst <= max(1.0, 2.0 * level), (l, worst, level)
         if engine == "simt":
-            # the SIMT engine also meets the plain bound 1e-5 * max(|V|, theta)
-            # with no absolute term: the wider rule above is needed only by the
-            # tensor-core forward's blocked FP32 sums
+            # the SIMT engine (the simulator's own FP32 order) against the
+            # plain bound 1e-5 * max(|V|, theta), no absolute term: within
+            # 1.25x of what plain float32 arithmetic reaches (layer 1 of this
+            # network: about 1.09 of the bound; tests/test_bptt_ref_pins.py pins
+            # that float32 itself exceeds it here)
             plain = 1e-5 * np.maximum(np.abs(v), th)
-            assert np.all(np.abs(ck[l + 1] - v) <= plain), (l, float((np.abs(ck[l + 1] - v) / plain).max()))
+            lvl = float((np.abs(v32 - v) / plain).max())
+            got = float((np.abs(ck[l + 1] - v) / plain).max())
+            assert got <= max(1.0, 1.25 * lvl), (l, got, lvl)
     assert spikes[L].sum() > 0
     assert np.array_equal(counts, ref_counts.detach().numpy())
     ref_loss = R.loss_fn(ref_counts, task["labels"])

@@ -110,12 +110,16 @@ def test_huge_dense_integer_valued_long_launch_bit_exact():
 
 def test_huge_dense_float_long_launch_sampled():
     """The benchmark's 100,000-neuron N(0, sigma) network, one 200-step
-    launch, sampled neurons advanced by the float64 oracle from the kernel's
-    spikes of the step before.  A sampled spike may differ only where the
-    oracle's compared state lies within 1e-4 * theta of theta (that neuron's
-    own trajectory then leaves the kernel's and it is dropped from the
-    comparison); the others must spike as the kernel does every step and end
-    within 1e-5 * max(|V|, theta) of the kernel's state."""
+    launch.  The sampled neurons are advanced by the oracle from the kernel's
+    spikes of the step before, in float64 and in the float32 mirror.  A
+    sampled spike may differ from float64's only where the oracle's compared
+    state lies within 1e-4 * theta of theta (that neuron's trajectory then
+    leaves the kernel's and it is dropped).  At the end the kernel's states
+    must lie within max(1, 2 x the mirror's own level) of 1e-5 * max(|V|,
+    theta) of float64's: over 200 free-running steps of ~12,500-term sums the
+    float32 mirror itself drifts past the plain bound (pinned on the CPU in
+    tests/test_oracle_pins.py), so the kernel is held to what float32
+    arithmetic reaches."""
     n, steps = 100_000, 200
     wl = W.huge_dense(n=n, steps=steps)
     w, raster, v, r = long_launch(wl, steps)
@@ -124,14 +128,16 @@ def test_huge_dense_float_long_launch_sampled():
     del w
     torch.cuda.empty_cache()
     th = np.asarray(np.float32(wl["threshold"]), np.float64)[J]
-    vJ = np.zeros(J.size)
-    rJ = np.zeros(J.size, np.int32)
+    v64, v32 = np.zeros(J.size), np.zeros(J.size)
+    r64, r32 = np.zeros(J.size, np.int32), np.zeros(J.size, np.int32)
     live = np.ones(J.size, bool)
     first = None
     for t in range(steps):
         spikers = np.nonzero(raster[t - 1])[0] if t > 0 else np.zeros(0, np.int64)
-        s, vJ, rJ, ct = compare.sampled_dense_step(wl, t, J, vJ, rJ, spikers, wJ[spikers], mode=O.F64)
-        diff = live & (raster[t, J] != s)
+        cols = wJ[spikers]
+        s64, v64, r64, ct = compare.sampled_dense_step(wl, t, J, v64, r64, spikers, cols, mode=O.F64)
+        s32, v32, r32, _ = compare.sampled_dense_step(wl, t, J, v32, r32, spikers, cols, mode=O.F32)
+        diff = live & ((raster[t, J] != s64) | (s32 != s64))
         if diff.any():
             gap = np.abs(ct[diff] - th[diff])
             assert np.all(gap < compare.NEAR * np.abs(th[diff])), \
@@ -139,10 +145,11 @@ def test_huge_dense_float_long_launch_sampled():
             first = first if first is not None else (t, int(J[diff][0]))
             live &= ~diff
     assert live.sum() >= 0.95 * J.size, f"{int((~live).sum())} of {J.size} dropped (first at {first})"
-    vv = np.asarray(v, np.float64)[J]
-    ratio = np.abs(vv - vJ) / (compare.RTOL * np.maximum(np.abs(vJ), th))
-    assert ratio[live].max() <= 1.0, f"state deviation {ratio[live].max():.3f} of the tolerance"
-    assert np.array_equal(np.asarray(r)[J][live], rJ[live])
+    tol = compare.RTOL * np.maximum(np.abs(v64), th)
+    kernel = (np.abs(np.asarray(v, np.float64)[J] - v64) / tol)[live].max()
+    mirror = (np.abs(v32 - v64) / tol)[live].max()
+    assert kernel <= max(1.0, 2.0 * mirror), (float(kernel), float(mirror))
+    assert np.array_equal(np.asarray(r)[J][live], r64[live])
 
 
 def test_set_weights_round_trip():
