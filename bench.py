@@ -818,8 +818,9 @@ def main():
                          "bytes_model": "event-proportional: 16 B per spike (row bounds), 16 B per synaptic "
                                         "event (synapse + accumulate), 56 B state and a raster bit per "
                                         "neuron and timestep",
-                         "kernel_bound": ("l2+barrier: the 80 MB synapse store stays in the 129 MB L2; each "
-                                          "timestep streams it from L2 once, then one grid barrier")
+                         "kernel_bound": ("l2+barrier: the pull store of incoming synapses (98 MB) stays in "
+                                          "the 129 MB L2; each timestep streams it from L2 once, then one grid "
+                                          "barrier")
                                          if pull else "l2 atomics: scattered accumulates into the pending-input "
                                                       "ring, L2-resident",
                          "form_bytes_per_launch": form_bytes,
