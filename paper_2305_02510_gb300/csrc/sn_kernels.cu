@@ -711,9 +711,14 @@ __global__ void __launch_bounds__(kBlock, CPL <= 2 ? 4 : 3) dense_kernel(NetArgs
 #pragma unroll
                             for (int h = 0; h < 2; ++h) {
                                 const int q = q0 + lane + 32 * h;
-                                if (act[u] && q < cnt)
-                                    a.W[(size_t)i * n + list[q]] =
-                                        clampf(__fadd_rn(val[u][h], dw[u]), a.wmin, a.wmax);
+                                if (act[u] && q < cnt) {
+                                    // a weight whose update rounds back to itself (an old
+                                    // pre-neuron's trace has decayed below its half ulp) is
+                                    // not written: same bits, no dirty sector
+                                    const float nv = clampf(__fadd_rn(val[u][h], dw[u]), a.wmin, a.wmax);
+                                    if (__float_as_uint(nv) != __float_as_uint(val[u][h]))
+                                        a.W[(size_t)i * n + list[q]] = nv;
+                                }
                             }
                         }
                     }
