@@ -78,17 +78,32 @@ __device__ __forceinline__ bool batch_finish(const BatchArgs &a, const BatchNet<
 // Neurons whose loads one thread issues together in the update phase.
 constexpr int kUpdAhead = 8;
 
-// Push of spiker i (local) of network nb: lanes stride the CSR row.
+// Synapses of a row whose loads a lane issues together before their adds.
+constexpr int kPushAhead = 8;
+
+// Push of spiker i (local) of network nb: lanes stride the CSR row, each
+// lane loading kPushAhead synapses before it issues their accumulates (the
+// accumulates are fixed-point, so their order does not matter).
 template <int MODE>
 __device__ __forceinline__ long long batch_push(const BatchArgs &a, const BatchNet<MODE> &nb, int i, int cur,
                                                 typename Tr<MODE>::A *ring, int lane) {
     const long long beg = a.rowptr[nb.off + i], end = a.rowptr[nb.off + i + 1];
-    for (long long p = beg + lane; p < end; p += 32) {
-        const unsigned e = __ldg(a.sidx + p);
-        const int post = (int)(e & 0xFFFu);
-        int sl = cur + (int)(e >> 12) + 1;
-        if (sl >= a.D1) sl -= a.D1;
-        atomicAdd(ring + (size_t)sl * nb.n + post, Tr<MODE>::to_acc(__ldg(a.sw + p)));
+    for (long long p0 = beg + lane; p0 < end; p0 += 32 * kPushAhead) {
+        unsigned e[kPushAhead], w[kPushAhead];
+#pragma unroll
+        for (int u = 0; u < kPushAhead; ++u) {
+            const long long p = p0 + 32 * u;
+            e[u] = p < end ? __ldg(a.sidx + p) : 0u;
+            w[u] = p < end ? __ldg(a.sw + p) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kPushAhead; ++u) {
+            if (p0 + 32 * u >= end) break;
+            const int post = (int)(e[u] & 0xFFFu);
+            int sl = cur + (int)(e[u] >> 12) + 1;
+            if (sl >= a.D1) sl -= a.D1;
+            atomicAdd(ring + (size_t)sl * nb.n + post, Tr<MODE>::to_acc(w[u]));
+        }
     }
     return end - beg;
 }
