@@ -160,6 +160,41 @@ sn_status sn_create(const sn_config *cfg, const sn_neurons *neurons,
 sn_status sn_create_axonal(const sn_config *cfg, const sn_neurons *neurons, const sn_synapses *synapses,
                            const int32_t *axonal_delay, sn_ctx **out);
 
+/* One shard of a sparse network run on several GPUs (Section 4 motivates
+ * networks larger than one device; one context per GPU, one rank per
+ * context).  The network is given whole (all n neurons' parameters, every
+ * synapse); this context simulates the neurons [first, first + count) with
+ * pull propagation and keeps every neuron's spike bits of the last max_delay
+ * steps.  first is a multiple of 32 and count a multiple of 32 unless the
+ * shard ends at n, so that every 32-neuron raster word belongs to one shard.
+ * The shards exchange spike rows: sn_run may advance at most
+ * steps_per_exchange steps (the network's smallest synaptic delay: a spike
+ * of step t reaches no neuron before t + that delay), and only once the
+ * other shards' spikes of every earlier step have been put in with
+ * sn_shard_put_spikes (SN_ESTATE otherwise).  A run of all shards with their
+ * rows exchanged after every sn_run equals the single context's run bit for
+ * bit.  Inputs (sn_set_input, sn_set_poisson) take global neuron indices;
+ * sn_get_state returns n values of which the shard's own are meaningful;
+ * sn_get_spikes returns whole rows (own words from this shard, the others as
+ * put in); the counters count this shard's spikes and their synaptic events.
+ * STDP, push propagation, sn_set_weights, sn_autotune and checkpoints are
+ * not available for shards (SN_EUNSUPPORTED / SN_ESTATE). */
+sn_status sn_create_shard(const sn_config *cfg, const sn_neurons *neurons, const sn_synapses *synapses,
+                          int32_t first, int32_t count, sn_ctx **out);
+
+/* The shard's range and the largest number of steps one sn_run may advance
+ * between exchanges (any pointer may be NULL); SN_ESTATE for a context that
+ * is not a shard. */
+sn_status sn_shard_info(const sn_ctx *ctx, int32_t *first, int32_t *count, int32_t *steps_per_exchange);
+
+/* The other shards' spikes of steps [t0, t1): rows of ceil(n/32) words of the
+ * whole network (the words of this shard's own neurons are ignored), into
+ * the history and the raster.  t0 must be the first step whose rows are not
+ * in yet, t1 at most the current step, t1 - t0 <= max_delay.  on_device = 1:
+ * `bits` is a device pointer read on the context's stream; 0: host memory,
+ * copied before the call returns. */
+sn_status sn_shard_put_spikes(sn_ctx *ctx, int64_t t0, int64_t t1, const uint32_t *bits, int32_t on_device);
+
 /* Create an all-to-all network from a dense row-major n x n weight matrix
  * (w[i*n + j] is the weight of i -> j, Section 2.1).  Every synapse has delay
  * `delay` (1..cfg->max_delay).  The diagonal takes part in propagation like

@@ -135,7 +135,8 @@ sn_status build_pull_store(sn_ctx *c) {
 sn_status select_pull(sn_ctx *c) {
     if (c->stdp) return fail(c, SN_EUNSUPPORTED, "STDP runs on push propagation");
     if (c->pull_grid == 0) {
-        cudaError_t e = plan_pull(c->n, c->D, c->m, &c->pull_grid, &c->pull_chunk, &c->pull_rows, &c->pull_smem);
+        const int own = c->shard_end ? (c->shard_end - c->shard_first + 31) / 32 : -1;
+        cudaError_t e = plan_pull(c->n, c->D, c->m, &c->pull_grid, &c->pull_chunk, &c->pull_rows, &c->pull_smem, own);
         if (e != cudaSuccess) return cuda_fail(c, e, "pull executor");
         if (c->pull_grid == 0)
             return fail(c, SN_EUNSUPPORTED,
@@ -316,6 +317,75 @@ sn_status sn_create(const sn_config *cfg, const sn_neurons *nr, const sn_synapse
     if ((s = size_sparse_executor(c))) return bail(s);
     if ((cfg->flags & SN_PROP_PULL) && (s = select_pull(c))) return bail(s);
     *out = c;
+    return SN_OK;
+}
+
+sn_status sn_create_shard(const sn_config *cfg, const sn_neurons *nr, const sn_synapses *sy, int32_t first,
+                          int32_t count, sn_ctx **out) {
+    if (!cfg || !nr || !sy || !out) return fail(nullptr, SN_EINVAL, "NULL argument");
+    const int n = nr->n;
+    if (first < 0 || count < 1 || (long long)first + count > n || first % 32 != 0 ||
+        (count % 32 != 0 && first + count != n))
+        return fail(nullptr, SN_EINVAL,
+                    "shard: first must be a multiple of 32 and [first, first + count) a range of whole 32-neuron "
+                    "words of [0, n) (the last shard may end at n)");
+    if (cfg->flags & (SN_EXEC_CTA | SN_EXEC_GRID))
+        return fail(nullptr, SN_EINVAL, "shard: executor flags do not apply (a shard runs pull propagation)");
+    int dmin = cfg->max_delay;
+    for (long long k = 0; k < sy->m && sy->delay; ++k)
+        if (sy->delay[k] >= 1 && sy->delay[k] < dmin) dmin = sy->delay[k];
+    sn_config c2 = *cfg;
+    c2.flags &= ~SN_PROP_PULL;
+    sn_ctx *c = nullptr;
+    sn_status s = sn_create(&c2, nr, sy, &c);
+    if (s) return s;
+    c->shard_first = first;
+    c->shard_end = first + count;
+    c->shard_dmin = dmin;
+    c->shard_known = 0;
+    if ((s = dalloc(c, &c->shard_stage, (size_t)c->D * c->words * 4)) || (s = select_pull(c))) {
+        std::string msg = c->err;
+        sn_destroy(c);
+        return fail(nullptr, s, "shard: " + msg);
+    }
+    *out = c;
+    return SN_OK;
+}
+
+sn_status sn_shard_info(const sn_ctx *c, int32_t *first, int32_t *count, int32_t *steps_per_exchange) {
+    if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
+    if (!c->shard_end) return SN_ESTATE;
+    if (first) *first = c->shard_first;
+    if (count) *count = c->shard_end - c->shard_first;
+    if (steps_per_exchange) *steps_per_exchange = c->shard_dmin;
+    return SN_OK;
+}
+
+sn_status sn_shard_put_spikes(sn_ctx *c, int64_t t0, int64_t t1, const uint32_t *bits, int32_t on_device) {
+    if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
+    if (!c->shard_end) return fail(c, SN_ESTATE, "not a shard (sn_create_shard)");
+    if (c->failed) return fail(c, SN_ESTATE, "context has a latched device error");
+    if (t0 != c->shard_known)
+        return fail(c, SN_EINVAL, "shard: the next rows to put start at step " + std::to_string(c->shard_known));
+    if (t1 < t0 || t1 > c->step)
+        return fail(c, SN_EINVAL, "shard: rows can be put only for steps this shard has run");
+    if (t1 - t0 > c->D) return fail(c, SN_EINVAL, "shard: at most max_delay rows per call");
+    if (t1 == t0) return SN_OK;
+    if (!bits) return fail(c, SN_EINVAL, "bits is NULL");
+    const int rows = (int)(t1 - t0);
+    const size_t bytes = (size_t)rows * c->words * 4;
+    const unsigned *src = bits;
+    if (!on_device) {
+        // the staging rows may still be read by an earlier put queued on the stream
+        if (sn_status q = quiesce(c)) return q;
+        SN_CUDA(c, cudaMemcpyAsync(c->shard_stage, bits, bytes, cudaMemcpyHostToDevice, c->stream));
+        src = c->shard_stage;
+    }
+    const int w0 = c->shard_first / 32, w1 = (c->shard_end + 31) / 32;
+    cudaError_t e = launch_shard_put(c->hist, c->raster, c->D, c->cap, c->words, w0, w1, t0, rows, src, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "shard spike rows");
+    if (!on_device) SN_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->shard_known = t1;
     return SN_OK;
 }
 
@@ -517,6 +587,7 @@ sn_status sn_set_poisson_stream(sn_ctx *c, int32_t nsrc, const int32_t *neuron, 
 sn_status sn_stdp(sn_ctx *c, float decay, float a_plus, float a_minus, float wmin, float wmax, int32_t enable) {
     if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
     if (c->kind != KIND_SPARSE && c->kind != KIND_DENSE) return fail(c, SN_EUNSUPPORTED, "STDP: single networks only");
+    if (c->shard_end && enable) return fail(c, SN_EUNSUPPORTED, "STDP is not available for a shard");
     if (!enable) { c->stdp = 0; return SN_OK; }
     if (c->dtype != SN_F32) return fail(c, SN_EUNSUPPORTED, "STDP needs an SN_F32 network");
     if (!c->all_delay_one)
@@ -587,6 +658,16 @@ sn_status sn_run(sn_ctx *c, int32_t steps) {
         return SN_OK;
     }
     if (c->kind != KIND_SPARSE && c->kind != KIND_DENSE) return fail(c, SN_ESTATE, "wrong context kind");
+    if (c->shard_end) {
+        // a shard runs at most the smallest delay's worth of steps, and only
+        // once the other shards' spikes of every earlier step are in
+        if (c->shard_known < c->step)
+            return fail(c, SN_ESTATE, "shard: the other shards' spikes of steps " + std::to_string(c->shard_known) +
+                                          " .. " + std::to_string(c->step - 1) + " are not in (sn_shard_put_spikes)");
+        if (steps > c->shard_dmin)
+            return fail(c, SN_EINVAL, "shard: a run may take at most the smallest synaptic delay (" +
+                                          std::to_string(c->shard_dmin) + ") steps between exchanges");
+    }
     NetArgs a;
     memset(&a, 0, sizeof(a));
     a.n = c->n; a.D1 = c->D1; a.words = c->words; a.cap = c->cap;
@@ -612,6 +693,8 @@ sn_status sn_run(sn_ctx *c, int32_t steps) {
         a.ring_until = (int)std::min<long long>(c->ring_live_until, 2147483647ll);
         a.hL = c->pull_rows;
         a.chunk = c->pull_chunk;
+        a.j_first = c->shard_end ? c->shard_first : 0;
+        a.j_end = c->shard_end ? c->shard_end : c->n;
         e = launch_sparse_pull(a, c->dtype, c->pull_grid, c->pull_smem, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "simulation launch");
         c->hist_live = true;
@@ -665,6 +748,7 @@ sn_status sn_reset(sn_ctx *c) {
     if (c->hist) SN_CUDA(c, cudaMemsetAsync(c->hist, 0, (size_t)c->D * c->words * 4, c->stream));
     c->hist_live = false;
     c->ring_live_until = 0;
+    c->shard_known = 0;
     SN_CUDA(c, cudaMemsetAsync(c->raster, 0, (size_t)c->cap * c->words * 4, c->stream));
     SN_CUDA(c, cudaMemsetAsync(c->ctl, 0, sizeof(Control), c->stream));
     c->step = 0;
@@ -811,6 +895,7 @@ sn_status sn_set_weights(sn_ctx *c, const float *w, int32_t on_device) {
     if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
     if (!w) return fail(c, SN_EINVAL, "w is NULL");
     if (c->failed) return fail(c, SN_ESTATE, "context is in an error state");
+    if (c->shard_end) return fail(c, SN_EUNSUPPORTED, "the weights of a shard are fixed at creation");
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     if (c->kind == KIND_DENSE) {
         if (c->step != 0)
@@ -892,7 +977,8 @@ static size_t save_size(const sn_ctx *c, bool has_trace, bool has_hist) {
 }
 
 static bool can_save(const sn_ctx *c) {
-    return c->kind == KIND_SPARSE || c->kind == KIND_DENSE || c->kind == KIND_BATCH || c->kind == KIND_SHARED_I8;
+    return !c->shard_end &&
+           (c->kind == KIND_SPARSE || c->kind == KIND_DENSE || c->kind == KIND_BATCH || c->kind == KIND_SHARED_I8);
 }
 
 sn_status sn_save(sn_ctx *c, void *buf, size_t *size) {
@@ -1008,6 +1094,7 @@ sn_status sn_load(sn_ctx *c, const void *buf, size_t size) {
 sn_status sn_set_propagation(sn_ctx *c, int32_t mode) {
     if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
     if (c->kind != KIND_SPARSE) return fail(c, SN_EUNSUPPORTED, "propagation mode: sparse single networks only");
+    if (c->shard_end && mode != SN_PULL) return fail(c, SN_EUNSUPPORTED, "a shard runs pull propagation only");
     if (mode == SN_PUSH) { c->prop_pull = 0; return SN_OK; }
     if (mode != SN_PULL) return fail(c, SN_EINVAL, "mode must be SN_PUSH or SN_PULL");
     return select_pull(c);

@@ -259,6 +259,7 @@ sn_status sn_autotune(sn_ctx *c, int32_t trial_steps, float *best_ms) {
     if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
     if (c->kind != KIND_BATCH && c->kind != KIND_SPARSE)
         return fail(c, SN_EUNSUPPORTED, "autotuning applies to batched and sparse contexts");
+    if (c->shard_end) return fail(c, SN_EUNSUPPORTED, "a shard runs pull propagation only: nothing to tune");
     if (c->failed) return fail(c, SN_ESTATE, "context has a latched device error");
     if (trial_steps < 1) return fail(c, SN_EINVAL, "trial_steps must be >= 1");
     if (c->kind == KIND_SPARSE) return sparse_autotune(c, trial_steps, best_ms);

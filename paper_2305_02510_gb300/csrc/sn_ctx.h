@@ -107,6 +107,12 @@ struct sn_ctx {
     unsigned char *sh_A0 = nullptr, *sh_A1 = nullptr, *sh_WT = nullptr;
     int *sh_V0 = nullptr;
     alignas(64) unsigned char sh_tmaps[3 * 128];
+    // shard of a sparse network (sn_create_shard): neurons [shard_first,
+    // shard_end) simulated here, the other shards' spikes put in by the caller
+    int shard_first = 0, shard_end = 0;  // shard_end == 0: not a shard
+    int shard_dmin = 1;                  // smallest synaptic delay of the network
+    long long shard_known = 0;           // every spike row before this step is complete
+    unsigned *shard_stage = nullptr;     // [max_delay][words] staging of host rows
     int failed = 0;                // sticky device failure seen
     std::string err;
     std::vector<void *> allocs;

@@ -74,6 +74,8 @@ struct NetArgs {
     int hD;                           // history depth (the maximum delay D)
     int hL;                           // rows of the pull kernel's shared-memory window
     int ring_until;                   // the ring may hold pending input for steps < ring_until
+    int j_first, j_end;               // pull: the neurons [j_first, j_end) this launch simulates
+                                      // (a shard of the network; 0 and n otherwise)
     // dense store
     float *W;                         // [n][n]
     float *partial;                   // [S][n] gather partial sums
@@ -208,7 +210,10 @@ cudaError_t plan_dense(int n, int *grid, int *chunk, int force_cpl = 0);
 // shared memory, or more than one neuron per thread).  Synapse words of the
 // pull store: x = ((D - d) * Wp + pre / 32) << 7 | (pre & 31),
 // Wp = roundup(ceil(n/32), 4).
-cudaError_t plan_pull(int n, int D, long long m, int *grid, int *chunk, int *rows, size_t *smem);
+cudaError_t plan_pull(int n, int D, long long m, int *grid, int *chunk, int *rows, size_t *smem,
+                      int own_slices = -1);
+cudaError_t launch_shard_put(unsigned *hist, unsigned *raster, int D, int cap, int words, int w0, int w1,
+                             long long t0, int rows, const unsigned *src, cudaStream_t s);
 cudaError_t launch_sparse_pull(const NetArgs &a, int dtype, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_pull_flush(const NetArgs &a, int dtype, int t0, cudaStream_t s);
 cudaError_t launch_gather_weights(const uint2 *syn, const long long *perm_inv, long long m,

@@ -91,8 +91,8 @@ __global__ void __launch_bounds__(kPullMaxBlock, 1) sparse_pull_kernel(NetArgs a
         s_win[i] = (tau >= 0 && w < W) ? __ldcg(a.hist + (size_t)(tau % D) * W + w) : 0u;
     }
 
-    const int j = blockIdx.x * a.chunk + threadIdx.x;
-    const bool mine = j < a.n;
+    const int j = a.j_first + blockIdx.x * a.chunk + threadIdx.x;
+    const bool mine = j < a.j_end;
     const int wbase = j - lane;                       // first neuron of this warp's slice
     V v = 0, th = 0, lk = 0, rs = 0, amp = 0;
     int rr = 0, R = 0, np = 0;
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(kPullMaxBlock, 1) sparse_pull_kernel(NetArgs a
         }
         const int tD = t % D;
         const unsigned ball = __ballot_sync(0xffffffffu, fire);
-        if (lane == 0 && wbase < a.n) {
+        if (lane == 0 && wbase < a.j_end) {
             a.hist[(size_t)tD * W + (wbase >> 5)] = ball;
             a.raster[(size_t)(t % a.cap) * W + (wbase >> 5)] = ball;
         }
@@ -265,13 +265,32 @@ __global__ void pull_flush_kernel(NetArgs a, int t0) {
     }
 }
 
+// Spike words of the other shards of a network, rows of steps t0 .. t0 + rows - 1
+// (whole-network rows of `words` words), into the history and the raster;
+// the words [w0, w1) are this shard's own and are left as its kernel wrote them.
+__global__ void shard_put_kernel(unsigned *hist, unsigned *raster, int D, int cap, int words, int w0, int w1,
+                                 long long t0, int rows, const unsigned *src) {
+    const long long total = (long long)rows * words;
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < total;
+         q += (long long)gridDim.x * blockDim.x) {
+        const int row = (int)(q / words), w = (int)(q % words);
+        if (w >= w0 && w < w1) continue;
+        const long long tau = t0 + row;
+        const unsigned bits = src[q];
+        hist[(size_t)(tau % D) * words + w] = bits;
+        raster[(size_t)(tau % cap) * words + w] = bits;
+    }
+}
+
 const void *pull_fn(int dtype) {
     return dtype == SN_F32 ? (const void *)sparse_pull_kernel<SN_F32> : (const void *)sparse_pull_kernel<SN_I32>;
 }
 
 }  // namespace
 
-cudaError_t plan_pull(int n, int D, long long m, int *grid, int *chunk, int *rows, size_t *smem) {
+// own_slices >= 0: a shard simulating that many 32-neuron slices of the
+// network (its window still holds every neuron's spike bits).
+cudaError_t plan_pull(int n, int D, long long m, int *grid, int *chunk, int *rows, size_t *smem, int own_slices) {
     *grid = 0;
     int dev = 0, sms = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -285,7 +304,8 @@ cudaError_t plan_pull(int n, int D, long long m, int *grid, int *chunk, int *row
     if (L < D) return cudaSuccess;
     // slices per block: spread over the SMs; a small network (at most 1024
     // neurons and 64 Ki synapses) runs as one block, without a grid barrier
-    const long long per = (words * 32 <= kPullMaxBlock && m <= 65536) ? words : (words + sms - 1) / sms;
+    const long long sl = own_slices >= 0 ? own_slices : words;
+    const long long per = (sl * 32 <= kPullMaxBlock && m <= 65536) ? sl : (sl + sms - 1) / sms;
     if (per * 32 > kPullMaxBlock) return cudaSuccess;
     const long long bytes = L * wp * 4;
     for (const void *fn : {pull_fn(SN_F32), pull_fn(SN_I32)}) {
@@ -297,7 +317,7 @@ cudaError_t plan_pull(int n, int D, long long m, int *grid, int *chunk, int *row
         if (p < 1) return cudaSuccess;
     }
     *chunk = (int)(per * 32);
-    *grid = (int)((n + *chunk - 1) / *chunk);
+    *grid = (int)((sl + per - 1) / per);
     *rows = (int)L;
     *smem = (size_t)bytes;
     return cudaSuccess;
@@ -312,6 +332,16 @@ cudaError_t launch_sparse_pull(const NetArgs &a, int dtype, int grid, size_t sme
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(a.chunk), args, smem, s);
+}
+
+cudaError_t launch_shard_put(unsigned *hist, unsigned *raster, int D, int cap, int words, int w0, int w1,
+                             long long t0, int rows, const unsigned *src, cudaStream_t s) {
+    const long long total = (long long)rows * words;
+    if (total == 0) return cudaSuccess;
+    const int block = 256;
+    const int grid = (int)std::min<long long>((total + block - 1) / block, 2048);
+    shard_put_kernel<<<grid, block, 0, s>>>(hist, raster, D, cap, words, w0, w1, t0, rows, src);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_pull_flush(const NetArgs &a, int dtype, int t0, cudaStream_t s) {

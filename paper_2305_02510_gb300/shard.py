@@ -108,3 +108,66 @@ def allreduce_gradients(grads, group=None):
     for g in grads:
         dist.all_reduce(g, op=dist.ReduceOp.SUM, group=group)
     return grads
+
+
+# ---------------------------------------------------------------------------
+# One network over several GPUs: each rank simulates a contiguous range of
+# the neurons (sn_create_shard) and the ranks exchange spike rows.  A spike of
+# step t reaches no neuron before t + d_min (the smallest synaptic delay), so
+# a rank advances d_min steps on the rows it has, then every rank's new rows
+# are combined (each rank contributes the words of its own neurons) and put
+# into every shard before the next d_min steps.
+
+def neuron_shard(n: int, rank: int, world: int):
+    """(first, count) of rank's neurons: a contiguous range of whole 32-neuron
+    raster words, the words split as evenly as possible (count 0 for ranks
+    beyond the word count)."""
+    words = (n + 31) // 32
+    w0 = words * rank // world
+    w1 = words * (rank + 1) // world
+    first = w0 * 32
+    return first, max(0, min(n, w1 * 32) - first)
+
+
+def exchange_loop(steps: int, per_exchange: int, run, own_rows, combine, put):
+    """Advance `steps` steps in runs of at most `per_exchange` steps; after each
+    run of steps [t, t + k): own_rows(t, t + k) gives this rank's rows (its own
+    words set, every other word zero), combine(rows) sums them over the ranks
+    (the ranks' words are disjoint, so the sum is the whole-network rows), and
+    put(t, t + k, rows) installs them.  Returns the steps advanced."""
+    t = 0
+    while t < steps:
+        k = min(per_exchange, steps - t)
+        run(k)
+        rows = own_rows(t, t + k)
+        put(t, t + k, combine(rows))
+        t += k
+    return t
+
+
+def run_shard(ctx, steps: int, t_start: int = 0, group=None):
+    """Advance the shard context `ctx` (sn_create_shard) by `steps` steps from
+    step t_start, exchanging spike rows with the other ranks of `group`
+    (torch.distributed; one all-reduce of the new rows per exchange).  Every
+    rank calls it with the same steps."""
+    import torch
+    import torch.distributed as dist
+    from . import sn as S
+    first, count, k = S.sn_shard_info(ctx)
+    w0, w1 = first // 32, (first + count + 31) // 32
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend(group) == "nccl" \
+        else torch.device("cpu")
+
+    def own_rows(t0, t1):
+        full = S.sn_get_spikes(ctx, t_start + t0, t_start + t1)
+        rows = np.zeros_like(full)
+        rows[:, w0:w1] = full[:, w0:w1]
+        return rows
+
+    def combine(rows):
+        x = torch.from_numpy(rows.view(np.int32).copy()).to(dev)
+        dist.all_reduce(x, op=dist.ReduceOp.SUM, group=group)
+        return x.cpu().numpy().view(np.uint32)
+
+    return exchange_loop(steps, k, lambda n_: S.sn_run(ctx, n_), own_rows, combine,
+                         lambda t0, t1, rows: S.sn_shard_put_spikes(ctx, t_start + t0, t_start + t1, rows))

@@ -88,6 +88,10 @@ def lib():
                                     C.POINTER(_P)],
                 "sn_create_axonal": [C.POINTER(sn_config), C.POINTER(sn_neurons), C.POINTER(sn_synapses), _P,
                                      C.POINTER(_P)],
+                "sn_create_shard": [C.POINTER(sn_config), C.POINTER(sn_neurons), C.POINTER(sn_synapses),
+                                    C.c_int32, C.c_int32, C.POINTER(_P)],
+                "sn_shard_info": [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)],
+                "sn_shard_put_spikes": [_P, C.c_int64, C.c_int64, _P, C.c_int32],
                 "sn_create_batch": [C.POINTER(sn_config), C.c_int32, C.POINTER(sn_neurons),
                                     C.POINTER(sn_synapses), C.POINTER(_P)],
                 "sn_batch_config": [_P, C.c_int32, C.c_int32],
@@ -254,6 +258,61 @@ def sn_create(threshold, leak, reset, refractory, pre, post, weight, delay, *, d
         keep.append(ax)
         _check(lib().sn_create_axonal(C.byref(cfg), C.byref(nr), C.byref(sy), _ptr(ax), C.byref(h)))
     return Ctx(h, nr.n, cfg.dtype, (nr.n + 31) // 32, "sparse", pre.size)
+
+
+def sn_create_shard(threshold, leak, reset, refractory, pre, post, weight, delay, first, count, *,
+                    dtype=SN_F32, max_delay=None, record_steps=0, stream=None) -> Ctx:
+    """Shard [first, first + count) of a sparse network (sn_create_shard)."""
+    keep = []
+    nr = _neurons(threshold, leak, reset, refractory, keep)
+    pre, post, w, d = _synapses(pre, post, weight, delay, keep)
+    sy = sn_synapses()
+    sy.m = pre.size
+    sy.pre, sy.post, sy.weight, sy.delay = _ptr(pre), _ptr(post), _ptr(w), _ptr(d)
+    D = int(max_delay if max_delay is not None else (d.max() if d.size else 1))
+    cfg = _config(dtype, D, SN_AUTO, record_steps, stream)
+    h = _P()
+    _check(lib().sn_create_shard(C.byref(cfg), C.byref(nr), C.byref(sy), int(first), int(count), C.byref(h)))
+    return Ctx(h, nr.n, cfg.dtype, (nr.n + 31) // 32, "shard", pre.size)
+
+
+def sn_shard_info(ctx: Ctx):
+    """(first, count, steps per exchange) of a shard."""
+    f, c, k = C.c_int32(), C.c_int32(), C.c_int32()
+    _check(lib().sn_shard_info(ctx.handle, C.byref(f), C.byref(c), C.byref(k)), ctx)
+    return f.value, c.value, k.value
+
+
+def sn_shard_put_spikes(ctx: Ctx, t0: int, t1: int, bits):
+    """The other shards' spike rows of steps [t0, t1): uint32 [t1 - t0, words]
+    (numpy, or a CUDA tensor of int32/uint32)."""
+    rows = int(t1) - int(t0)
+    if hasattr(bits, "data_ptr"):
+        if not _is_dev(bits):
+            raise ValueError("bits: a torch tensor must be a CUDA tensor")
+        _out(bits, rows * ctx.words * 4, "sn_shard_put_spikes (bits)")
+        dev = 1
+    else:
+        bits = np.ascontiguousarray(bits, np.uint32)
+        if bits.size < rows * ctx.words:
+            raise ValueError(f"bits: need {rows} x {ctx.words} words, got {bits.size}")
+        dev = 0
+    _check(lib().sn_shard_put_spikes(ctx.handle, int(t0), int(t1), _ptr(bits) if rows else None, dev), ctx)
+
+
+def from_workload_shard(wl, first, count, *, record_steps=None, stream=None) -> Ctx:
+    """Shard [first, first + count) of a sparse workload dict, with its inputs."""
+    rec = wl["steps"] if record_steps is None else record_steps
+    ctx = sn_create_shard(wl["threshold"], wl["leak"], wl["reset"], wl["refractory"], wl["pre"], wl["post"],
+                          wl["weight"], wl["delay"], first, count, dtype=wl["dtype"],
+                          max_delay=wl["max_delay"], record_steps=rec, stream=stream)
+    ev = wl["events"]
+    if len(ev["step"]):
+        sn_set_input(ctx, ev["step"], ev["neuron"], ev["value"])
+    po = wl["poisson"]
+    if len(po["neuron"]):
+        sn_set_poisson(ctx, po["neuron"], po["rate"], po["amplitude"], po["seed"])
+    return ctx
 
 
 def sn_create_dense(threshold, leak, reset, refractory, w, delay=1, *, max_delay=None,

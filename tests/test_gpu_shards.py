@@ -125,3 +125,99 @@ def test_bptt_batch_shards_sum_to_whole_batch_gradient():
         s = parts[0][l] + parts[1][l]
         rel = float((s - g).norm() / g.norm())
         assert g.norm() > 0 and rel < 1e-5, (l, rel)
+
+
+# ---------------------------------------------------------------------------
+# One network over several GPUs: shard contexts (sn_create_shard), emulated
+# here one after another on one GPU with the rows exchanged on the host, must
+# reproduce the single pull context bit for bit.
+
+def run_network_shards(wl, world, steps):
+    from paper_2305_02510_gb300 import sn as S
+    ctxs = [S.from_workload_shard(wl, *shard.neuron_shard(wl["n"], r, world), record_steps=steps)
+            for r in range(world)]
+    k = S.sn_shard_info(ctxs[0])[2]
+    ranges = [shard.neuron_shard(wl["n"], r, world) for r in range(world)]
+
+    def run(n_steps):
+        for c in ctxs:
+            S.sn_run(c, n_steps)
+
+    def own_rows(t0, t1):
+        rows = []
+        for c, (f, cnt) in zip(ctxs, ranges):
+            full = S.sn_get_spikes(c, t0, t1)
+            own = np.zeros_like(full)
+            own[:, f // 32:(f + cnt + 31) // 32] = full[:, f // 32:(f + cnt + 31) // 32]
+            rows.append(own)
+        return rows
+
+    def combine(rows):
+        return np.sum([r.astype(np.uint64) for r in rows], axis=0).astype(np.uint32)
+
+    def put(t0, t1, rows):
+        for c in ctxs:
+            S.sn_shard_put_spikes(c, t0, t1, rows)
+
+    assert shard.exchange_loop(steps, k, run, own_rows, combine, put) == steps
+    raster = S.unpack_raster(S.sn_get_spikes(ctxs[0], 0, steps), wl["n"])
+    v = np.zeros(wl["n"], np.float32 if wl["dtype"] == "f32" else np.int32)
+    r = np.zeros(wl["n"], np.int32)
+    spikes = events = 0
+    for c, (f, cnt) in zip(ctxs, ranges):
+        vv, rr = S.sn_get_state(c)
+        v[f:f + cnt], r[f:f + cnt] = vv[f:f + cnt], rr[f:f + cnt]
+        _, sp, ev = S.sn_get_counters(c)
+        spikes, events = spikes + sp, events + ev
+        assert np.array_equal(S.unpack_raster(S.sn_get_spikes(c, 0, steps), wl["n"]), raster)
+    return raster, v, r, spikes, events, k
+
+
+@pytest.mark.parametrize("case,world", [("small-d2", 2), ("small-d2", 3), ("sparse-float", 2),
+                                        ("sparse-float", 4), ("sparse-int", 3)])
+def test_network_shards_equal_single_context(case, world):
+    from paper_2305_02510_gb300 import sn as S
+    if case == "small-d2":
+        wl = W.random_small(21, n=300, integer=False, steps=120, max_delay=5, p=0.05, events_rate=2.0)
+        wl["delay"] = np.maximum(np.asarray(wl["delay"], np.int32), 2)   # smallest delay 2: exchange every 2 steps
+        steps = 120
+    else:
+        wl = W.large_sparse(integer=case == "sparse-int", n=20_000, steps=80)
+        steps = 80
+    raster, v, r, spikes, events, k = run_network_shards(wl, world, steps)
+    assert k == int(np.min(wl["delay"]))
+    whole = S.from_workload(wl, flags=S.SN_PROP_PULL, record_steps=steps)
+    S.sn_run(whole, steps)
+    want = S.unpack_raster(S.sn_get_spikes(whole, 0, steps), wl["n"])
+    wv, wr = S.sn_get_state(whole)
+    assert np.array_equal(raster, want), f"first differing step {np.nonzero((raster != want).any(1))[0][:1]}"
+    assert np.array_equal(v.view(np.uint32), np.asarray(wv).view(np.uint32)) and np.array_equal(r, wr)
+    _, wsp, wev = S.sn_get_counters(whole)
+    assert spikes == wsp and events == wev and want[-1].sum() > 0
+
+
+def test_shard_exchange_rules():
+    from paper_2305_02510_gb300 import sn as S
+    wl = W.random_small(22, n=100, integer=True, steps=20, max_delay=4, p=0.1)
+    wl["delay"] = np.maximum(np.asarray(wl["delay"], np.int32), 2)
+    c = S.from_workload_shard(wl, 32, 68, record_steps=20)
+    assert S.sn_shard_info(c) == (32, 68, 2)
+    with pytest.raises(S.SnError) as e:            # more than the smallest delay at once
+        S.sn_run(c, 3)
+    assert e.value.status == S.SN_EINVAL
+    S.sn_run(c, 2)
+    with pytest.raises(S.SnError) as e:            # the other shard's rows are not in yet
+        S.sn_run(c, 1)
+    assert e.value.status == S.SN_ESTATE
+    with pytest.raises(S.SnError) as e:            # rows of steps not run
+        S.sn_shard_put_spikes(c, 0, 3, np.zeros((3, 4), np.uint32))
+    assert e.value.status == S.SN_EINVAL
+    S.sn_shard_put_spikes(c, 0, 2, np.zeros((2, 4), np.uint32))
+    S.sn_run(c, 2)
+    for bad in (dict(first=16, count=32), dict(first=0, count=40)):
+        with pytest.raises(S.SnError) as e:
+            S.from_workload_shard(wl, bad["first"], bad["count"])
+        assert e.value.status == S.SN_EINVAL
+    with pytest.raises(S.SnError) as e:
+        S.sn_set_propagation(c, S.SN_PUSH)
+    assert e.value.status == S.SN_EUNSUPPORTED

@@ -160,3 +160,96 @@ def test_shards_on_two_gloo_ranks_equal_one_rank():
         b = b.numpy()
         assert np.abs(b).max() > 0
         assert np.allclose(a, b, rtol=1e-12, atol=1e-14 * np.abs(b).max())
+
+
+def _network_shard_rank(rank, world, port, out):
+    """One rank of a sharded network with the oracle standing in for its GPU:
+    each step it advances the whole oracle network from its own rows (the
+    other ranks' rows of the current exchange window still zero) and keeps
+    only its own neurons; the rows move through shard.exchange_loop, the
+    product's exchange schedule, with a gloo all-reduce."""
+    import numpy as np
+    import torch
+    from oracle import oracle as O
+    from paper_2305_02510_gb300 import shard, workloads as W
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    wl = _sharded_workload()
+    n, D, T = wl["n"], wl["max_delay"], wl["steps"]
+    first, count = shard.neuron_shard(n, rank, world)
+    mine = slice(first, first + count)
+    words = (n + 31) // 32
+    loc = np.zeros((T, n), np.uint8)          # rows this rank knows
+    v = np.asarray(np.float32(wl["reset"]), np.float64).copy()
+    r = np.zeros(n, np.int32)
+    state = {"t": 0}
+
+    def run(k):
+        for u in range(state["t"], state["t"] + k):
+            hist = np.zeros((D, n), np.uint8)
+            for q in range(D):
+                tau = u - D + q
+                if tau >= 0:
+                    hist[q] = loc[tau]
+            st = O.state_from(wl, u, v, r, hist)
+            st, row, _ = O.run(wl, O.F32, 1, state=st)
+            v[mine], r[mine] = st.v[mine], st.r[mine]
+            loc[u, mine] = row[0, mine]
+        state["t"] += k
+
+    def own_rows(t0, t1):
+        bits = np.zeros((t1 - t0, words * 32), np.uint8)
+        bits[:, mine] = loc[t0:t1, mine]
+        return np.packbits(bits, axis=1, bitorder="little").view(np.uint32)
+
+    def combine(rows):
+        x = torch.from_numpy(rows.view(np.int32).astype(np.int64))
+        dist.all_reduce(x, op=dist.ReduceOp.SUM)
+        return x.numpy().astype(np.uint32)
+
+    def put(t0, t1, rows):
+        full = np.unpackbits(rows.view(np.uint8), axis=1, bitorder="little")[:, :n]
+        loc[t0:t1] = full
+
+    k = int(np.min(wl["delay"]))
+    shard.exchange_loop(T, k, run, own_rows, combine, put)
+    states = [None] * world
+    dist.all_gather_object(states, (first, count, v[mine].copy(), r[mine].copy()))
+    if rank == 0:
+        out["raster"] = loc.copy()
+        out["states"] = states
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def _sharded_workload():
+    import numpy as np
+    from paper_2305_02510_gb300 import workloads as W
+    wl = W.random_small(31, n=150, integer=False, steps=60, max_delay=5, p=0.06, events_rate=2.0)
+    wl["delay"] = np.maximum(np.asarray(wl["delay"], np.int32), 2)
+    return wl
+
+
+def test_network_shards_on_two_gloo_ranks_equal_one_rank():
+    """A single network split over two ranks by neuron range, exchanging spike
+    rows every d_min = 2 steps: the combined raster and every neuron's state
+    equal the unsharded oracle run (float32 mirror) bit for bit."""
+    import numpy as np
+    from oracle import oracle as O
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        out = m.dict()
+        port = _free_port()
+        procs = [ctx.Process(target=_network_shard_rank, args=(r, 2, port, out)) for r in range(2)]
+        for p in procs:
+            p.start()
+        for p in procs:
+            p.join(300)
+            assert p.exitcode == 0
+        res = dict(out)
+    wl = _sharded_workload()
+    st, want, _ = O.run(wl, O.F32, wl["steps"])
+    assert want.sum() > 0 and np.array_equal(res["raster"], want)
+    for first, count, v, r in res["states"]:
+        assert np.array_equal(v, st.v[first:first + count]) and np.array_equal(r, st.r[first:first + count])
