@@ -84,6 +84,7 @@ struct sn_ctx {
     cudaGraphNode_t graph_kernel = nullptr;
     // feedforward network trained by BPTT
     int ff_layers = 0, ff_batch = 0, ff_steps = 0, ff_k = 10, ff_splits = 1, ff_refr = 0;
+    size_t ff_part_elems = 0;          // floats of the weight gradient's partial-sum buffer
     float ff_theta = 1, ff_leak = 0, ff_reset = 0, ff_slope = 10;
     std::vector<int> ff_sizes;
     std::vector<uint8_t *> ff_D;       // device delays per layer

@@ -104,7 +104,12 @@ sn_status tc_weight_grad(sn_ctx *c, int l, float *dW) {
     a.M = nin; a.N = nout;
     a.tiles_m = (nin + 127) / 128; a.tiles_n = (nout + 127) / 128;
     const int tiles = a.tiles_m * a.tiles_n;
-    int ks = std::max(1, std::min({sms / std::max(1, tiles), c->ff_splits, rows_p / 64 / 8}));
+    // K (the T * B rows) split over enough blocks to fill the GPU, as far as
+    // the partial-sum buffer holds the splits (a narrow output layer has few
+    // tiles and takes many splits)
+    const long long cap = (long long)(c->ff_part_elems / ((size_t)nin * nout));
+    int ks = (int)std::max(1LL, std::min<long long>({(long long)(sms / std::max(1, tiles)), cap,
+                                                     (long long)(rows_p / 64 / 8)}));
     a.ksplit = ks;
     a.nacc = 4; a.mode = 1; a.D = c->ff_D[l - 1]; a.ldc = nout; a.ctl = c->ctl;
     const long long count = (long long)nin * nout;
@@ -299,6 +304,7 @@ sn_status sn_create_ff(const sn_config *cfg, int32_t layers, const int32_t *size
         (s = dalloc(c, &c->ctl, sizeof(Control))))
         return bail(s);
     if (cudaMemset(c->ctl, 0, sizeof(Control)) != cudaSuccess) return bail(SN_ECUDA);
+    c->ff_part_elems = (size_t)c->ff_splits * nin_max * nout_max;
     // every layer's synaptic input kept for the backward, unless asked not to
     // or the memory is not there (then the backward recomputes it)
     if (!(cfg->flags & SN_FF_RECOMPUTE)) {
