@@ -73,9 +73,10 @@ typedef enum {
 typedef enum {
     SN_F32 = 0,  /* float state.  Push propagation sums the synaptic input
                     exactly in fixed point (2^-32) and rounds it once to
-                    float; pull propagation adds the weights in float in
-                    ascending (delay, pre, input index) order.  Neither
-                    depends on thread timing.                                */
+                    float; pull propagation adds the weights in float,
+                    the oldest spikes first (descending delay, then
+                    ascending pre and input index).  Neither depends on
+                    thread timing.                                           */
     SN_I32 = 1   /* exact integer state; parameters and weights must be
                     integral (checked)                                       */
 } sn_dtype;
@@ -294,8 +295,9 @@ sn_status sn_stdp(sn_ctx *ctx, float decay, float a_plus, float a_minus,
 /* Propagation of a sparse network (sn_create), SN_PUSH or SN_PULL.
  *   push: each spike of step t adds its weights to the pending input of its
  *     targets for steps t + d (event-driven; work grows with the spike count).
- *   pull: each neuron sums, over its incoming synapses in ascending (delay,
- *     pre, input index) order, the weights whose pre-neuron spiked at t - d
+ *   pull: each neuron sums, over its incoming synapses in descending delay,
+ *     then ascending pre and input index, the weights whose pre-neuron spiked
+ *     at t - d
  *     (Section 2.1's "spikes of the previous step times the weights", with
  *     delays); work is the synapse count every step, independent of activity.
  *     In SN_F32 mode this is exactly the FP32 mirror's order of additions.

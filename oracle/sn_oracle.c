@@ -31,9 +31,13 @@
  *   ORC_INT: integer values; all operations are exact in double while the
  *            magnitudes stay below 2^53 (checked: the state compared with
  *            the threshold must stay below 2^31 in magnitude).
- * Canonical order of the synaptic sum for post-neuron j at step t:
- *   acc = 0; for each incoming synapse in ascending (delay, pre, input index):
- *   if pre spiked at t - delay: acc = acc + w.   Then V = (L(V) + acc) + ext.
+ * Canonical order of the synaptic sum for post-neuron j at step t (the paper
+ * fixes none: Section 2.1 writes the input as the spikes times the weights,
+ * Section 2.2 as the deliveries of the delay registers): the arrivals are
+ * added oldest spike first, i.e.
+ *   acc = 0; for each incoming synapse in descending delay, then ascending
+ *   pre and input index: if pre spiked at t - delay: acc = acc + w.
+ * Then V = (L(V) + acc) + ext.
  * External input of (t, j): the explicit events of (t, j) in the order given,
  * then the Poisson source of j (if any), summed into ext starting from 0.
  *
@@ -139,7 +143,7 @@ typedef struct { int32_t d, pre; int64_t k; } inc_key;
 static int cmp_inc(const void *a, const void *b)
 {
     const inc_key *x = (const inc_key *)a, *y = (const inc_key *)b;
-    if (x->d != y->d) return x->d < y->d ? -1 : 1;
+    if (x->d != y->d) return x->d > y->d ? -1 : 1;      /* oldest spike (largest delay) first */
     if (x->pre != y->pre) return x->pre < y->pre ? -1 : 1;
     return x->k < y->k ? -1 : (x->k > y->k);
 }

@@ -20,6 +20,10 @@
 using namespace sn;
 
 thread_local std::string g_create_err;
+namespace sn {
+thread_local long long g_fault_alloc = 0;
+thread_local int g_fault_depth = 0;
+}  // namespace sn
 
 namespace {
 
@@ -72,12 +76,17 @@ sn_status size_sparse_executor(sn_ctx *c) {
     return SN_OK;
 }
 
-// Incoming synapses of every neuron in ascending (delay, pre, input index)
-// order, laid out for the pull kernel: the neurons 32s .. 32s+31 form slice s;
-// entry q of neuron 32s + l is half q % 2 of uint4 number
-// pin_off[s] + (q / 2) * 32 + l, as {((D - d) * Wp + pre / 32) << 7 | pre % 32,
-// weight bits}; unused halves stay all-zero.  Built from the CSR, whose rows
-// keep the input order, so ties of (delay, pre) stay in input order.
+// Incoming synapses of every neuron in the canonical order of the float sum:
+// descending delay, then ascending pre and input index (the oldest spikes
+// first), laid out for the pull kernel in two regions per slice of 32 neurons
+// (neurons 32s .. 32s+31): first the synapses of delay >= 2 (the ones a step
+// can add before the previous step's spikes are in), then those of delay 1.
+// Entry q of a region of neuron 32s + l is half q % 2 of uint4 number
+// start + (q / 2) * 32 + l, as {((D - d) * Wp + pre / 32) << 7 | pre % 32,
+// weight bits}; the delay->=2 region of slice s starts at pin_off[s] and is
+// padded to its longest list, the delay-1 region follows it; unused halves
+// stay all-zero.  Built from the CSR, whose rows keep the input order, so ties
+// of (delay, pre) stay in input order.
 sn_status build_pull_store(sn_ctx *c) {
     const int n = c->n;
     const long long m = c->m;
@@ -86,48 +95,57 @@ sn_status build_pull_store(sn_ctx *c) {
     std::vector<long long> rowptr(n + 1);
     SN_CUDA(c, cudaMemcpy(syn.data(), c->syn, (size_t)(m > 0 ? m : 1) * 8, cudaMemcpyDeviceToHost));
     SN_CUDA(c, cudaMemcpy(rowptr.data(), c->rowptr, (size_t)(n + 1) * 8, cudaMemcpyDeviceToHost));
-    // CSR positions bucketed by delay, stable (pre ascending, input order)
-    std::vector<long long> dstart(c->D + 2, 0);
-    for (long long p = 0; p < m; ++p) dstart[(syn[p].x >> kPostBits) + 1]++;
-    for (int d = 0; d <= c->D; ++d) dstart[d + 1] += dstart[d];
+    // CSR positions bucketed by delay, largest delay first, stable (pre
+    // ascending, input order within a pre)
+    const int D = c->D;
+    std::vector<long long> dstart(D + 2, 0);             // bucket k holds delay D - k
+    for (long long p = 0; p < m; ++p) dstart[(D - 1 - (int)(syn[p].x >> kPostBits)) + 1]++;
+    for (int k = 0; k <= D; ++k) dstart[k + 1] += dstart[k];
     std::vector<uint32_t> byd(m > 0 ? m : 1), pre_of(m > 0 ? m : 1);
-    std::vector<int> len(n, 0);
+    std::vector<int> lenA(n, 0), lenB(n, 0);
     for (int i = 0; i < n; ++i)
         for (long long p = rowptr[i]; p < rowptr[i + 1]; ++p) {
-            byd[dstart[syn[p].x >> kPostBits]++] = (uint32_t)p;
+            const int d = (int)(syn[p].x >> kPostBits) + 1;
+            byd[dstart[D - d]++] = (uint32_t)p;
             pre_of[p] = (uint32_t)i;
-            len[syn[p].x & kPostMask]++;
+            (d == 1 ? lenB : lenA)[syn[p].x & kPostMask]++;
         }
     const int slices = (n + 31) / 32;
-    std::vector<long long> off(slices);
+    std::vector<long long> off(slices), offB(slices);
     long long total = 0;
     for (int sl = 0; sl < slices; ++sl) {
-        int L = 0;
-        for (int j = sl * 32; j < std::min(n, sl * 32 + 32); ++j) L = std::max(L, len[j]);
+        int LA = 0, LB = 0;
+        for (int j = sl * 32; j < std::min(n, sl * 32 + 32); ++j) {
+            LA = std::max(LA, lenA[j]);
+            LB = std::max(LB, lenB[j]);
+        }
         off[sl] = total;
-        total += (long long)((L + 1) / 2) * 32;
+        offB[sl] = total + (long long)((LA + 1) / 2) * 32;
+        total = offB[sl] + (long long)((LB + 1) / 2) * 32;
     }
     std::vector<uint4> pin(total > 0 ? total : 1, make_uint4(0, 0, 0, 0));
     const unsigned wp = (unsigned)((c->words + 3) & ~3);   // window row stride of the pull kernel
-    std::vector<int> fill(n, 0);
+    std::vector<int> fillA(n, 0), fillB(n, 0);
     for (long long k = 0; k < m; ++k) {
         const uint32_t p = byd[k];
         const int j = (int)(syn[p].x & kPostMask);
-        const int q = fill[j]++;
-        uint4 &u = pin[off[j >> 5] + (long long)(q >> 1) * 32 + (j & 31)];
         const unsigned pre = pre_of[p], d = (syn[p].x >> kPostBits) + 1;
-        const unsigned x = (((unsigned)(c->D - d) * wp + (pre >> 5)) << 7) | (pre & 31u);
+        const int q = d == 1 ? fillB[j]++ : fillA[j]++;
+        uint4 &u = pin[(d == 1 ? offB : off)[j >> 5] + (long long)(q >> 1) * 32 + (j & 31)];
+        const unsigned x = (((unsigned)(D - d) * wp + (pre >> 5)) << 7) | (pre & 31u);
         if (q & 1) { u.z = x; u.w = syn[p].y; } else { u.x = x; u.y = syn[p].y; }
     }
     sn_status s;
     if (!c->pin) {
         if ((s = dalloc(c, &c->pin, (size_t)(total > 0 ? total : 1) * 16)) ||
-            (s = dalloc(c, &c->pin_off, (size_t)slices * 8)) || (s = dalloc(c, &c->pin_len, (size_t)n * 4)))
+            (s = dalloc(c, &c->pin_off, (size_t)slices * 8)) || (s = dalloc(c, &c->pin_len, (size_t)n * 4)) ||
+            (s = dalloc(c, &c->pin_len1, (size_t)n * 4)))
             return s;
     }
     SN_CUDA(c, cudaMemcpy(c->pin, pin.data(), (size_t)(total > 0 ? total : 1) * 16, cudaMemcpyHostToDevice));
     SN_CUDA(c, cudaMemcpy(c->pin_off, off.data(), (size_t)slices * 8, cudaMemcpyHostToDevice));
-    SN_CUDA(c, cudaMemcpy(c->pin_len, len.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
+    SN_CUDA(c, cudaMemcpy(c->pin_len, lenA.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
+    SN_CUDA(c, cudaMemcpy(c->pin_len1, lenB.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
     c->pin_stale = false;
     return SN_OK;
 }
@@ -248,6 +266,7 @@ const char *sn_last_error(const sn_ctx *ctx) {
 }
 
 sn_status sn_create(const sn_config *cfg, const sn_neurons *nr, const sn_synapses *sy, sn_ctx **out) {
+    FaultScope fault_scope;
     sn_status s = check_config(cfg);
     if (s) return s;
     if (!nr || !sy || !out) return fail(nullptr, SN_EINVAL, "NULL argument");
@@ -322,6 +341,7 @@ sn_status sn_create(const sn_config *cfg, const sn_neurons *nr, const sn_synapse
 
 sn_status sn_create_shard(const sn_config *cfg, const sn_neurons *nr, const sn_synapses *sy, int32_t first,
                           int32_t count, sn_ctx **out) {
+    FaultScope fault_scope;
     if (!cfg || !nr || !sy || !out) return fail(nullptr, SN_EINVAL, "NULL argument");
     const int n = nr->n;
     if (first < 0 || count < 1 || (long long)first + count > n || first % 32 != 0 ||
@@ -391,6 +411,7 @@ sn_status sn_shard_put_spikes(sn_ctx *c, int64_t t0, int64_t t1, const uint32_t 
 
 sn_status sn_create_axonal(const sn_config *cfg, const sn_neurons *nr, const sn_synapses *sy,
                            const int32_t *axonal_delay, sn_ctx **out) {
+    FaultScope fault_scope;
     if (!axonal_delay) return sn_create(cfg, nr, sy, out);
     sn_status s = check_config(cfg);
     if (s) return s;
@@ -420,6 +441,7 @@ sn_status sn_create_axonal(const sn_config *cfg, const sn_neurons *nr, const sn_
 
 sn_status sn_create_dense(const sn_config *cfg, const sn_neurons *nr, const float *w, int32_t delay,
                           sn_ctx **out) {
+    FaultScope fault_scope;
     sn_status s = check_config(cfg);
     if (s) return s;
     if (!nr || !out) return fail(nullptr, SN_EINVAL, "NULL argument");
@@ -689,7 +711,7 @@ sn_status sn_run(sn_ctx *c, int32_t steps) {
             sn_status st = build_pull_store(c);
             if (st) return st;
         }
-        a.pin = c->pin; a.pin_off = c->pin_off; a.pin_len = c->pin_len;
+        a.pin = c->pin; a.pin_off = c->pin_off; a.pin_len = c->pin_len; a.pin_len1 = c->pin_len1;
         a.ring_until = (int)std::min<long long>(c->ring_live_until, 2147483647ll);
         a.hL = c->pull_rows;
         a.chunk = c->pull_chunk;

@@ -135,6 +135,7 @@ extern "C" {
 
 sn_status sn_create_batch(const sn_config *cfg, int32_t nets, const sn_neurons *neurons,
                           const sn_synapses *synapses, sn_ctx **out) {
+    sn::FaultScope fault_scope;
     if (!cfg || !neurons || !synapses || !out) return fail(nullptr, SN_EINVAL, "NULL argument");
     if (cfg->dtype != SN_F32 && cfg->dtype != SN_I32) return fail(nullptr, SN_EINVAL, "bad dtype");
     if (cfg->max_delay < 1 || cfg->max_delay > kBatchMaxDelay)

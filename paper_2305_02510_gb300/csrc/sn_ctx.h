@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -36,7 +37,8 @@ struct sn_ctx {
     size_t pull_smem = 0;
     uint4 *pin = nullptr;              // incoming synapses in 32-neuron slices
     long long *pin_off = nullptr;
-    int *pin_len = nullptr;
+    int *pin_len = nullptr;            // synapses of delay >= 2 of each neuron
+    int *pin_len1 = nullptr;           // synapses of delay 1 of each neuron
     bool pin_stale = true;             // the pull store must be (re)built from the CSR
     unsigned *hist = nullptr;          // [D][words] spike bits whose deliveries may be due
     bool hist_live = false;            // hist may hold spikes not yet delivered
@@ -148,10 +150,31 @@ inline sn_status quiesce(sn_ctx *c) {
         if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);   \
     } while (0)
 
+// Host-side fault injection for tests of the failure paths: while a create
+// call runs with the environment variable SN_FAULT_ALLOC_AT = k (k >= 1), its
+// k-th device allocation fails with SN_ENOMEM (no allocation is made).
+extern thread_local long long g_fault_alloc;   // allocations left before the injected failure; 0 = off
+extern thread_local int g_fault_depth;
+
+struct FaultScope {
+    FaultScope() {
+        if (g_fault_depth++ == 0) {
+            const char *e = std::getenv("SN_FAULT_ALLOC_AT");
+            g_fault_alloc = e ? std::atoll(e) : 0;
+            if (g_fault_alloc < 0) g_fault_alloc = 0;
+        }
+    }
+    ~FaultScope() {
+        if (--g_fault_depth == 0) g_fault_alloc = 0;
+    }
+};
+
 template <typename T>
 inline sn_status dalloc(sn_ctx *c, T **p, size_t bytes) {
     void *q = nullptr;
     if (bytes == 0) bytes = 16;
+    if (g_fault_alloc > 0 && --g_fault_alloc == 0)
+        return fail(c, SN_ENOMEM, "injected device allocation failure (SN_FAULT_ALLOC_AT)");
     cudaError_t e = cudaMalloc(&q, bytes);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();

@@ -218,6 +218,7 @@ sn_status sn_ff_set_engine(sn_ctx *c, int32_t engine) {
 
 sn_status sn_create_ff(const sn_config *cfg, int32_t layers, const int32_t *sizes, const uint8_t *const *delays,
                        const sn_ff_params *p, int32_t batch, int32_t steps, sn_ctx **out) {
+    sn::FaultScope fault_scope;
     if (!cfg || !sizes || !delays || !p || !out) return fail(nullptr, SN_EINVAL, "NULL argument");
     if (layers < 1 || layers > 16) return fail(nullptr, SN_EINVAL, "layers must be in 1..16");
     if (batch < 1 || steps < 1) return fail(nullptr, SN_EINVAL, "batch and steps must be >= 1");

@@ -69,7 +69,8 @@ struct NetArgs {
     // 32-neuron slices, pairs {pre | (delay-1) << 26, weight bits} x 2
     const uint4 *pin;
     const long long *pin_off;         // [slices] first uint4 of each slice
-    const int *pin_len;               // [n] incoming synapses of each neuron
+    const int *pin_len;               // [n] incoming synapses of delay >= 2 of each neuron
+    const int *pin_len1;              // [n] incoming synapses of delay 1 (the region after them)
     unsigned *hist;                   // [hD][words] spike bits of step tau in row tau % hD
     int hD;                           // history depth (the maximum delay D)
     int hL;                           // rows of the pull kernel's shared-memory window

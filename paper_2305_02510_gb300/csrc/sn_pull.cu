@@ -5,9 +5,9 @@
 // Every block keeps the spike bits of recent steps in a shared-memory window
 // of hL rows of Wp = roundup(ceil(n/32), 4) words: the row of step tau sits
 // at position tau - base.  Each thread owns one neuron, holds its state in
-// registers and walks the neuron's incoming synapses in ascending (delay,
-// pre, input index) order, testing the bit of pre at step t - d and adding
-// the weight.  A synapse is stored as x = e << 7 | (pre & 31) with
+// registers and walks the neuron's incoming synapses in descending delay,
+// then ascending pre and input index (the oldest spikes first), testing the
+// bit of pre at step t - d and adding the weight.  A synapse is stored as x = e << 7 | (pre & 31) with
 // e = (D - d) * Wp + pre / 32, the word offset of its bit from the row of step
 // t - D, so that a test is one shift, one shared load and one funnel shift.
 // The synapses of 32 consecutive neurons form a slice (one warp): entry q of
@@ -20,9 +20,11 @@
 //
 // One grid barrier per step, split: a block arrives once its spike words of
 // step t are in the global history, then (while the other blocks finish)
-// compacts its window when the next row would fall off its end and loads
-// the first synapses of step t + 1; after the wait it copies row t into the
-// window.  The global history (row of step tau in slot tau % D) holds, between
+// compacts its window when the next row would fall off its end and sums the
+// synapses of delay >= 2 of step t + 1, which read rows up to t - 1 only; after
+// the wait it copies row t into the window and adds the synapses of delay 1.
+// The synapses of delay >= 2 and of delay 1 sit in two regions of the store,
+// so that both loops read whole 512-byte runs per warp.  The global history (row of step tau in slot tau % D) holds, between
 // runs, every spike of the last D steps whose deliveries are still due;
 // pull_flush_kernel turns them into pending ring input when the context
 // switches to push propagation.
@@ -75,6 +77,22 @@ __device__ __forceinline__ void pull_load(uint4 (&e)[kPullUnroll], const uint4 *
 }
 
 
+// The synapses [0, np) of one region (np per lane, npmax the warp's largest)
+// added to acc; e0 holds the region's first kPullUnroll pairs on entry and
+// nothing useful on exit.
+template <int MODE>
+__device__ __forceinline__ void pull_region(typename PullAcc<MODE>::T &acc, uint4 (&e0)[kPullUnroll],
+                                            uint4 (&e1)[kPullUnroll], const uint4 *ent, int np, int npmax,
+                                            const unsigned char *win, unsigned row0) {
+    constexpr int P = kPullUnroll;
+    for (int p0 = 0; p0 < npmax; p0 += 2 * P) {
+        pull_load(e1, ent, p0 + P, np);
+        pull_batch<MODE>(acc, e0, win, row0);
+        pull_load(e0, ent, p0 + 2 * P, np);
+        pull_batch<MODE>(acc, e1, win, row0);
+    }
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(kPullMaxBlock, 1) sparse_pull_kernel(NetArgs a) {
     using V = typename Tr<MODE>::V;
@@ -95,7 +113,7 @@ __global__ void __launch_bounds__(kPullMaxBlock, 1) sparse_pull_kernel(NetArgs a
     const bool mine = j < a.j_end;
     const int wbase = j - lane;                       // first neuron of this warp's slice
     V v = 0, th = 0, lk = 0, rs = 0, amp = 0;
-    int rr = 0, R = 0, np = 0;
+    int rr = 0, R = 0, npA = 0, npB = 0;
     unsigned thr = 0;
     unsigned long long outdeg = 0;
     const uint4 *ent = a.pin;
@@ -108,11 +126,16 @@ __global__ void __launch_bounds__(kPullMaxBlock, 1) sparse_pull_kernel(NetArgs a
         R = a.R[j];
         thr = a.prate[j];
         amp = ((const V *)a.pamp)[j];
-        np = (a.pin_len[j] + 1) >> 1;
+        npA = (a.pin_len[j] + 1) >> 1;
+        npB = (a.pin_len1[j] + 1) >> 1;
         outdeg = (unsigned long long)(a.rowptr[j + 1] - a.rowptr[j]);
         ent = a.pin + a.pin_off[j >> 5] + lane;
     }
-    const int npmax = __reduce_max_sync(0xffffffffu, np);   // pairs of the warp's longest list
+    // pairs of the warp's longest list in each region; the delay-1 region
+    // starts after the slice's delay->=2 region
+    const int npAmax = __reduce_max_sync(0xffffffffu, npA);
+    const int npBmax = __reduce_max_sync(0xffffffffu, npB);
+    const uint4 *entB = ent + (size_t)npAmax * 32;
     using RA = typename Tr<MODE>::A;
     RA *ring = (RA *)a.ring;
     unsigned long long my_spikes = 0, my_events = 0;
@@ -120,19 +143,20 @@ __global__ void __launch_bounds__(kPullMaxBlock, 1) sparse_pull_kernel(NetArgs a
     // synapse loads run one half (four pairs) ahead of their use
     constexpr int P = kPullUnroll;
     uint4 ea[P], eb[P];
-    pull_load(ea, ent, 0, np);
+    pull_load(ea, ent, 0, npA);
     __syncthreads();
+    // the delay >= 2 part of the first step: every row it reads is in the window
+    Acc acc = 0;
+    if (a.steps > 0) {
+        pull_region<MODE>(acc, ea, eb, ent, npA, npAmax, win, (unsigned)((a.t0 - base - D) * Wp) * 4u);
+        pull_load(ea, entB, 0, npB);
+    }
     for (int s = 0; s < a.steps; ++s) {
         const int t = a.t0 + s;
         const unsigned row0 = (unsigned)((t - base - D) * Wp) * 4u;
         bool fire = false;
-        Acc acc = 0;
-        for (int p0 = 0; p0 < npmax; p0 += 2 * P) {
-            pull_load(eb, ent, p0 + P, np);
-            pull_batch<MODE>(acc, ea, win, row0);
-            pull_load(ea, ent, p0 + 2 * P, np);
-            pull_batch<MODE>(acc, eb, win, row0);
-        }
+        // the delay-1 part: row t - 1 is in the window
+        pull_region<MODE>(acc, ea, eb, entB, npB, npBmax, win, row0);
         if (mine) {
             // input still pending in the ring from an earlier push run
             V ring_in = 0;
@@ -187,7 +211,7 @@ __global__ void __launch_bounds__(kPullMaxBlock, 1) sparse_pull_kernel(NetArgs a
         unsigned gen = 0;
         if (threadIdx.x == 0 && gridDim.x > 1) gen = bar_arrive(a.ctl);
         // the first synapses of step t + 1 (the store is static)
-        pull_load(ea, ent, 0, np);
+        pull_load(ea, ent, 0, npA);
         int pos = t - base;                           // window position of row t
         if (pos >= L) {
             // rows t-D+1 .. t-1 move down by sh = pos - D + 1 rows to positions
@@ -207,6 +231,13 @@ __global__ void __launch_bounds__(kPullMaxBlock, 1) sparse_pull_kernel(NetArgs a
             }
             base = t - D + 1;
             pos = D - 1;
+        }
+        // the delay >= 2 part of step t + 1 (rows t + 1 - d <= t - 1, all in the
+        // window) while the other blocks arrive; then the first delay-1 loads
+        acc = 0;
+        if (s + 1 < a.steps) {
+            pull_region<MODE>(acc, ea, eb, ent, npA, npAmax, win, (unsigned)((t + 1 - base - D) * Wp) * 4u);
+            pull_load(ea, entB, 0, npB);
         }
         if (threadIdx.x == 0) {
             s_ok = gridDim.x > 1 ? bar_wait(a.ctl, gen) : 1;

@@ -106,6 +106,7 @@ sn_status shared_set_poisson(sn_ctx *c, int32_t nsrc, const int32_t *neuron, con
 
 extern "C" sn_status sn_create_shared_dense_i8(const sn_config *cfg, const sn_neurons *nr, const int8_t *w,
                                                int32_t trains, sn_ctx **out) {
+    sn::FaultScope fault_scope;
     if (!cfg || !nr || !w || !out) return fail(nullptr, SN_EINVAL, "NULL argument");
     if (cfg->dtype != SN_I32) return fail(nullptr, SN_EINVAL, "the shared dense network is integer (SN_I32)");
     if (cfg->max_delay != 1) return fail(nullptr, SN_EINVAL, "the shared dense network has delay 1 (max_delay = 1)");

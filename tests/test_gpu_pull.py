@@ -1,10 +1,10 @@
 """Pull propagation of sparse networks through the C ABI, against the CPU
 oracle.
 
-Pull sums each neuron's incoming weights in float in ascending (delay, pre,
-input index) order, the order of the oracle's FP32 mirror, so float runs must
-match the mirror bit for bit (spikes and states, every step), not only within
-the float tolerance; integer runs are bit-exact as always.  Switching between
+Pull sums each neuron's incoming weights in float, the oldest spikes first
+(descending delay, then ascending pre and input index), the order of the
+oracle's FP32 mirror, so float runs must match the mirror bit for bit (spikes
+and states, every step), not only within the float tolerance; integer runs are bit-exact as always.  Switching between
 push and pull, checkpoints across the switch and the autotuner's choice must
 leave the trajectory unchanged.
 """

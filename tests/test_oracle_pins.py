@@ -557,3 +557,21 @@ def test_fp32_mirror_drifts_past_the_state_bound_over_long_dense_runs():
     ratio = np.abs(a.v - b.v) / (1e-5 * np.maximum(np.abs(a.v), 1.0))
     assert ratio.max() > 1.5, ratio.max()
     assert np.quantile(ratio, 0.99) < 1.0
+
+
+def test_synaptic_sum_order_fp32():
+    """The float32 mirror adds a step's arrivals oldest spike first (largest
+    delay first, then pre-neuron): into neuron 3 at step 2 arrive +1e8 and +1
+    (delay 2, from neurons 0 and 1, spiking at step 0) and -1e8 (delay 1, from
+    neuron 2, spiking at step 1).  Oldest first, (1e8 + 1) - 1e8 = 0 in
+    float32; in ascending delay order it would be (-1e8 + 1e8) + 1 = 1;
+    float64 gives 1 either way."""
+    wl = W._base(4, "f32", [0.5, 0.5, 0.5, 1e30], 0.0, 0.0, 0, 2, 3)
+    wl.update(pre=np.array([0, 1, 2], np.int32), post=np.array([3, 3, 3], np.int32),
+              weight=np.array([1e8, 1.0, -1e8]), delay=np.array([2, 2, 1], np.int32))
+    wl["events"] = dict(step=np.array([0, 0, 1], np.int32), neuron=np.array([0, 1, 2], np.int32),
+                        value=np.ones(3))
+    st32, r32, _ = O.run(wl, O.F32, 3, record_v=True)
+    st64, r64, _ = O.run(wl, O.F64, 3, record_v=True)
+    assert r32[0, :2].tolist() == [1, 1] and r32[1, 2] == 1
+    assert st32.ctrace[2, 3] == 0.0 and st64.ctrace[2, 3] == 1.0
