@@ -85,8 +85,10 @@ sn_status size_sparse_executor(sn_ctx *c) {
 // start + (q / 2) * 32 + l, as {((D - d) * Wp + pre / 32) << 7 | pre % 32,
 // weight bits}; the delay->=2 region of slice s starts at pin_off[s] and is
 // padded to its longest list, the delay-1 region follows it; unused halves
-// stay all-zero.  Built from the CSR, whose rows keep the input order, so ties
-// of (delay, pre) stay in input order.
+// stay all-zero.  A network run by one block (no grid barrier to overlap) keeps
+// every synapse in the first region, the delay-1 ones last.  Built from the
+// CSR, whose rows keep the input order, so ties of (delay, pre) stay in input
+// order.
 sn_status build_pull_store(sn_ctx *c) {
     const int n = c->n;
     const long long m = c->m;
@@ -103,12 +105,13 @@ sn_status build_pull_store(sn_ctx *c) {
     for (int k = 0; k <= D; ++k) dstart[k + 1] += dstart[k];
     std::vector<uint32_t> byd(m > 0 ? m : 1), pre_of(m > 0 ? m : 1);
     std::vector<int> lenA(n, 0), lenB(n, 0);
+    const bool one_region = c->pull_grid == 1;
     for (int i = 0; i < n; ++i)
         for (long long p = rowptr[i]; p < rowptr[i + 1]; ++p) {
             const int d = (int)(syn[p].x >> kPostBits) + 1;
             byd[dstart[D - d]++] = (uint32_t)p;
             pre_of[p] = (uint32_t)i;
-            (d == 1 ? lenB : lenA)[syn[p].x & kPostMask]++;
+            (d == 1 && !one_region ? lenB : lenA)[syn[p].x & kPostMask]++;
         }
     const int slices = (n + 31) / 32;
     std::vector<long long> off(slices), offB(slices);
@@ -130,8 +133,9 @@ sn_status build_pull_store(sn_ctx *c) {
         const uint32_t p = byd[k];
         const int j = (int)(syn[p].x & kPostMask);
         const unsigned pre = pre_of[p], d = (syn[p].x >> kPostBits) + 1;
-        const int q = d == 1 ? fillB[j]++ : fillA[j]++;
-        uint4 &u = pin[(d == 1 ? offB : off)[j >> 5] + (long long)(q >> 1) * 32 + (j & 31)];
+        const bool inB = d == 1 && !one_region;
+        const int q = inB ? fillB[j]++ : fillA[j]++;
+        uint4 &u = pin[(inB ? offB : off)[j >> 5] + (long long)(q >> 1) * 32 + (j & 31)];
         const unsigned x = (((unsigned)(D - d) * wp + (pre >> 5)) << 7) | (pre & 31u);
         if (q & 1) { u.z = x; u.w = syn[p].y; } else { u.x = x; u.y = syn[p].y; }
     }
@@ -267,6 +271,7 @@ const char *sn_last_error(const sn_ctx *ctx) {
 
 sn_status sn_create(const sn_config *cfg, const sn_neurons *nr, const sn_synapses *sy, sn_ctx **out) {
     FaultScope fault_scope;
+    NvtxRange nvtx("sn_create");
     sn_status s = check_config(cfg);
     if (s) return s;
     if (!nr || !sy || !out) return fail(nullptr, SN_EINVAL, "NULL argument");
@@ -342,6 +347,7 @@ sn_status sn_create(const sn_config *cfg, const sn_neurons *nr, const sn_synapse
 sn_status sn_create_shard(const sn_config *cfg, const sn_neurons *nr, const sn_synapses *sy, int32_t first,
                           int32_t count, sn_ctx **out) {
     FaultScope fault_scope;
+    NvtxRange nvtx("sn_create");
     if (!cfg || !nr || !sy || !out) return fail(nullptr, SN_EINVAL, "NULL argument");
     const int n = nr->n;
     if (first < 0 || count < 1 || (long long)first + count > n || first % 32 != 0 ||
@@ -382,6 +388,7 @@ sn_status sn_shard_info(const sn_ctx *c, int32_t *first, int32_t *count, int32_t
 }
 
 sn_status sn_shard_put_spikes(sn_ctx *c, int64_t t0, int64_t t1, const uint32_t *bits, int32_t on_device) {
+    NvtxRange nvtx("sn_shard_put_spikes");
     if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
     if (!c->shard_end) return fail(c, SN_ESTATE, "not a shard (sn_create_shard)");
     if (c->failed) return fail(c, SN_ESTATE, "context has a latched device error");
@@ -412,6 +419,7 @@ sn_status sn_shard_put_spikes(sn_ctx *c, int64_t t0, int64_t t1, const uint32_t 
 sn_status sn_create_axonal(const sn_config *cfg, const sn_neurons *nr, const sn_synapses *sy,
                            const int32_t *axonal_delay, sn_ctx **out) {
     FaultScope fault_scope;
+    NvtxRange nvtx("sn_create");
     if (!axonal_delay) return sn_create(cfg, nr, sy, out);
     sn_status s = check_config(cfg);
     if (s) return s;
@@ -442,6 +450,7 @@ sn_status sn_create_axonal(const sn_config *cfg, const sn_neurons *nr, const sn_
 sn_status sn_create_dense(const sn_config *cfg, const sn_neurons *nr, const float *w, int32_t delay,
                           sn_ctx **out) {
     FaultScope fault_scope;
+    NvtxRange nvtx("sn_create");
     sn_status s = check_config(cfg);
     if (s) return s;
     if (!nr || !out) return fail(nullptr, SN_EINVAL, "NULL argument");
@@ -667,6 +676,7 @@ static sn_status read_status(sn_ctx *c) {
 }
 
 sn_status sn_run(sn_ctx *c, int32_t steps) {
+    NvtxRange nvtx("sn_run");
     if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
     if (c->failed) return fail(c, SN_ESTATE, "context has a latched device error");
     if (steps < 0) return fail(c, SN_EINVAL, "steps < 0");
@@ -745,6 +755,7 @@ sn_status sn_run(sn_ctx *c, int32_t steps) {
 }
 
 sn_status sn_reset(sn_ctx *c) {
+    NvtxRange nvtx("sn_reset");
     if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
     if (c->kind == KIND_SHARED_I8) {
         const size_t bn = (size_t)c->sh_B * c->n;
@@ -1004,6 +1015,7 @@ static bool can_save(const sn_ctx *c) {
 }
 
 sn_status sn_save(sn_ctx *c, void *buf, size_t *size) {
+    NvtxRange nvtx("sn_save");
     if (!c || !size) return fail(c, SN_EINVAL, "NULL argument");
     if (!can_save(c)) return fail(c, SN_ESTATE, "wrong context kind");
     const bool has_hist = c->kind == KIND_SPARSE && c->hist_live;
@@ -1052,6 +1064,7 @@ sn_status sn_save(sn_ctx *c, void *buf, size_t *size) {
 }
 
 sn_status sn_load(sn_ctx *c, const void *buf, size_t size) {
+    NvtxRange nvtx("sn_load");
     if (!c || !buf) return fail(c, SN_EINVAL, "NULL argument");
     if (size < sizeof(SaveHeader)) return fail(c, SN_EINVAL, "buffer too small");
     SaveHeader hd;

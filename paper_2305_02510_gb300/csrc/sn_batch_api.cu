@@ -257,6 +257,7 @@ sn_status sn_create_batch(const sn_config *cfg, int32_t nets, const sn_neurons *
 }
 
 sn_status sn_autotune(sn_ctx *c, int32_t trial_steps, float *best_ms) {
+    NvtxRange nvtx("sn_autotune");
     if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
     if (c->kind != KIND_BATCH && c->kind != KIND_SPARSE)
         return fail(c, SN_EUNSUPPORTED, "autotuning applies to batched and sparse contexts");

@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "sn_internal.h"
 
 using namespace sn;
@@ -149,6 +151,15 @@ inline sn_status quiesce(sn_ctx *c) {
         cudaError_t e_ = (call);                                     \
         if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #call);   \
     } while (0)
+
+// An NVTX range over one library call (visible to profilers that record
+// NVTX; free when none is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Host-side fault injection for tests of the failure paths: while a create
 // call runs with the environment variable SN_FAULT_ALLOC_AT = k (k >= 1), its

@@ -331,6 +331,7 @@ sn_status sn_create_ff(const sn_config *cfg, int32_t layers, const int32_t *size
 }
 
 sn_status sn_ff_forward(sn_ctx *c, const uint8_t *input, const float *const *w, float *counts) {
+    NvtxRange nvtx("sn_ff_forward");
     if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
     if (c->kind != KIND_FF) return fail(c, SN_ESTATE, "not a feedforward context");
     if (!input || !w || !counts) return fail(c, SN_EINVAL, "NULL argument");
@@ -367,6 +368,7 @@ sn_status sn_ff_forward(sn_ctx *c, const uint8_t *input, const float *const *w, 
 }
 
 sn_status sn_backward(sn_ctx *c, const float *grad_counts, float *const *grad_w, int32_t on_device) {
+    NvtxRange nvtx("sn_backward");
     if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
     if (c->kind != KIND_FF) return fail(c, SN_ESTATE, "not a feedforward context");
     if (!on_device) return fail(c, SN_EUNSUPPORTED, "sn_backward takes device buffers (on_device = 1)");

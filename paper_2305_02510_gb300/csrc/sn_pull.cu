@@ -210,6 +210,10 @@ __global__ void __launch_bounds__(kPullMaxBlock, 1) sparse_pull_kernel(NetArgs a
         __syncthreads();                              // every warp's words of step t are stored
         unsigned gen = 0;
         if (threadIdx.x == 0 && gridDim.x > 1) gen = bar_arrive(a.ctl);
+        // a single block reads the status word now, so that the read overlaps
+        // the work below (a grid reads it after the barrier)
+        int stop_early = 0;
+        if (threadIdx.x == 0 && gridDim.x == 1) stop_early = ld_status(a.ctl);
         // the first synapses of step t + 1 (the store is static)
         pull_load(ea, ent, 0, npA);
         int pos = t - base;                           // window position of row t
@@ -232,6 +236,13 @@ __global__ void __launch_bounds__(kPullMaxBlock, 1) sparse_pull_kernel(NetArgs a
             base = t - D + 1;
             pos = D - 1;
         }
+        // a single block owns every word of row t: it puts its own words into
+        // the window now, and its store keeps the delay-1 synapses at the end of
+        // the first region, so the sum below is the whole step's
+        if (gridDim.x == 1) {
+            if (lane == 0 && wbase < a.j_end) s_win[(size_t)pos * Wp + (wbase >> 5)] = ball;
+            __syncthreads();
+        }
         // the delay >= 2 part of step t + 1 (rows t + 1 - d <= t - 1, all in the
         // window) while the other blocks arrive; then the first delay-1 loads
         acc = 0;
@@ -241,13 +252,15 @@ __global__ void __launch_bounds__(kPullMaxBlock, 1) sparse_pull_kernel(NetArgs a
         }
         if (threadIdx.x == 0) {
             s_ok = gridDim.x > 1 ? bar_wait(a.ctl, gen) : 1;
-            s_stop = ld_status(a.ctl);
+            s_stop = gridDim.x > 1 ? ld_status(a.ctl) : stop_early;
         }
         __syncthreads();
         if (!s_ok) break;
-        // row t enters the window
-        for (int i = threadIdx.x; i < W; i += blockDim.x)
-            s_win[(size_t)pos * Wp + i] = __ldcg(a.hist + (size_t)tD * W + i);
+        // row t enters the window (a single block has put it in above)
+        if (gridDim.x > 1) {
+            for (int i = threadIdx.x; i < W; i += blockDim.x)
+                s_win[(size_t)pos * Wp + i] = __ldcg(a.hist + (size_t)tD * W + i);
+        }
         __syncthreads();
         if (s_stop) break;
     }
