@@ -309,17 +309,28 @@ def extras(S, W, torch, stream, flush):
         # per spike: its weight row (4n B); per neuron and step: the update's
         # state traffic
         abytes = spk * 4 * n + 1000 * n * STATE_BYTES
+        sector_bytes = None
         if stdp:
             # spiking rows written back; spiking columns read+written in every
-            # other row (one 32 B sector per element at this density)
-            abytes += spk * 4 * n + spk * (n - spk / 1000) * 8
-        res["dense_stdp" if stdp else "dense"] = {
+            # other row (4 B each way per element)
+            col = spk * (n - spk / 1000)
+            abytes += spk * 4 * n + col * 8
+            # the same at the memory's granularity: a column element is alone in
+            # its 32-byte sector at this density, so reading it moves 32 B
+            # (writes of unchanged weights are skipped, so none are counted)
+            sector_bytes = abytes - col * 8 + col * 32
+        line_ = {
             "workload": wl["name"], "neurons": n, "timesteps": 1000, "ms": ms,
             "synaptic_events_per_s": ev / (ms / 1e3), "timesteps_per_s": 1000 / (ms / 1e3),
             "spikes_per_timestep": spk / 1000,
             "roofline": {"bound": "hbm", "achieved": abytes / (ms / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": abytes / (ms / 1e3) / 1e9 / peak, "peak_source": src,
                          "kernel": "dense_kernel<1,true,false>" if stdp else "dense_kernel<1,false,true>"}}
+        if sector_bytes is not None:
+            line_["roofline"]["frac_sector_reads"] = sector_bytes / (ms / 1e3) / 1e9 / peak
+            line_["roofline"]["sector_note"] = ("column pass counted at 32 B per element read (one sector "
+                                                "each), unchanged weights not written")
+        res["dense_stdp" if stdp else "dense"] = line_
         del ctx
     res["dense_stdp"]["stdp_overhead"] = res["dense_stdp"]["ms"] / res["dense"]["ms"]
     # batched networks against the plain per-network path
