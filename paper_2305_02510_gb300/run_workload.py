@@ -30,6 +30,8 @@ def main():
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--propagation", choices=["push", "pull"], default="push",
                     help="large-sparse: push or pull propagation")
+    ap.add_argument("--dense-slab", type=int, default=0, choices=[0, 1, 2, 4, 8],
+                    help="large-dense: column slab of 32 * k columns per block (SN_DENSE_SLAB; 0 = the library's choice)")
     args = ap.parse_args()
     import __graft_entry__ as G
     G.build()
@@ -59,7 +61,8 @@ def main():
     elif wl_name in ("large-dense", "large-dense-stdp"):
         n = int(16384 * args.scale) // 32 * 32
         ctx = S.from_workload(W.large_dense(n=n, stdp=wl_name.endswith("stdp"), steps=T), record_steps=T,
-                              stream=stream.cuda_stream)
+                              stream=stream.cuda_stream,
+                              flags=S.SN_DENSE_SLAB(args.dense_slab) if args.dense_slab else S.SN_AUTO)
     elif wl_name == "batched":
         nets = W.batched_nets(count=max(1, int(4096 * args.scale)), steps=T)
         ctx = S.from_batch_workloads(nets, record_steps=T, stream=stream.cuda_stream)
