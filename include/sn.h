@@ -104,6 +104,17 @@ typedef enum {
                                tuning).  SN_EUNSUPPORTED if that grid is not
                                co-resident                                        */
 #define SN_DENSE_SLAB_MASK 0xF00u
+#define SN_PULL_PLAIN 0x1000u
+#define SN_PULL_CODED 0x2000u
+                            /* sn_create only: the form of the pull store (see
+                               sn_pull_store_info).  Without either flag the
+                               library builds the plain form while it takes at
+                               most 80 % of the L2 cache, else the smaller
+                               form.  The two forms
+                               hold the same synapses in the same order, so
+                               the results are identical; the flags let tests
+                               and tuning run either                          */
+#define SN_PULL_STORE_MASK 0x3000u
 
 #define SN_MAX_DELAY 64     /* largest supported synaptic delay                    */
 
@@ -111,7 +122,8 @@ typedef struct {
     int32_t dtype;          /* sn_dtype                                            */
     int32_t max_delay;      /* D: every synaptic delay lies in 1..D, D <= 64       */
     uint32_t flags;         /* SN_AUTO or one SN_EXEC_* value, optionally with
-                               SN_PROP_PULL or SN_DENSE_SLAB(k)                    */
+                               SN_PROP_PULL, one SN_PULL_* form or
+                               SN_DENSE_SLAB(k)                                    */
     int32_t record_steps;   /* spike-raster capacity in steps (a ring); sn_get_spikes
                                can return any of the last record_steps steps; 0
                                means 1                                              */
@@ -310,6 +322,19 @@ sn_status sn_stdp(sn_ctx *ctx, float decay, float a_plus, float a_minus,
 #define SN_PULL 1
 sn_status sn_set_propagation(sn_ctx *ctx, int32_t mode);
 sn_status sn_get_propagation(const sn_ctx *ctx, int32_t *mode);
+
+/* The pull store of a sparse context, built on the first pull run (or by
+ * SN_PROP_PULL / sn_set_propagation).  Every synapse is one entry; the store
+ * pads each region of a 32-neuron slice to the slice's longest list.
+ *   *format  (may be NULL): 0 = not built yet, SN_PULL_PLAIN = 8 bytes per
+ *            entry (bit offset, weight), SN_PULL_CODED = 6 bytes per entry
+ *            (weight and the 16-bit step of the bit offset from the previous
+ *            entry; a larger step takes filler entries of weight 0);
+ *   *bytes   (may be NULL): device bytes of the store, padding included;
+ *   *entries (may be NULL): entries of all lists, fillers included
+ *            (m when there are none).
+ * SN_EINVAL for a context that is not a sparse network. */
+sn_status sn_pull_store_info(const sn_ctx *ctx, int32_t *format, int64_t *bytes, int64_t *entries);
 
 /* Advance `steps` timesteps (steps >= 0) from the current step.  Queued on the
  * context's stream; a step counter makes repeated calls continue the run. */

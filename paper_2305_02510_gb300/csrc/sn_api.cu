@@ -33,8 +33,10 @@ sn_status check_config(const sn_config *cfg) {
     if (cfg->max_delay < 1 || cfg->max_delay > SN_MAX_DELAY)
         return fail(nullptr, SN_EINVAL, "max_delay must be in 1..64");
     if (cfg->record_steps < 0) return fail(nullptr, SN_EINVAL, "record_steps < 0");
-    if (cfg->flags & ~(SN_EXEC_CTA | SN_EXEC_GRID | SN_PROP_PULL | SN_DENSE_SLAB_MASK))
+    if (cfg->flags & ~(SN_EXEC_CTA | SN_EXEC_GRID | SN_PROP_PULL | SN_DENSE_SLAB_MASK | SN_PULL_STORE_MASK))
         return fail(nullptr, SN_EINVAL, "unknown flags");
+    if ((cfg->flags & SN_PULL_STORE_MASK) == SN_PULL_STORE_MASK)
+        return fail(nullptr, SN_EINVAL, "SN_PULL_PLAIN and SN_PULL_CODED are exclusive");
     if ((cfg->flags & SN_EXEC_CTA) && (cfg->flags & SN_EXEC_GRID))
         return fail(nullptr, SN_EINVAL, "SN_EXEC_CTA and SN_EXEC_GRID are exclusive");
     return SN_OK;
@@ -81,14 +83,29 @@ sn_status size_sparse_executor(sn_ctx *c) {
 // first), laid out for the pull kernel in two regions per slice of 32 neurons
 // (neurons 32s .. 32s+31): first the synapses of delay >= 2 (the ones a step
 // can add before the previous step's spikes are in), then those of delay 1.
-// Entry q of a region of neuron 32s + l is half q % 2 of uint4 number
-// start + (q / 2) * 32 + l, as {((D - d) * Wp + pre / 32) << 7 | pre % 32,
-// weight bits}; the delay->=2 region of slice s starts at pin_off[s] and is
-// padded to its longest list, the delay-1 region follows it; unused halves
-// stay all-zero.  A network run by one block (no grid barrier to overlap) keeps
-// every synapse in the first region, the delay-1 ones last.  Built from the
-// CSR, whose rows keep the input order, so ties of (delay, pre) stay in input
-// order.
+// A synapse's bit in the kernel's spike window lies y = (D - d) * Wp * 32 + pre
+// bits after the row of step t - D, and y never decreases along a list.
+// Two forms of the store, both in uint4 units, both padded per region to the
+// slice's longest list (padding is all-zero):
+//  - plain: entry q of the neuron in lane l is half q % 2 of uint4
+//    start + (q / 2) * 32 + l, as {(y / 32 * 4) << 5 | y % 32, weight bits}
+//    (8 bytes per synapse);
+//  - coded: entries in groups of 8; group g of lane l is the uint4s
+//    start + g * 96 + {0, 32, 64} + l, holding weights 0-3, weights 4-7 and the
+//    eight 16-bit steps y_q - y_(q-1) (the first step is 0; the first y is
+//    pin_y0[region * n + j]).  A step above 65535 is taken in filler entries
+//    of step 65535 and weight 0, which add +0 (an exact no-op: the sum starts
+//    at +0 and is never -0) at offsets inside the window (6 bytes per synapse
+//    plus the fillers).
+// The form is the plain one while its store takes at most 80 % of the L2,
+// else the smaller one, unless pin_format forces one.  (At 10^5 neurons and
+// delays 1..16, 100 synapses a neuron run at the same speed in both forms;
+// at 125 the plain store, 124 MB, no longer stays in the L2 and the coded
+// one, 96 MB, runs 1.6x faster.)  The delay->=2
+// region of slice s starts at pin_off[s]; the delay-1 region follows it.  A
+// network run by one block (no grid barrier to overlap) keeps every synapse
+// in the first region, the delay-1 ones last.  Built from the CSR, whose rows
+// keep the input order, so ties of (delay, pre) stay in input order.
 sn_status build_pull_store(sn_ctx *c) {
     const int n = c->n;
     const long long m = c->m;
@@ -104,52 +121,106 @@ sn_status build_pull_store(sn_ctx *c) {
     for (long long p = 0; p < m; ++p) dstart[(D - 1 - (int)(syn[p].x >> kPostBits)) + 1]++;
     for (int k = 0; k <= D; ++k) dstart[k + 1] += dstart[k];
     std::vector<uint32_t> byd(m > 0 ? m : 1), pre_of(m > 0 ? m : 1);
-    std::vector<int> lenA(n, 0), lenB(n, 0);
-    const bool one_region = c->pull_grid == 1;
     for (int i = 0; i < n; ++i)
         for (long long p = rowptr[i]; p < rowptr[i + 1]; ++p) {
-            const int d = (int)(syn[p].x >> kPostBits) + 1;
-            byd[dstart[D - d]++] = (uint32_t)p;
+            byd[dstart[D - 1 - (int)(syn[p].x >> kPostBits)]++] = (uint32_t)p;
             pre_of[p] = (uint32_t)i;
-            (d == 1 && !one_region ? lenB : lenA)[syn[p].x & kPostMask]++;
         }
-    const int slices = (n + 31) / 32;
-    std::vector<long long> off(slices), offB(slices);
-    long long total = 0;
-    for (int sl = 0; sl < slices; ++sl) {
-        int LA = 0, LB = 0;
-        for (int j = sl * 32; j < std::min(n, sl * 32 + 32); ++j) {
-            LA = std::max(LA, lenA[j]);
-            LB = std::max(LB, lenB[j]);
-        }
-        off[sl] = total;
-        offB[sl] = total + (long long)((LA + 1) / 2) * 32;
-        total = offB[sl] + (long long)((LB + 1) / 2) * 32;
-    }
-    std::vector<uint4> pin(total > 0 ? total : 1, make_uint4(0, 0, 0, 0));
-    const unsigned wp = (unsigned)((c->words + 3) & ~3);   // window row stride of the pull kernel
-    std::vector<int> fillA(n, 0), fillB(n, 0);
+    const bool one_region = c->pull_grid == 1;
+    const unsigned long long wbits = (unsigned long long)((c->words + 3) & ~3) * 32;   // window row, bits
+    auto region_of = [&](uint32_t p) { return ((syn[p].x >> kPostBits) == 0 && !one_region) ? 1 : 0; };
+    auto y_of = [&](uint32_t p) {
+        return (unsigned)((unsigned long long)(D - 1 - (int)(syn[p].x >> kPostBits)) * wbits + pre_of[p]);
+    };
+    // list lengths of both forms (the coded one with its fillers)
+    std::vector<int> len[2] = {std::vector<int>(n, 0), std::vector<int>(n, 0)};
+    std::vector<int> lenc[2] = {std::vector<int>(n, 0), std::vector<int>(n, 0)};
+    std::vector<unsigned> y0(2 * (size_t)n, 0u), ylast(2 * (size_t)n, 0u);
     for (long long k = 0; k < m; ++k) {
         const uint32_t p = byd[k];
-        const int j = (int)(syn[p].x & kPostMask);
-        const unsigned pre = pre_of[p], d = (syn[p].x >> kPostBits) + 1;
-        const bool inB = d == 1 && !one_region;
-        const int q = inB ? fillB[j]++ : fillA[j]++;
-        uint4 &u = pin[(inB ? offB : off)[j >> 5] + (long long)(q >> 1) * 32 + (j & 31)];
-        const unsigned x = (((unsigned)(D - d) * wp + (pre >> 5)) << 7) | (pre & 31u);
-        if (q & 1) { u.z = x; u.w = syn[p].y; } else { u.x = x; u.y = syn[p].y; }
+        const int j = (int)(syn[p].x & kPostMask), r = region_of(p);
+        const unsigned y = y_of(p);
+        if (len[r][j]++ == 0) { y0[(size_t)r * n + j] = y; lenc[r][j] = 1; }
+        else lenc[r][j] += (int)std::max(1u, (y - ylast[(size_t)r * n + j] + 65534u) / 65535u);
+        ylast[(size_t)r * n + j] = y;
+    }
+    const int slices = (n + 31) / 32;
+    long long total[2] = {0, 0};                          // uint4s: plain, coded
+    std::vector<long long> off[2] = {std::vector<long long>(slices), std::vector<long long>(slices)};
+    std::vector<long long> offB[2] = {std::vector<long long>(slices), std::vector<long long>(slices)};
+    for (int sl = 0; sl < slices; ++sl) {
+        int LA[2] = {0, 0}, LB[2] = {0, 0};
+        for (int j = sl * 32; j < std::min(n, sl * 32 + 32); ++j) {
+            LA[0] = std::max(LA[0], len[0][j]);  LB[0] = std::max(LB[0], len[1][j]);
+            LA[1] = std::max(LA[1], lenc[0][j]); LB[1] = std::max(LB[1], lenc[1][j]);
+        }
+        off[0][sl] = total[0];
+        offB[0][sl] = total[0] + (long long)((LA[0] + 1) / 2) * 32;
+        total[0] = offB[0][sl] + (long long)((LB[0] + 1) / 2) * 32;
+        off[1][sl] = total[1];
+        offB[1][sl] = total[1] + (long long)((LA[1] + 7) / 8) * 96;
+        total[1] = offB[1][sl] + (long long)((LB[1] + 7) / 8) * 96;
+    }
+    // the library's choice: the plain form (fewer instructions a synapse)
+    // while its store stays well inside the L2, which serves it every step;
+    // the coded form when that keeps the store smaller
+    int l2 = 0, dev = 0;
+    SN_CUDA(c, cudaGetDevice(&dev));
+    SN_CUDA(c, cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev));
+    const bool plain_fits = (double)total[0] * 16 <= 0.8 * (double)l2;
+    const int f = c->pin_format == 1 ? 0 : c->pin_format == 2 ? 1 : (!plain_fits && total[1] < total[0] ? 1 : 0);
+    const long long tot = std::max(total[f], 1ll);
+    std::vector<uint4> pin(tot, make_uint4(0, 0, 0, 0));
+    auto comp = [](uint4 &v, int i) -> unsigned & { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; };
+    std::vector<int> fill[2] = {std::vector<int>(n, 0), std::vector<int>(n, 0)};
+    for (long long k = 0; k < m; ++k) {
+        const uint32_t p = byd[k];
+        const int j = (int)(syn[p].x & kPostMask), r = region_of(p), l = j & 31;
+        const unsigned y = y_of(p);
+        const long long start = (r ? offB[f] : off[f])[j >> 5];
+        if (f == 0) {
+            const int q = fill[r][j]++;
+            uint4 &u = pin[start + (long long)(q >> 1) * 32 + l];
+            const unsigned x = ((y >> 5) << 7) | (y & 31u);
+            if (q & 1) { u.z = x; u.w = syn[p].y; } else { u.x = x; u.y = syn[p].y; }
+            continue;
+        }
+        unsigned step = fill[r][j] == 0 ? 0u : y - ylast[(size_t)r * n + j];
+        ylast[(size_t)r * n + j] = y;
+        for (;;) {
+            const int q = fill[r][j]++;
+            const long long g = start + (long long)(q >> 3) * 96 + l;
+            const unsigned st = std::min(step, 65535u);
+            comp(pin[g + 64], (q & 7) >> 1) |= (q & 1) ? st << 16 : st;
+            if (step <= 65535u) {
+                comp(pin[g + (q & 4 ? 32 : 0)], q & 3) = syn[p].y;
+                break;
+            }
+            step -= 65535u;                               // a filler: weight 0
+        }
     }
     sn_status s;
+    const size_t bytes = (size_t)tot * 16;
+    if (c->pin && c->pin_cap < bytes) { dfree(c, c->pin); c->pin = nullptr; }
     if (!c->pin) {
-        if ((s = dalloc(c, &c->pin, (size_t)(total > 0 ? total : 1) * 16)) ||
-            (s = dalloc(c, &c->pin_off, (size_t)slices * 8)) || (s = dalloc(c, &c->pin_len, (size_t)n * 4)) ||
-            (s = dalloc(c, &c->pin_len1, (size_t)n * 4)))
+        if ((s = dalloc(c, &c->pin, bytes))) return s;
+        c->pin_cap = bytes;
+    }
+    if (!c->pin_off) {
+        if ((s = dalloc(c, &c->pin_off, (size_t)slices * 8)) || (s = dalloc(c, &c->pin_len, (size_t)n * 4)) ||
+            (s = dalloc(c, &c->pin_len1, (size_t)n * 4)) || (s = dalloc(c, &c->pin_y0, (size_t)n * 8)))
             return s;
     }
-    SN_CUDA(c, cudaMemcpy(c->pin, pin.data(), (size_t)(total > 0 ? total : 1) * 16, cudaMemcpyHostToDevice));
-    SN_CUDA(c, cudaMemcpy(c->pin_off, off.data(), (size_t)slices * 8, cudaMemcpyHostToDevice));
-    SN_CUDA(c, cudaMemcpy(c->pin_len, lenA.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
-    SN_CUDA(c, cudaMemcpy(c->pin_len1, lenB.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
+    const std::vector<int> &lA = f ? lenc[0] : len[0], &lB = f ? lenc[1] : len[1];
+    SN_CUDA(c, cudaMemcpy(c->pin, pin.data(), bytes, cudaMemcpyHostToDevice));
+    SN_CUDA(c, cudaMemcpy(c->pin_off, off[f].data(), (size_t)slices * 8, cudaMemcpyHostToDevice));
+    SN_CUDA(c, cudaMemcpy(c->pin_len, lA.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
+    SN_CUDA(c, cudaMemcpy(c->pin_len1, lB.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
+    SN_CUDA(c, cudaMemcpy(c->pin_y0, y0.data(), (size_t)n * 8, cudaMemcpyHostToDevice));
+    c->pin_coded = f;
+    c->pin_bytes = (long long)bytes;
+    c->pin_entries = 0;
+    for (int j = 0; j < n; ++j) c->pin_entries += (long long)lA[j] + lB[j];
     c->pin_stale = false;
     return SN_OK;
 }
@@ -302,6 +373,7 @@ sn_status sn_create(const sn_config *cfg, const sn_neurons *nr, const sn_synapse
     c->D = cfg->max_delay;
     c->D1 = c->D + 1;
     c->flags = cfg->flags;
+    c->pin_format = (cfg->flags & SN_PULL_CODED) ? 2 : (cfg->flags & SN_PULL_PLAIN) ? 1 : 0;
     c->m = m;
     c->all_delay_one = all1;
     c->stream = (cudaStream_t)cfg->cuda_stream;
@@ -455,7 +527,8 @@ sn_status sn_create_dense(const sn_config *cfg, const sn_neurons *nr, const floa
     if (s) return s;
     if (!nr || !out) return fail(nullptr, SN_EINVAL, "NULL argument");
     if (cfg->dtype != SN_F32) return fail(nullptr, SN_EUNSUPPORTED, "dense networks are SN_F32 only");
-    if (cfg->flags & SN_PROP_PULL) return fail(nullptr, SN_EUNSUPPORTED, "SN_PROP_PULL applies to sn_create networks");
+    if (cfg->flags & (SN_PROP_PULL | SN_PULL_STORE_MASK))
+        return fail(nullptr, SN_EUNSUPPORTED, "SN_PROP_PULL and SN_PULL_* apply to sn_create networks");
     const int n = nr->n;
     if (n < 1 || n > 200000) return fail(nullptr, SN_EINVAL, "dense n must be in 1 .. 200000");
     if (delay < 1 || delay > cfg->max_delay) return fail(nullptr, SN_EINVAL, "delay outside 1..max_delay");
@@ -722,12 +795,13 @@ sn_status sn_run(sn_ctx *c, int32_t steps) {
             if (st) return st;
         }
         a.pin = c->pin; a.pin_off = c->pin_off; a.pin_len = c->pin_len; a.pin_len1 = c->pin_len1;
+        a.pin_y0 = c->pin_y0;
         a.ring_until = (int)std::min<long long>(c->ring_live_until, 2147483647ll);
         a.hL = c->pull_rows;
         a.chunk = c->pull_chunk;
         a.j_first = c->shard_end ? c->shard_first : 0;
         a.j_end = c->shard_end ? c->shard_end : c->n;
-        e = launch_sparse_pull(a, c->dtype, c->pull_grid, c->pull_smem, c->stream);
+        e = launch_sparse_pull(a, c->dtype, c->pin_coded != 0, c->pull_grid, c->pull_smem, c->stream);
         if (e != cudaSuccess) return cuda_fail(c, e, "simulation launch");
         c->hist_live = true;
     } else {
@@ -1138,6 +1212,16 @@ sn_status sn_set_propagation(sn_ctx *c, int32_t mode) {
 sn_status sn_get_propagation(const sn_ctx *c, int32_t *mode) {
     if (!c || !mode) return SN_EINVAL;
     *mode = (c->kind == KIND_SPARSE && c->prop_pull && !c->stdp) ? SN_PULL : SN_PUSH;
+    return SN_OK;
+}
+
+sn_status sn_pull_store_info(const sn_ctx *c, int32_t *format, int64_t *bytes, int64_t *entries) {
+    if (!c) return fail(nullptr, SN_EINVAL, "ctx is NULL");
+    if (c->kind != KIND_SPARSE) return fail(nullptr, SN_EINVAL, "not a sparse network");
+    const bool built = c->pin != nullptr && c->pin_bytes > 0;
+    if (format) *format = !built ? 0 : c->pin_coded ? (int32_t)SN_PULL_CODED : (int32_t)SN_PULL_PLAIN;
+    if (bytes) *bytes = built ? c->pin_bytes : 0;
+    if (entries) *entries = built ? c->pin_entries : 0;
     return SN_OK;
 }
 

@@ -41,6 +41,11 @@ struct sn_ctx {
     long long *pin_off = nullptr;
     int *pin_len = nullptr;            // synapses of delay >= 2 of each neuron
     int *pin_len1 = nullptr;           // synapses of delay 1 of each neuron
+    unsigned *pin_y0 = nullptr;        // coded store: [2][n] bit offset of each region's first entry
+    size_t pin_cap = 0;                // bytes allocated for pin
+    int pin_coded = 0;                 // 1: the store holds 16-bit offset steps (coded form)
+    int pin_format = 0;                // 0 = the smaller of the two forms, 1 = plain, 2 = coded
+    long long pin_bytes = 0, pin_entries = 0;   // store size; entries incl. padding and gap fillers
     bool pin_stale = true;             // the pull store must be (re)built from the CSR
     unsigned *hist = nullptr;          // [D][words] spike bits whose deliveries may be due
     bool hist_live = false;            // hist may hold spikes not yet delivered

@@ -66,11 +66,13 @@ struct NetArgs {
     const uint2 *csc;                 // {pre, CSR position}
     void *ring;                       // [D1][n] pending input (int64 fixed point / int32 / float)
     // sparse store for pull propagation (sn_pull.cu): incoming synapses of
-    // 32-neuron slices, pairs {pre | (delay-1) << 26, weight bits} x 2
+    // 32-neuron slices, plain ({bit offset, weight bits} pairs) or coded
+    // (groups of 8 weights and 16-bit offset steps)
     const uint4 *pin;
     const long long *pin_off;         // [slices] first uint4 of each slice
     const int *pin_len;               // [n] incoming synapses of delay >= 2 of each neuron
     const int *pin_len1;              // [n] incoming synapses of delay 1 (the region after them)
+    const unsigned *pin_y0;           // coded store: [2][n] window bit offset of each region's first entry
     unsigned *hist;                   // [hD][words] spike bits of step tau in row tau % hD
     int hD;                           // history depth (the maximum delay D)
     int hL;                           // rows of the pull kernel's shared-memory window
@@ -215,7 +217,7 @@ cudaError_t plan_pull(int n, int D, long long m, int *grid, int *chunk, int *row
                       int own_slices = -1);
 cudaError_t launch_shard_put(unsigned *hist, unsigned *raster, int D, int cap, int words, int w0, int w1,
                              long long t0, int rows, const unsigned *src, cudaStream_t s);
-cudaError_t launch_sparse_pull(const NetArgs &a, int dtype, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_sparse_pull(const NetArgs &a, int dtype, bool coded, int grid, size_t smem, cudaStream_t s);
 cudaError_t launch_pull_flush(const NetArgs &a, int dtype, int t0, cudaStream_t s);
 cudaError_t launch_gather_weights(const uint2 *syn, const long long *perm_inv, long long m,
                                   float *out, cudaStream_t s);

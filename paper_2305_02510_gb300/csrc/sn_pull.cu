@@ -7,13 +7,20 @@
 // at position tau - base.  Each thread owns one neuron, holds its state in
 // registers and walks the neuron's incoming synapses in descending delay,
 // then ascending pre and input index (the oldest spikes first), testing the
-// bit of pre at step t - d and adding the weight.  A synapse is stored as x = e << 7 | (pre & 31) with
-// e = (D - d) * Wp + pre / 32, the word offset of its bit from the row of step
-// t - D, so that a test is one shift, one shared load and one funnel shift.
-// The synapses of 32 consecutive neurons form a slice (one warp): entry q of
-// lane l sits in pair q / 2 of the slice, so that each 16-byte load of a warp
-// reads 512 contiguous bytes.  Unused halves of a pair are all-zero entries,
-// which add +0 (an exact no-op: the sum starts at +0 and is never -0).  In
+// bit of pre at step t - d and adding the weight.  That bit lies
+// y = (D - d) * Wp * 32 + pre bits after the row of step t - D, and y never
+// decreases along a neuron's list.  The synapses of 32 consecutive neurons
+// form a slice (one warp), stored in one of two forms (built on the host):
+//  - plain, 8 bytes a synapse: x = (y / 32) << 7 | y % 32 and the weight bits;
+//    entry q of lane l sits in pair q / 2 of the slice, so that each 16-byte
+//    load of a warp reads 512 contiguous bytes; a test is one shift, one
+//    shared load and one funnel shift;
+//  - coded, 6 bytes a synapse: groups of 8 entries, each group three 16-byte
+//    loads of the lane (weights 0-3, weights 4-7, the eight 16-bit steps of y),
+//    y running from the region's first offset; a step above 65535 is split
+//    over filler entries of weight 0.
+// Unused entries and fillers add +0 (an exact no-op: the sum starts at +0 and
+// is never -0), at offsets inside the window.  In
 // SN_F32 mode the sum is a float accumulation in that order, the FP32
 // mirror's order, so the state does not depend on thread timing and matches
 // the mirror bit for bit.
@@ -40,6 +47,7 @@ namespace {
 
 constexpr int kPullUnroll = 4;      // 16-byte loads (two synapses each) per half of the double buffer
 constexpr int kPullMaxBlock = 1024;
+constexpr int kPullDepth = 2;       // units' buffers in rotation (one unit's loads ahead of its use)
 
 template <int MODE> struct PullAcc;
 template <> struct PullAcc<SN_F32> {
@@ -77,24 +85,95 @@ __device__ __forceinline__ void pull_load(uint4 (&e)[kPullUnroll], const uint4 *
 }
 
 
-// The synapses [0, np) of one region (np per lane, npmax the warp's largest)
-// added to acc; e0 holds the region's first kPullUnroll pairs on entry and
-// nothing useful on exit.
-template <int MODE>
-__device__ __forceinline__ void pull_region(typename PullAcc<MODE>::T &acc, uint4 (&e0)[kPullUnroll],
-                                            uint4 (&e1)[kPullUnroll], const uint4 *ent, int np, int npmax,
-                                            const unsigned char *win, unsigned row0) {
-    constexpr int P = kPullUnroll;
-    for (int p0 = 0; p0 < npmax; p0 += 2 * P) {
-        pull_load(e1, ent, p0 + P, np);
-        pull_batch<MODE>(acc, e0, win, row0);
-        pull_load(e0, ent, p0 + 2 * P, np);
-        pull_batch<MODE>(acc, e1, win, row0);
+// Coded store: a group of 8 synapses is three uint4s of a lane (weights 0-3,
+// weights 4-7, eight 16-bit offset steps), 96 uint4s apart per group in a
+// slice; y is the synapse's bit offset from the start of the window.
+constexpr int kCodedBuf = 3;
+
+__device__ __forceinline__ void coded_load(uint4 (&e)[kCodedBuf], const uint4 *ent, int g, int ng) {
+    if (g < ng) {
+        const uint4 *p = ent + (size_t)g * 96;
+        e[0] = __ldg(p);
+        e[1] = __ldg(p + 32);
+        e[2] = __ldg(p + 64);
+    } else {
+        e[0] = e[1] = e[2] = make_uint4(0u, 0u, 0u, 0u);
     }
 }
 
 template <int MODE>
+__device__ __forceinline__ void coded_one(typename PullAcc<MODE>::T &acc, unsigned &y, unsigned step,
+                                          unsigned wbits, const unsigned char *win) {
+    y += step;
+    const unsigned word = *(const unsigned *)(win + ((y >> 3) & ~3u));
+    if (__funnelshift_r(word, word, y) & 1u) acc = PullAcc<MODE>::add(acc, wbits);
+}
+
+template <int MODE>
+__device__ __forceinline__ void coded_batch(typename PullAcc<MODE>::T &acc, unsigned &y,
+                                            const uint4 (&e)[kCodedBuf], const unsigned char *win) {
+    coded_one<MODE>(acc, y, e[2].x & 0xffffu, e[0].x, win);
+    coded_one<MODE>(acc, y, e[2].x >> 16, e[0].y, win);
+    coded_one<MODE>(acc, y, e[2].y & 0xffffu, e[0].z, win);
+    coded_one<MODE>(acc, y, e[2].y >> 16, e[0].w, win);
+    coded_one<MODE>(acc, y, e[2].z & 0xffffu, e[1].x, win);
+    coded_one<MODE>(acc, y, e[2].z >> 16, e[1].y, win);
+    coded_one<MODE>(acc, y, e[2].w & 0xffffu, e[1].z, win);
+    coded_one<MODE>(acc, y, e[2].w >> 16, e[1].w, win);
+}
+
+// The two forms behind one interface.  A unit is what one batch of loads
+// brings in: four pairs (plain; np counts pairs) or a group of 8 (coded; np
+// counts groups).  A region is summed with DEPTH units' buffers in rotation,
+// DEPTH - 1 units ahead of their use.
+template <bool CODED> constexpr int kUnitRegs = CODED ? kCodedBuf : kPullUnroll;
+
+template <bool CODED>
+__device__ __forceinline__ void unit_load(uint4 (&e)[kUnitRegs<CODED>], const uint4 *ent, int u, int np) {
+    if constexpr (CODED) coded_load(e, ent, u, np);
+    else pull_load(e, ent, u * kPullUnroll, np);
+}
+
+template <int MODE, bool CODED>
+__device__ __forceinline__ void unit_sum(typename PullAcc<MODE>::T &acc, unsigned &y,
+                                         const uint4 (&e)[kUnitRegs<CODED>], const unsigned char *win,
+                                         unsigned row0) {
+    if constexpr (CODED) coded_batch<MODE>(acc, y, e, win);
+    else pull_batch<MODE>(acc, e, win, row0);
+}
+
+template <bool CODED>
+__device__ __forceinline__ int region_units(int np) { return CODED ? np : (np + kPullUnroll - 1) / kPullUnroll; }
+
+// The first DEPTH - 1 units of a region into buffers 0 .. DEPTH - 2.
+template <bool CODED, int DEPTH>
+__device__ __forceinline__ void region_start(uint4 (&e)[DEPTH][kUnitRegs<CODED>], const uint4 *ent, int np) {
+#pragma unroll
+    for (int k = 0; k + 1 < DEPTH; ++k) unit_load<CODED>(e[k], ent, k, np);
+}
+
+// The region's synapses added to acc (np per lane, npmax the warp's largest),
+// the first entry at bit y0 after byte row0 of the window (coded form);
+// region_start has filled the buffers on entry, which hold nothing useful on
+// exit.
+template <int MODE, bool CODED, int DEPTH>
+__device__ __forceinline__ void region_sum(typename PullAcc<MODE>::T &acc, uint4 (&e)[DEPTH][kUnitRegs<CODED>],
+                                           const uint4 *ent, int np, int npmax, const unsigned char *win,
+                                           unsigned row0, unsigned y0) {
+    unsigned y = row0 * 8u + y0;
+    const int umax = region_units<CODED>(npmax);
+    for (int u0 = 0; u0 < umax; u0 += DEPTH) {
+#pragma unroll
+        for (int k = 0; k < DEPTH; ++k) {
+            unit_load<CODED>(e[(k + DEPTH - 1) % DEPTH], ent, u0 + k + DEPTH - 1, np);
+            unit_sum<MODE, CODED>(acc, y, e[k], win, row0);
+        }
+    }
+}
+
+template <int MODE, bool CODED>
 __global__ void __launch_bounds__(kPullMaxBlock, 1) sparse_pull_kernel(NetArgs a) {
+    constexpr int DEPTH = kPullDepth;
     using V = typename Tr<MODE>::V;
     using Acc = typename PullAcc<MODE>::T;
     extern __shared__ uint4 s_win4[];                 // [hL][Wp] words
@@ -114,7 +193,7 @@ __global__ void __launch_bounds__(kPullMaxBlock, 1) sparse_pull_kernel(NetArgs a
     const int wbase = j - lane;                       // first neuron of this warp's slice
     V v = 0, th = 0, lk = 0, rs = 0, amp = 0;
     int rr = 0, R = 0, npA = 0, npB = 0;
-    unsigned thr = 0;
+    unsigned thr = 0, yA = 0, yB = 0;
     unsigned long long outdeg = 0;
     const uint4 *ent = a.pin;
     if (mine) {
@@ -126,37 +205,41 @@ __global__ void __launch_bounds__(kPullMaxBlock, 1) sparse_pull_kernel(NetArgs a
         R = a.R[j];
         thr = a.prate[j];
         amp = ((const V *)a.pamp)[j];
-        npA = (a.pin_len[j] + 1) >> 1;
-        npB = (a.pin_len1[j] + 1) >> 1;
+        // units of the store per region: pairs (plain) or groups of 8 (coded)
+        npA = CODED ? (a.pin_len[j] + 7) >> 3 : (a.pin_len[j] + 1) >> 1;
+        npB = CODED ? (a.pin_len1[j] + 7) >> 3 : (a.pin_len1[j] + 1) >> 1;
+        if (CODED) {
+            yA = a.pin_y0[j];
+            yB = a.pin_y0[(size_t)a.n + j];
+        }
         outdeg = (unsigned long long)(a.rowptr[j + 1] - a.rowptr[j]);
         ent = a.pin + a.pin_off[j >> 5] + lane;
     }
-    // pairs of the warp's longest list in each region; the delay-1 region
+    // units of the warp's longest list in each region; the delay-1 region
     // starts after the slice's delay->=2 region
     const int npAmax = __reduce_max_sync(0xffffffffu, npA);
     const int npBmax = __reduce_max_sync(0xffffffffu, npB);
-    const uint4 *entB = ent + (size_t)npAmax * 32;
+    const uint4 *entB = ent + (size_t)npAmax * (CODED ? 96 : 32);
     using RA = typename Tr<MODE>::A;
     RA *ring = (RA *)a.ring;
     unsigned long long my_spikes = 0, my_events = 0;
     bool overflow = false;
-    // synapse loads run one half (four pairs) ahead of their use
-    constexpr int P = kPullUnroll;
-    uint4 ea[P], eb[P];
-    pull_load(ea, ent, 0, npA);
+    // synapse loads run one half (four pairs or a group of 8) ahead of their use
+    uint4 e[DEPTH][kUnitRegs<CODED>];
+    region_start<CODED, DEPTH>(e, ent, npA);
     __syncthreads();
     // the delay >= 2 part of the first step: every row it reads is in the window
     Acc acc = 0;
     if (a.steps > 0) {
-        pull_region<MODE>(acc, ea, eb, ent, npA, npAmax, win, (unsigned)((a.t0 - base - D) * Wp) * 4u);
-        pull_load(ea, entB, 0, npB);
+        region_sum<MODE, CODED, DEPTH>(acc, e, ent, npA, npAmax, win, (unsigned)((a.t0 - base - D) * Wp) * 4u, yA);
+        region_start<CODED, DEPTH>(e, entB, npB);
     }
     for (int s = 0; s < a.steps; ++s) {
         const int t = a.t0 + s;
         const unsigned row0 = (unsigned)((t - base - D) * Wp) * 4u;
         bool fire = false;
         // the delay-1 part: row t - 1 is in the window
-        pull_region<MODE>(acc, ea, eb, entB, npB, npBmax, win, row0);
+        region_sum<MODE, CODED, DEPTH>(acc, e, entB, npB, npBmax, win, row0, yB);
         if (mine) {
             // input still pending in the ring from an earlier push run
             V ring_in = 0;
@@ -215,7 +298,7 @@ __global__ void __launch_bounds__(kPullMaxBlock, 1) sparse_pull_kernel(NetArgs a
         int stop_early = 0;
         if (threadIdx.x == 0 && gridDim.x == 1) stop_early = ld_status(a.ctl);
         // the first synapses of step t + 1 (the store is static)
-        pull_load(ea, ent, 0, npA);
+        region_start<CODED, DEPTH>(e, ent, npA);
         int pos = t - base;                           // window position of row t
         if (pos >= L) {
             // rows t-D+1 .. t-1 move down by sh = pos - D + 1 rows to positions
@@ -247,8 +330,9 @@ __global__ void __launch_bounds__(kPullMaxBlock, 1) sparse_pull_kernel(NetArgs a
         // window) while the other blocks arrive; then the first delay-1 loads
         acc = 0;
         if (s + 1 < a.steps) {
-            pull_region<MODE>(acc, ea, eb, ent, npA, npAmax, win, (unsigned)((t + 1 - base - D) * Wp) * 4u);
-            pull_load(ea, entB, 0, npB);
+            region_sum<MODE, CODED, DEPTH>(acc, e, ent, npA, npAmax, win,
+                                           (unsigned)((t + 1 - base - D) * Wp) * 4u, yA);
+            region_start<CODED, DEPTH>(e, entB, npB);
         }
         if (threadIdx.x == 0) {
             s_ok = gridDim.x > 1 ? bar_wait(a.ctl, gen) : 1;
@@ -326,8 +410,12 @@ __global__ void shard_put_kernel(unsigned *hist, unsigned *raster, int D, int ca
     }
 }
 
-const void *pull_fn(int dtype) {
-    return dtype == SN_F32 ? (const void *)sparse_pull_kernel<SN_F32> : (const void *)sparse_pull_kernel<SN_I32>;
+const void *pull_fn(int dtype, bool coded) {
+    if (coded)
+        return dtype == SN_F32 ? (const void *)sparse_pull_kernel<SN_F32, true>
+                               : (const void *)sparse_pull_kernel<SN_I32, true>;
+    return dtype == SN_F32 ? (const void *)sparse_pull_kernel<SN_F32, false>
+                           : (const void *)sparse_pull_kernel<SN_I32, false>;
 }
 
 }  // namespace
@@ -352,11 +440,13 @@ cudaError_t plan_pull(int n, int D, long long m, int *grid, int *chunk, int *row
     const long long per = (sl * 32 <= kPullMaxBlock && m <= 65536) ? sl : (sl + sms - 1) / sms;
     if (per * 32 > kPullMaxBlock) return cudaSuccess;
     const long long bytes = L * wp * 4;
-    for (const void *fn : {pull_fn(SN_F32), pull_fn(SN_I32)}) {
+    const int block = (int)(per * 32);
+    for (const void *fn : {pull_fn(SN_F32, false), pull_fn(SN_I32, false), pull_fn(SN_F32, true),
+                           pull_fn(SN_I32, true)}) {
         e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
         if (e != cudaSuccess) return e;
         int p = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, fn, (int)(per * 32), (size_t)bytes);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&p, fn, block, (size_t)bytes);
         if (e != cudaSuccess) return e;
         if (p < 1) return cudaSuccess;
     }
@@ -367,9 +457,9 @@ cudaError_t plan_pull(int n, int D, long long m, int *grid, int *chunk, int *row
     return cudaSuccess;
 }
 
-cudaError_t launch_sparse_pull(const NetArgs &a, int dtype, int grid, size_t smem, cudaStream_t s) {
+cudaError_t launch_sparse_pull(const NetArgs &a, int dtype, bool coded, int grid, size_t smem, cudaStream_t s) {
     void *args[] = {(void *)&a};
-    const void *fn = pull_fn(dtype);
+    const void *fn = pull_fn(dtype, coded);
     // the grid barrier's arrival count starts every launch at zero
     cudaError_t e = cudaMemsetAsync(&a.ctl->bar, 0, sizeof(GridBarrier), s);
     if (e != cudaSuccess) return e;

@@ -30,6 +30,10 @@ def main():
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--propagation", choices=["push", "pull"], default="push",
                     help="large-sparse: push or pull propagation")
+    ap.add_argument("--pull-form", choices=["auto", "plain", "coded"], default="auto",
+                    help="large-sparse with pull: the pull store's form (SN_PULL_PLAIN / SN_PULL_CODED)")
+    ap.add_argument("--synapses-per-neuron", type=int, default=100,
+                    help="large-sparse: incoming synapses per neuron (k)")
     ap.add_argument("--dense-slab", type=int, default=0, choices=[0, 1, 2, 4, 8],
                     help="large-dense: column slab of 32 * k columns per block (SN_DENSE_SLAB; 0 = the library's choice)")
     args = ap.parse_args()
@@ -56,7 +60,8 @@ def main():
         print(json.dumps({"workload": wl_name, "ms": 1e3 * min(times)}))
         return
     if wl_name == "large-sparse":
-        ctx = S.from_workload(W.large_sparse(steps=T), record_steps=T, stream=stream.cuda_stream)
+        form = {"auto": 0, "plain": S.SN_PULL_PLAIN, "coded": S.SN_PULL_CODED}[args.pull_form]
+        ctx = S.from_workload(W.large_sparse(k=args.synapses_per_neuron, steps=T), record_steps=T, stream=stream.cuda_stream, flags=form)
         S.sn_set_propagation(ctx, S.SN_PULL if args.propagation == "pull" else S.SN_PUSH)
     elif wl_name in ("large-dense", "large-dense-stdp"):
         n = int(16384 * args.scale) // 32 * 32
@@ -79,7 +84,10 @@ def main():
         S.sn_sync(ctx)
         times.append(a.elapsed_time(b))
     steps, spikes, events = S.sn_get_counters(ctx)
-    print(json.dumps({"workload": wl_name, "steps": T, "ms": min(times), "spikes": spikes, "events": events}))
+    out = {"workload": wl_name, "steps": T, "ms": min(times), "spikes": spikes, "events": events}
+    if wl_name == "large-sparse" and args.propagation == "pull":
+        out["pull_store"] = dict(zip(("format", "bytes", "entries"), S.sn_pull_store_info(ctx)))
+    print(json.dumps(out))
 
 
 if __name__ == "__main__":

@@ -21,6 +21,7 @@ SN_OK, SN_EINVAL, SN_ENOMEM, SN_ECUDA, SN_ESTATE, SN_ETIMEOUT, SN_EUNSUPPORTED, 
 SN_F32, SN_I32 = 0, 1
 SN_AUTO, SN_EXEC_CTA, SN_EXEC_GRID, SN_PROP_PULL, SN_FF_RECOMPUTE = 0, 1, 2, 4, 8
 SN_PUSH, SN_PULL = 0, 1
+SN_PULL_PLAIN, SN_PULL_CODED = 0x1000, 0x2000
 
 
 def SN_DENSE_SLAB(k: int) -> int:
@@ -121,6 +122,7 @@ def lib():
                                     C.POINTER(C.c_int64)],
                 "sn_set_propagation": [_P, C.c_int32],
                 "sn_get_propagation": [_P, C.POINTER(C.c_int32)],
+                "sn_pull_store_info": [_P, C.POINTER(C.c_int32), C.POINTER(C.c_int64), C.POINTER(C.c_int64)],
                 "sn_save": [_P, _P, C.POINTER(C.c_size_t)],
                 "sn_load": [_P, _P, C.c_size_t],
                 "sn_selftest_barrier_timeout": [_P, C.POINTER(C.c_int32)],
@@ -407,6 +409,14 @@ def sn_get_propagation(ctx: Ctx) -> int:
     m = C.c_int32(0)
     _check(lib().sn_get_propagation(ctx.handle, C.byref(m)), ctx)
     return m.value
+
+
+def sn_pull_store_info(ctx: Ctx):
+    """(format, bytes, entries) of a sparse context's pull store: format 0 (not
+    built), SN_PULL_PLAIN or SN_PULL_CODED."""
+    f, b, e = C.c_int32(0), C.c_int64(0), C.c_int64(0)
+    _check(lib().sn_pull_store_info(ctx.handle, C.byref(f), C.byref(b), C.byref(e)), ctx)
+    return f.value, b.value, e.value
 
 
 def split_batch_raster(bits, net_n):

@@ -273,7 +273,9 @@ def _dense(S, n=4, delay=1, D=2, dtype=0, wval=0.5, flags=0):
     (dict(delay=3), "SN_EINVAL", "delay"),
     (dict(wval=float("inf")), "SN_EINVAL", "weight"),
     (dict(flags=3 << 8), "SN_EINVAL", "SN_DENSE_SLAB"),
-    (dict(flags=16 << 8), "SN_EINVAL", "flags"),
+    (dict(flags=64 << 8), "SN_EINVAL", "flags"),
+    (dict(flags=0x1000), "SN_EUNSUPPORTED", "SN_PULL_"),
+    (dict(flags=0x3000), "SN_EINVAL", "exclusive"),
 ])
 def test_dense_rejects_bad_arguments(S, kw, status, frag):
     st, msg = _dense(S, **kw)
