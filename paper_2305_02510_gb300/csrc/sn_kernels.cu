@@ -143,8 +143,10 @@ __global__ void __launch_bounds__(kBlock) sparse_kernel(NetArgs a) {
                     const int pre = (int)c.x;
                     if (spiked(rrow, pre)) continue;
                     const float dw = __fmul_rn(a.a_plus, xo[pre]);
-                    float w = __uint_as_float(a.syn[c.y].y);
-                    a.syn[c.y].y = __float_as_uint(clampf(__fadd_rn(w, dw), a.wmin, a.wmax));
+                    const float w = ld_scattered((const float *)&a.syn[c.y] + 1);
+                    const float nw = clampf(__fadd_rn(w, dw), a.wmin, a.wmax);
+                    // an update that rounds back to the same bits leaves the sector clean
+                    if (__float_as_uint(nw) != __float_as_uint(w)) a.syn[c.y].y = __float_as_uint(nw);
                 }
             }
         } else {
@@ -546,10 +548,14 @@ __global__ void __launch_bounds__(kBlock, CPL <= 2 ? 4 : 3) dense_kernel(NetArgs
     using Gm = VecGeom<CPL>;
     int *wpre = smem;                                  // [words + 1]
     int *list = smem + a.words + 1;                    // [kDListMax]
+    // the spike-bit row of the step, read once from global memory
+    unsigned *s_bits = (unsigned *)(smem + a.words + 1 + kDListMax);   // [words]
     // [nwarp][cw], vector path [nwarp][RPI][cw]; 16-byte aligned
-    float *wpart = (float *)(smem + ((a.words + 1 + kDListMax + 3) & ~3));
+    float *wpart = (float *)(smem + ((2 * a.words + 1 + kDListMax + 3) & ~3));
     __shared__ int s_scan[kBlock / 32];
     __shared__ int s_stop;
+    __shared__ float s_x[STDP ? kBlock : 1];           // pre-step traces of the slab's neurons
+    __shared__ float s_carry[kBlock];                  // delay 1: the fold of the last step
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n = a.n;
     const int c0 = blockIdx.x * cw;
@@ -574,17 +580,25 @@ __global__ void __launch_bounds__(kBlock, CPL <= 2 ? 4 : 3) dense_kernel(NetArgs
         s_amp[threadIdx.x] = ((const float *)a.pamp)[j];
     }
     unsigned long long my_spikes = 0;
+    // with delay 1 the input of step t + 1 is this thread's own fold of step
+    // t (kept in shared memory), and the pre-step trace its own update's (in
+    // a register); both are also stored for the next launch
+    float x_own = 0.0f;
+    // a status latched by another block is read once per step without
+    // waiting for it, and acted on at the end of the step
+    int st = 0;
+    if (threadIdx.x == 0) s_stop = ld_status(a.ctl);
+    __syncthreads();
+    if (s_stop) return;
 
     for (int s = 0; s < a.steps; ++s) {
-        if (threadIdx.x == 0) s_stop = ld_status(a.ctl);
-        __syncthreads();
-        if (s_stop) break;
+        if (threadIdx.x == 0) st = ld_status(a.ctl);
         const int t = a.t0 + s;
         const int cur = t % a.D1;
         // ---- update(t)
         bool fire = false;
         if (mine) {
-            const float acc = ring[(size_t)cur * n + j];
+            const float acc = (s > 0 && a.dense_delay == 1) ? s_carry[threadIdx.x] : ring[(size_t)cur * n + j];
             float ext = 0.0f;
             if (t < a.ev_nsteps) {
                 int lo = a.ev_off[t], hi = a.ev_off[t + 1];
@@ -600,8 +614,10 @@ __global__ void __launch_bounds__(kBlock, CPL <= 2 ? 4 : 3) dense_kernel(NetArgs
             fire = lif_update_f32(v, rr, acc, ext, s_th[threadIdx.x], s_lk[threadIdx.x], s_rs[threadIdx.x],
                                   s_R[threadIdx.x]);
             if constexpr (STDP) {
-                const float xo = a.trace[(size_t)((t + 2) % 3) * n + j];
-                a.trace[(size_t)(t % 3) * n + j] = __fadd_rn(__fmul_rn(a.decay, xo), fire ? 1.0f : 0.0f);
+                const float xo = s > 0 ? x_own : a.trace[(size_t)((t + 2) % 3) * n + j];
+                s_x[threadIdx.x] = xo;
+                x_own = __fadd_rn(__fmul_rn(a.decay, xo), fire ? 1.0f : 0.0f);
+                a.trace[(size_t)(t % 3) * n + j] = x_own;
             }
         }
         if (threadIdx.x < cw) {
@@ -616,7 +632,12 @@ __global__ void __launch_bounds__(kBlock, CPL <= 2 ? 4 : 3) dense_kernel(NetArgs
         if (!grid_barrier(a.ctl)) break;
 
         // ---- gather(t): input of t + delay (and STDP of step t)
-        const unsigned *row_bits = a.spk + (size_t)(t & 1) * a.words;
+        {
+            const unsigned *g_bits = a.spk + (size_t)(t & 1) * a.words;
+            for (int w = threadIdx.x; w < a.words; w += blockDim.x) s_bits[w] = g_bits[w];
+            __syncthreads();
+        }
+        const unsigned *row_bits = s_bits;
         popcount_prefix(row_bits, a.words, wpre, s_scan);
         const int k = wpre[a.words];
         const float *xo = STDP ? a.trace + (size_t)((t + 2) % 3) * n : nullptr;   // x(t-1)
@@ -632,7 +653,7 @@ __global__ void __launch_bounds__(kBlock, CPL <= 2 ? 4 : 3) dense_kernel(NetArgs
             const int col = c0 + lane + 32 * q;
             sc[q] = false;
             xc[q] = 0.0f;
-            if (STDP && col < n) { sc[q] = spiked(row_bits, col); xc[q] = xo[col]; }
+            if (STDP && col < n) { sc[q] = spiked(row_bits, col); xc[q] = s_x[lane + 32 * q]; }
         }
         for (int base = 0; base < k; base += kDListMax) {
             const int cnt = min(kDListMax, k - base);
@@ -662,6 +683,47 @@ __global__ void __launch_bounds__(kBlock, CPL <= 2 ? 4 : 3) dense_kernel(NetArgs
                     for (int u = 0; u < RF; ++u)
 #pragma unroll
                         for (int q = 0; q < CPL; ++q) acc[q] = __fadd_rn(acc[q], w16[u][q]);
+                }
+            }
+            if constexpr (STDP) {
+                // up to RS spiking rows per warp in flight: their slab weights
+                // and pre traces are loaded together, then each row in turn is
+                // updated, written back and added (the order of the sum); the
+                // loop takes every row, so the one-row loop below has none left
+                constexpr int RS = CPL >= 4 ? 2 : 8 / CPL;
+                for (; r < cnt; r += RS * nwarp) {
+                    float wv[RS][CPL], xr[RS];
+                    int ir[RS];
+#pragma unroll
+                    for (int u = 0; u < RS; ++u) {
+                        const bool ok = r + u * nwarp < cnt;
+                        ir[u] = ok ? list[r + u * nwarp] : -1;
+                        xr[u] = ok ? xo[ir[u]] : 0.0f;
+                        const float *row = a.W + (size_t)(ok ? ir[u] : 0) * n;
+#pragma unroll
+                        for (int q = 0; q < CPL; ++q) {
+                            const int col = c0 + lane + 32 * q;
+                            wv[u][q] = (ok && col < n) ? row[col] : 0.0f;
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < RS; ++u) {
+                        if (ir[u] < 0) break;
+                        float *row = a.W + (size_t)ir[u] * n;
+#pragma unroll
+                        for (int q = 0; q < CPL; ++q) {
+                            const int col = c0 + lane + 32 * q;
+                            if (col >= n) continue;
+                            float w = wv[u][q];
+                            if (col != ir[u]) {
+                                float dw = sc[q] ? __fmul_rn(a.a_plus, xr[u]) : 0.0f;
+                                dw = __fsub_rn(dw, __fmul_rn(a.a_minus, xc[q]));
+                                w = clampf(__fadd_rn(w, dw), a.wmin, a.wmax);
+                                row[col] = w;
+                            }
+                            acc[q] = __fadd_rn(acc[q], w);
+                        }
+                    }
                 }
             }
             for (; r < cnt; r += nwarp) {
@@ -702,7 +764,7 @@ __global__ void __launch_bounds__(kBlock, CPL <= 2 ? 4 : 3) dense_kernel(NetArgs
 #pragma unroll
                             for (int h = 0; h < 2; ++h) {
                                 const int q = q0 + lane + 32 * h;
-                                val[u][h] = (act[u] && q < cnt) ? a.W[(size_t)i * n + list[q]] : 0.0f;
+                                val[u][h] = (act[u] && q < cnt) ? ld_scattered(a.W + (size_t)i * n + list[q]) : 0.0f;
                             }
                         }
 #pragma unroll
@@ -743,8 +805,11 @@ __global__ void __launch_bounds__(kBlock, CPL <= 2 ? 4 : 3) dense_kernel(NetArgs
 #pragma unroll
             for (int w = 0; w < parts; ++w) sum = __fadd_rn(sum, wpart[w * cw + threadIdx.x]);
             ring[(size_t)((t + a.dense_delay) % a.D1) * n + j] = sum;
+            s_carry[threadIdx.x] = sum;
         }
+        if (threadIdx.x == 0) s_stop = st;
         __syncthreads();
+        if (s_stop) break;
     }
     if (mine) {
         ((float *)a.V)[j] = v;
@@ -774,7 +839,7 @@ cudaError_t launch_barrier_selftest(Control *ctl, int blocks, cudaStream_t s) {
 // per warp for any CPL, as much as CPL = 4's scalar partials).
 static size_t dense_smem(int words, int cpl) {
     const size_t part = (size_t)(kBlock / 32) * 32 * (cpl > 4 ? cpl : 4) * sizeof(float);
-    return (size_t)((words + 1 + kDListMax + 3) & ~3) * sizeof(int) + part;
+    return (size_t)((2 * words + 1 + kDListMax + 3) & ~3) * sizeof(int) + part;
 }
 
 // vec: the vector gather (no STDP, n % 4 == 0, W 16-byte aligned)
