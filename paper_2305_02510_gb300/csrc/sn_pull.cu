@@ -47,7 +47,6 @@ namespace {
 
 constexpr int kPullUnroll = 4;      // 16-byte loads (two synapses each) per half of the double buffer
 constexpr int kPullMaxBlock = 1024;
-constexpr int kPullDepth = 2;       // units' buffers in rotation (one unit's loads ahead of its use)
 
 template <int MODE> struct PullAcc;
 template <> struct PullAcc<SN_F32> {
@@ -122,58 +121,61 @@ __device__ __forceinline__ void coded_batch(typename PullAcc<MODE>::T &acc, unsi
     coded_one<MODE>(acc, y, e[2].w >> 16, e[1].w, win);
 }
 
-// The two forms behind one interface.  A unit is what one batch of loads
-// brings in: four pairs (plain; np counts pairs) or a group of 8 (coded; np
-// counts groups).  A region is summed with DEPTH units' buffers in rotation,
-// DEPTH - 1 units ahead of their use.
-template <bool CODED> constexpr int kUnitRegs = CODED ? kCodedBuf : kPullUnroll;
-
-template <bool CODED>
-__device__ __forceinline__ void unit_load(uint4 (&e)[kUnitRegs<CODED>], const uint4 *ent, int u, int np) {
-    if constexpr (CODED) coded_load(e, ent, u, np);
-    else pull_load(e, ent, u * kPullUnroll, np);
-}
-
-template <int MODE, bool CODED>
-__device__ __forceinline__ void unit_sum(typename PullAcc<MODE>::T &acc, unsigned &y,
-                                         const uint4 (&e)[kUnitRegs<CODED>], const unsigned char *win,
-                                         unsigned row0) {
-    if constexpr (CODED) coded_batch<MODE>(acc, y, e, win);
-    else pull_batch<MODE>(acc, e, win, row0);
-}
-
-template <bool CODED>
-__device__ __forceinline__ int region_units(int np) { return CODED ? np : (np + kPullUnroll - 1) / kPullUnroll; }
-
-// The first DEPTH - 1 units of a region into buffers 0 .. DEPTH - 2.
-template <bool CODED, int DEPTH>
-__device__ __forceinline__ void region_start(uint4 (&e)[DEPTH][kUnitRegs<CODED>], const uint4 *ent, int np) {
-#pragma unroll
-    for (int k = 0; k + 1 < DEPTH; ++k) unit_load<CODED>(e[k], ent, k, np);
-}
-
-// The region's synapses added to acc (np per lane, npmax the warp's largest),
-// the first entry at bit y0 after byte row0 of the window (coded form);
-// region_start has filled the buffers on entry, which hold nothing useful on
-// exit.
-template <int MODE, bool CODED, int DEPTH>
-__device__ __forceinline__ void region_sum(typename PullAcc<MODE>::T &acc, uint4 (&e)[DEPTH][kUnitRegs<CODED>],
-                                           const uint4 *ent, int np, int npmax, const unsigned char *win,
-                                           unsigned row0, unsigned y0) {
-    unsigned y = row0 * 8u + y0;
-    const int umax = region_units<CODED>(npmax);
-    for (int u0 = 0; u0 < umax; u0 += DEPTH) {
-#pragma unroll
-        for (int k = 0; k < DEPTH; ++k) {
-            unit_load<CODED>(e[(k + DEPTH - 1) % DEPTH], ent, u0 + k + DEPTH - 1, np);
-            unit_sum<MODE, CODED>(acc, y, e[k], win, row0);
-        }
+// The synapses [0, np) of one region of the plain form (np pairs per lane,
+// npmax the warp's largest) added to acc; e0 holds the region's first
+// kPullUnroll pairs on entry and nothing useful on exit.
+template <int MODE>
+__device__ __forceinline__ void pull_region(typename PullAcc<MODE>::T &acc, uint4 (&e0)[kPullUnroll],
+                                            uint4 (&e1)[kPullUnroll], const uint4 *ent, int np, int npmax,
+                                            const unsigned char *win, unsigned row0) {
+    constexpr int P = kPullUnroll;
+    for (int p0 = 0; p0 < npmax; p0 += 2 * P) {
+        pull_load(e1, ent, p0 + P, np);
+        pull_batch<MODE>(acc, e0, win, row0);
+        pull_load(e0, ent, p0 + 2 * P, np);
+        pull_batch<MODE>(acc, e1, win, row0);
     }
+}
+
+// The same for the coded form: ng groups (the warp's largest ngmax), the
+// first entry at bit y0 after byte row0 of the window.
+template <int MODE>
+__device__ __forceinline__ void coded_region(typename PullAcc<MODE>::T &acc, uint4 (&e0)[kCodedBuf],
+                                             uint4 (&e1)[kCodedBuf], const uint4 *ent, int ng, int ngmax,
+                                             const unsigned char *win, unsigned row0, unsigned y0) {
+    unsigned y = row0 * 8u + y0;
+    for (int g0 = 0; g0 < ngmax; g0 += 2) {
+        coded_load(e1, ent, g0 + 1, ng);
+        coded_batch<MODE>(acc, y, e0, win);
+        coded_load(e0, ent, g0 + 2, ng);
+        coded_batch<MODE>(acc, y, e1, win);
+    }
+}
+
+// The two forms behind one interface (overloads on the buffer size): the
+// load of a region's first unit (four pairs or a group of 8), and the
+// region's sum, one unit's loads ahead of their use.
+__device__ __forceinline__ void region_start(uint4 (&e)[kPullUnroll], const uint4 *ent, int np) {
+    pull_load(e, ent, 0, np);
+}
+__device__ __forceinline__ void region_start(uint4 (&e)[kCodedBuf], const uint4 *ent, int ng) {
+    coded_load(e, ent, 0, ng);
+}
+template <int MODE>
+__device__ __forceinline__ void region_sum(typename PullAcc<MODE>::T &acc, uint4 (&e0)[kPullUnroll],
+                                           uint4 (&e1)[kPullUnroll], const uint4 *ent, int np, int npmax,
+                                           const unsigned char *win, unsigned row0, unsigned) {
+    pull_region<MODE>(acc, e0, e1, ent, np, npmax, win, row0);
+}
+template <int MODE>
+__device__ __forceinline__ void region_sum(typename PullAcc<MODE>::T &acc, uint4 (&e0)[kCodedBuf],
+                                           uint4 (&e1)[kCodedBuf], const uint4 *ent, int ng, int ngmax,
+                                           const unsigned char *win, unsigned row0, unsigned y0) {
+    coded_region<MODE>(acc, e0, e1, ent, ng, ngmax, win, row0, y0);
 }
 
 template <int MODE, bool CODED>
 __global__ void __launch_bounds__(kPullMaxBlock, 1) sparse_pull_kernel(NetArgs a) {
-    constexpr int DEPTH = kPullDepth;
     using V = typename Tr<MODE>::V;
     using Acc = typename PullAcc<MODE>::T;
     extern __shared__ uint4 s_win4[];                 // [hL][Wp] words
@@ -225,21 +227,21 @@ __global__ void __launch_bounds__(kPullMaxBlock, 1) sparse_pull_kernel(NetArgs a
     unsigned long long my_spikes = 0, my_events = 0;
     bool overflow = false;
     // synapse loads run one half (four pairs or a group of 8) ahead of their use
-    uint4 e[DEPTH][kUnitRegs<CODED>];
-    region_start<CODED, DEPTH>(e, ent, npA);
+    uint4 ea[CODED ? kCodedBuf : kPullUnroll], eb[CODED ? kCodedBuf : kPullUnroll];
+    region_start(ea, ent, npA);
     __syncthreads();
     // the delay >= 2 part of the first step: every row it reads is in the window
     Acc acc = 0;
     if (a.steps > 0) {
-        region_sum<MODE, CODED, DEPTH>(acc, e, ent, npA, npAmax, win, (unsigned)((a.t0 - base - D) * Wp) * 4u, yA);
-        region_start<CODED, DEPTH>(e, entB, npB);
+        region_sum<MODE>(acc, ea, eb, ent, npA, npAmax, win, (unsigned)((a.t0 - base - D) * Wp) * 4u, yA);
+        region_start(ea, entB, npB);
     }
     for (int s = 0; s < a.steps; ++s) {
         const int t = a.t0 + s;
         const unsigned row0 = (unsigned)((t - base - D) * Wp) * 4u;
         bool fire = false;
         // the delay-1 part: row t - 1 is in the window
-        region_sum<MODE, CODED, DEPTH>(acc, e, entB, npB, npBmax, win, row0, yB);
+        region_sum<MODE>(acc, ea, eb, entB, npB, npBmax, win, row0, yB);
         if (mine) {
             // input still pending in the ring from an earlier push run
             V ring_in = 0;
@@ -298,7 +300,7 @@ __global__ void __launch_bounds__(kPullMaxBlock, 1) sparse_pull_kernel(NetArgs a
         int stop_early = 0;
         if (threadIdx.x == 0 && gridDim.x == 1) stop_early = ld_status(a.ctl);
         // the first synapses of step t + 1 (the store is static)
-        region_start<CODED, DEPTH>(e, ent, npA);
+        region_start(ea, ent, npA);
         int pos = t - base;                           // window position of row t
         if (pos >= L) {
             // rows t-D+1 .. t-1 move down by sh = pos - D + 1 rows to positions
@@ -330,9 +332,8 @@ __global__ void __launch_bounds__(kPullMaxBlock, 1) sparse_pull_kernel(NetArgs a
         // window) while the other blocks arrive; then the first delay-1 loads
         acc = 0;
         if (s + 1 < a.steps) {
-            region_sum<MODE, CODED, DEPTH>(acc, e, ent, npA, npAmax, win,
-                                           (unsigned)((t + 1 - base - D) * Wp) * 4u, yA);
-            region_start<CODED, DEPTH>(e, entB, npB);
+            region_sum<MODE>(acc, ea, eb, ent, npA, npAmax, win, (unsigned)((t + 1 - base - D) * Wp) * 4u, yA);
+            region_start(ea, entB, npB);
         }
         if (threadIdx.x == 0) {
             s_ok = gridDim.x > 1 ? bar_wait(a.ctl, gen) : 1;
