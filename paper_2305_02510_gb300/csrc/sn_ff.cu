@@ -31,10 +31,13 @@
 namespace sn {
 
 constexpr int kFFDelays = 4;
+constexpr unsigned short kBf16One = 0x3f80;          // 1.0 in BF16
 
 // ---------------------------------------------------------------------------
-// input spikes (bytes) -> bit rows [T*B][words]
-__global__ void ff_pack_kernel(const uint8_t *in, int rows, int n, int words, unsigned *out) {
+// input spikes (bytes) -> bit rows [T*B][words], and, if sbf is given, BF16
+// rows [T*B][ldbf] (1 or 0; the tensor cores' spike operand)
+__global__ void ff_pack_kernel(const uint8_t *in, int rows, int n, int words, unsigned *out,
+                               unsigned short *sbf, int ldbf) {
     const int lane = threadIdx.x & 31;
     constexpr int kU = 4;                      // words per warp and iteration (loads in flight)
     const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -48,6 +51,7 @@ __global__ void ff_pack_kernel(const uint8_t *in, int rows, int n, int words, un
             const long long r = w / words;
             const int i = (int)(w - r * words) * 32 + lane;
             bit[u] = w < total && i < n && in[r * n + i] != 0;
+            if (sbf && w < total && i < n) sbf[r * ldbf + i] = bit[u] ? kBf16One : 0;
         }
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
@@ -141,7 +145,8 @@ __device__ __forceinline__ float ff_leak(float v, float lk, float rs) {
 
 __global__ void ff_scan_fwd_kernel(const float *__restrict__ I, int n, int words, int B, int T, int k,
                                    FFNeuron p, unsigned *__restrict__ S, float *__restrict__ vck,
-                                   int *__restrict__ rck, float *__restrict__ counts) {
+                                   int *__restrict__ rck, float *__restrict__ counts,
+                                   unsigned short *__restrict__ sbf, int ldbf) {
     const int lane = threadIdx.x & 31;
     const int per_b = words * 32;
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -177,6 +182,7 @@ __global__ void ff_scan_fwd_kernel(const float *__restrict__ I, int n, int words
         }
         const unsigned word = __ballot_sync(0xffffffffu, s);
         if (lane == 0) S[((size_t)t * B + b) * words + (j >> 5)] = word;
+        if (sbf && live) sbf[((size_t)t * B + b) * ldbf + j] = s ? kBf16One : 0;
         if (live && (t % k) == k - 1) {
             const size_t ci = ((size_t)(t / k) * B + b) * n + j;
             vck[ci] = v;
@@ -472,13 +478,14 @@ static int blocks_for(long long work, int per) {
     return (int)(b < 1 ? 1 : b);
 }
 
-cudaError_t ff_pack(const uint8_t *in, int rows, int n, int words, unsigned *out, cudaStream_t s) {
+cudaError_t ff_pack(const uint8_t *in, int rows, int n, int words, unsigned *out, void *sbf, int ldbf,
+                    cudaStream_t s) {
     const long long warps = (long long)rows * words;
     // a grid-stride loop over at most 2048 blocks (block launches, not
     // bandwidth, bound one word per warp)
     int nb = blocks_for(warps * 32 / 4, 256);
     nb = nb < 2048 ? nb : 2048;
-    ff_pack_kernel<<<nb, 256, 0, s>>>(in, rows, n, words, out);
+    ff_pack_kernel<<<nb, 256, 0, s>>>(in, rows, n, words, out, (unsigned short *)sbf, ldbf);
     return cudaGetLastError();
 }
 
@@ -491,11 +498,13 @@ cudaError_t ff_delay_fwd(const unsigned *sprev, int words_in, const float *W, co
 }
 
 cudaError_t ff_scan_fwd(const float *I, int n, int B, int T, int k, float theta, float leak, float reset,
-                        int refractory, unsigned *S, float *vck, int *rck, float *counts, cudaStream_t s) {
+                        int refractory, unsigned *S, float *vck, int *rck, float *counts, void *sbf, int ldbf,
+                        cudaStream_t s) {
     FFNeuron p{theta, leak, reset, 0.0f, refractory};
     const int words = (n + 31) / 32;
     const long long threads = (long long)B * words * 32;
-    ff_scan_fwd_kernel<<<blocks_for(threads, 256), 256, 0, s>>>(I, n, words, B, T, k, p, S, vck, rck, counts);
+    ff_scan_fwd_kernel<<<blocks_for(threads, 256), 256, 0, s>>>(I, n, words, B, T, k, p, S, vck, rck, counts,
+                                                                (unsigned short *)sbf, ldbf);
     return cudaGetLastError();
 }
 

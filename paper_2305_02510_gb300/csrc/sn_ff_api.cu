@@ -42,12 +42,14 @@ bool use_tc(const sn_ctx *c) { return c->ff_tc_ok && c->ff_engine != SN_FF_SIMT;
 // 4 delays x 3 exact BF16 weight parts (4 passes of 3 parts each), accumulated
 // block by block (ff_tc_forward).  Unpacks the previous layer's spikes, and their transpose
 // when the weight gradient will need it.
-sn_status tc_forward(sn_ctx *c, int l, bool want_st, float *I) {
+sn_status tc_forward(sn_ctx *c, int l, bool want_st, float *I, bool sbf_ready = false) {
     const int B = c->ff_batch, rows = B * c->ff_steps;
     const int nin = c->ff_sizes[l - 1], nout = c->ff_sizes[l];
     const int nin_p = up(nin, 64), rows_out = up(nout, 128), rows_p = up(rows, 64);
-    cudaError_t e = ff_tc_spikes(c->ff_S[l - 1], rows, nin, (nin + 31) / 32, nin_p, rows_p, c->ff_Sbf,
-                                 want_st ? c->ff_ST : nullptr, c->stream);
+    cudaError_t e = cudaSuccess;
+    if (!sbf_ready || want_st)
+        e = ff_tc_spikes(c->ff_S[l - 1], rows, nin, (nin + 31) / 32, nin_p, rows_p, sbf_ready ? nullptr : c->ff_Sbf,
+                         want_st ? c->ff_ST : nullptr, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "spike operands");
     FfTcMaps maps;
     FfTcArgs a;
@@ -339,10 +341,13 @@ sn_status sn_ff_forward(sn_ctx *c, const uint8_t *input, const float *const *w, 
         if (!w[l]) return fail(c, SN_EINVAL, "weight pointer is NULL");
     const int B = c->ff_batch, T = c->ff_steps, L = c->ff_layers;
     const int rows = B * T;
-    cudaError_t e = ff_pack(input, rows, c->ff_sizes[0], (c->ff_sizes[0] + 31) / 32, c->ff_S[0], c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "input pack");
     const bool tc = use_tc(c);
     c->ff_fwd_tc = tc;
+    // with the tensor cores, the input packing and each layer's recurrence
+    // also write the spikes as the next contraction's BF16 operand
+    cudaError_t e = ff_pack(input, rows, c->ff_sizes[0], (c->ff_sizes[0] + 31) / 32, c->ff_S[0],
+                            tc ? c->ff_Sbf : nullptr, up(c->ff_sizes[0], 64), c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "input pack");
     for (int l = 1; l <= L; ++l) {
         const int nin = c->ff_sizes[l - 1], nout = c->ff_sizes[l];
         float *I = c->ff_Ik.empty() ? c->ff_I : c->ff_Ik[l];
@@ -353,14 +358,15 @@ sn_status sn_ff_forward(sn_ctx *c, const uint8_t *input, const float *const *w, 
                                    l > 1 ? c->ff_Wb[l - 1] : nullptr, (nin + 63) / 64 * 64, (nout + 127) / 128 * 128,
                                    c->ff_Wf[l - 1], c->stream)))
                 return cuda_fail(c, e, "weight parts");
-            sn_status st = tc_forward(c, l, false, I);
+            sn_status st = tc_forward(c, l, false, I, true);
             if (st) return st;
         } else if ((e = ff_delay_fwd(c->ff_S[l - 1], (nin + 31) / 32, w[l - 1], c->ff_DM[l - 1], nin, nout, B, 0,
                                      rows, I, c->stream))) {
             return cuda_fail(c, e, "forward synaptic input");
         }
         if ((e = ff_scan_fwd(I, nout, B, T, c->ff_k, c->ff_theta, c->ff_leak, c->ff_reset, c->ff_refr,
-                             c->ff_S[l], c->ff_vck[l], c->ff_rck[l], l == L ? counts : nullptr, c->stream)))
+                             c->ff_S[l], c->ff_vck[l], c->ff_rck[l], l == L ? counts : nullptr,
+                             tc && l < L ? c->ff_Sbf : nullptr, up(nout, 64), c->stream)))
             return cuda_fail(c, e, "forward recurrence");
     }
     c->ff_have_forward = true;

@@ -151,11 +151,14 @@ size_t shared_smem_bytes();
 cudaError_t launch_shared_transpose(const int *src, int *dst, int n, int B, cudaStream_t s);
 
 // Feedforward (BPTT) kernels, sn_ff.cu
-cudaError_t ff_pack(const uint8_t *in, int rows, int n, int words, unsigned *out, cudaStream_t s);
+// sbf (may be null): the spikes also as BF16 rows of ldbf elements
+cudaError_t ff_pack(const uint8_t *in, int rows, int n, int words, unsigned *out, void *sbf, int ldbf,
+                    cudaStream_t s);
 cudaError_t ff_delay_fwd(const unsigned *sprev, int words_in, const float *W, const void *dm, int n_in,
                          int n_out, int B, int row0, int rows, float *I, cudaStream_t s);
 cudaError_t ff_scan_fwd(const float *I, int n, int B, int T, int k, float theta, float leak, float reset,
-                        int refractory, unsigned *S, float *vck, int *rck, float *counts, cudaStream_t s);
+                        int refractory, unsigned *S, float *vck, int *rck, float *counts, void *sbf, int ldbf,
+                        cudaStream_t s);
 cudaError_t ff_scan_bwd(const float *I, int n, int B, int T, int k, float theta, float leak, float reset,
                         int refractory, float slope, const float *vck, const int *rck, const float *gs,
                         const float *gc, float *gI, cudaStream_t s);
