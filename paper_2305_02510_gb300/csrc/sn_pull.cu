@@ -335,17 +335,18 @@ __global__ void __launch_bounds__(kPullMaxBlock, 1) sparse_pull_kernel(NetArgs a
             region_sum<MODE>(acc, ea, eb, ent, npA, npAmax, win, (unsigned)((t + 1 - base - D) * Wp) * 4u, yA);
             region_start(ea, entB, npB);
         }
-        if (threadIdx.x == 0) {
-            s_ok = gridDim.x > 1 ? bar_wait(a.ctl, gen) : 1;
-            s_stop = gridDim.x > 1 ? ld_status(a.ctl) : stop_early;
-        }
+        if (threadIdx.x == 0) s_ok = gridDim.x > 1 ? bar_wait(a.ctl, gen) : 1;
         __syncthreads();
         if (!s_ok) break;
-        // row t enters the window (a single block has put it in above)
+        // row t enters the window (a single block has put it in above); the
+        // status word is read while the row's loads are in flight
+        int st = stop_early;
         if (gridDim.x > 1) {
+            if (threadIdx.x == 0) st = ld_status(a.ctl);
             for (int i = threadIdx.x; i < W; i += blockDim.x)
                 s_win[(size_t)pos * Wp + i] = __ldcg(a.hist + (size_t)tD * W + i);
         }
+        if (threadIdx.x == 0) s_stop = st;
         __syncthreads();
         if (s_stop) break;
     }

@@ -263,7 +263,7 @@ def sn_create(threshold, leak, reset, refractory, pre, post, weight, delay, *, d
 
 
 def sn_create_shard(threshold, leak, reset, refractory, pre, post, weight, delay, first, count, *,
-                    dtype=SN_F32, max_delay=None, record_steps=0, stream=None) -> Ctx:
+                    dtype=SN_F32, max_delay=None, record_steps=0, stream=None, flags=SN_AUTO) -> Ctx:
     """Shard [first, first + count) of a sparse network (sn_create_shard)."""
     keep = []
     nr = _neurons(threshold, leak, reset, refractory, keep)
@@ -272,7 +272,7 @@ def sn_create_shard(threshold, leak, reset, refractory, pre, post, weight, delay
     sy.m = pre.size
     sy.pre, sy.post, sy.weight, sy.delay = _ptr(pre), _ptr(post), _ptr(w), _ptr(d)
     D = int(max_delay if max_delay is not None else (d.max() if d.size else 1))
-    cfg = _config(dtype, D, SN_AUTO, record_steps, stream)
+    cfg = _config(dtype, D, flags, record_steps, stream)
     h = _P()
     _check(lib().sn_create_shard(C.byref(cfg), C.byref(nr), C.byref(sy), int(first), int(count), C.byref(h)))
     return Ctx(h, nr.n, cfg.dtype, (nr.n + 31) // 32, "shard", pre.size)
@@ -302,12 +302,12 @@ def sn_shard_put_spikes(ctx: Ctx, t0: int, t1: int, bits):
     _check(lib().sn_shard_put_spikes(ctx.handle, int(t0), int(t1), _ptr(bits) if rows else None, dev), ctx)
 
 
-def from_workload_shard(wl, first, count, *, record_steps=None, stream=None) -> Ctx:
+def from_workload_shard(wl, first, count, *, record_steps=None, stream=None, flags=SN_AUTO) -> Ctx:
     """Shard [first, first + count) of a sparse workload dict, with its inputs."""
     rec = wl["steps"] if record_steps is None else record_steps
     ctx = sn_create_shard(wl["threshold"], wl["leak"], wl["reset"], wl["refractory"], wl["pre"], wl["post"],
                           wl["weight"], wl["delay"], first, count, dtype=wl["dtype"],
-                          max_delay=wl["max_delay"], record_steps=rec, stream=stream)
+                          max_delay=wl["max_delay"], record_steps=rec, stream=stream, flags=flags)
     ev = wl["events"]
     if len(ev["step"]):
         sn_set_input(ctx, ev["step"], ev["neuron"], ev["value"])

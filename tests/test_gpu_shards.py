@@ -132,9 +132,9 @@ def test_bptt_batch_shards_sum_to_whole_batch_gradient():
 # here one after another on one GPU with the rows exchanged on the host, must
 # reproduce the single pull context bit for bit.
 
-def run_network_shards(wl, world, steps):
+def run_network_shards(wl, world, steps, flags=0):
     from paper_2305_02510_gb300 import sn as S
-    ctxs = [S.from_workload_shard(wl, *shard.neuron_shard(wl["n"], r, world), record_steps=steps)
+    ctxs = [S.from_workload_shard(wl, *shard.neuron_shard(wl["n"], r, world), record_steps=steps, flags=flags)
             for r in range(world)]
     k = S.sn_shard_info(ctxs[0])[2]
     ranges = [shard.neuron_shard(wl["n"], r, world) for r in range(world)]
@@ -173,9 +173,12 @@ def run_network_shards(wl, world, steps):
     return raster, v, r, spikes, events, k
 
 
-@pytest.mark.parametrize("case,world", [("small-d2", 2), ("small-d2", 3), ("sparse-float", 2),
-                                        ("sparse-float", 4), ("sparse-int", 3)])
-def test_network_shards_equal_single_context(case, world):
+@pytest.mark.parametrize("case,world,form", [("small-d2", 2, 0), ("small-d2", 3, 0x2000), ("sparse-float", 2, 0),
+                                             ("sparse-float", 4, 0), ("sparse-float", 3, 0x2000),
+                                             ("sparse-int", 3, 0)])
+def test_network_shards_equal_single_context(case, world, form):
+    """form 0x2000 (SN_PULL_CODED): the shards hold the coded pull store, the
+    single context the plain one; the runs must still agree bit for bit."""
     from paper_2305_02510_gb300 import sn as S
     if case == "small-d2":
         wl = W.random_small(21, n=300, integer=False, steps=120, max_delay=5, p=0.05, events_rate=2.0)
@@ -184,7 +187,7 @@ def test_network_shards_equal_single_context(case, world):
     else:
         wl = W.large_sparse(integer=case == "sparse-int", n=20_000, steps=80)
         steps = 80
-    raster, v, r, spikes, events, k = run_network_shards(wl, world, steps)
+    raster, v, r, spikes, events, k = run_network_shards(wl, world, steps, flags=form)
     assert k == int(np.min(wl["delay"]))
     whole = S.from_workload(wl, flags=S.SN_PROP_PULL, record_steps=steps)
     S.sn_run(whole, steps)
