@@ -423,58 +423,54 @@ cudaError_t max_grid_sparse(int dtype, int stdp, int block, int *grid) {
 
 constexpr int kDListMax = 4096;                    // spikers held in shared memory
 
-// Spikers of a spike-bit row with rank in [lo, hi) (ascending neuron order).
-__device__ void extract_ranks(const unsigned *rrow, const int *wpre, int words, int lo, int hi,
-                              int *list) {
-    int a = 0, b = words;
-    while (a < b) {
-        const int mid = (a + b) >> 1;
-        if (wpre[mid + 1] <= lo) a = mid + 1; else b = mid;
+// Spike ranks of a spike-bit row in shared memory: each thread takes the
+// contiguous words [w0, w0 + per) and counts their spikes; an exclusive block
+// scan gives the rank (position in ascending neuron order) of the thread's
+// first spike.  Returns the row's spike count; two block barriers.
+struct RankSpan {
+    int w0, w1, base;
+};
+__device__ int block_spike_ranks(const unsigned *bits, int words, int *s_scan, RankSpan &sp) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int per = (words + blockDim.x - 1) / blockDim.x;
+    sp.w0 = min(words, (int)threadIdx.x * per);
+    sp.w1 = min(words, sp.w0 + per);
+    int c = 0;
+    for (int w = sp.w0; w < sp.w1; ++w) c += __popc(bits[w]);
+    int incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
     }
-    for (int w = a + threadIdx.x; w < words && wpre[w] < hi; w += blockDim.x) {
-        unsigned bits = rrow[w];
-        int rank = wpre[w];
-        while (bits) {
-            const int bpos = __ffs(bits) - 1;
-            bits &= bits - 1u;
+    if (lane == 31) s_scan[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int v = lane < nw ? s_scan[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += y;
+        }
+        if (lane < nw) s_scan[lane] = v;
+    }
+    __syncthreads();
+    sp.base = (warp ? s_scan[warp - 1] : 0) + incl - c;
+    return s_scan[nw - 1];
+}
+
+// The spikers of this thread's words with rank in [lo, hi) into list[rank - lo].
+__device__ __forceinline__ void emit_ranks(const unsigned *bits, const RankSpan &sp, int lo, int hi, int *list) {
+    int rank = sp.base;
+    for (int w = sp.w0; w < sp.w1 && rank < hi; ++w) {
+        unsigned b = bits[w];
+        while (b) {
+            const int bpos = __ffs(b) - 1;
+            b &= b - 1u;
             if (rank >= lo && rank < hi) list[rank - lo] = w * 32 + bpos;
             ++rank;
         }
     }
-}
-
-// Block-wide exclusive prefix of the popcounts of a spike-bit row into wpre
-// (words + 1 entries; wpre[words] = total).
-__device__ void popcount_prefix(const unsigned *row, int words, int *wpre, int *s_scan) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    int run = 0;
-    for (int w0 = 0; w0 < words; w0 += blockDim.x) {
-        const int w = w0 + threadIdx.x;
-        const int c = w < words ? __popc(row[w]) : 0;
-        int incl = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane == 31) s_scan[warp] = incl;
-        __syncthreads();
-        if (warp == 0) {
-            int v = lane < nw ? s_scan[lane] : 0;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, v, o);
-                if (lane >= o) v += y;
-            }
-            if (lane < nw) s_scan[lane] = v;
-        }
-        __syncthreads();
-        if (w < words) wpre[w] = run + (warp ? s_scan[warp - 1] : 0) + incl - c;
-        run += s_scan[nw - 1];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) wpre[words] = run;
-    __syncthreads();
 }
 
 // Vector gather of one list chunk (no STDP; n % 4 == 0 and W 16-byte aligned).
@@ -546,12 +542,11 @@ __global__ void __launch_bounds__(kBlock, CPL <= 2 ? 4 : 3) dense_kernel(NetArgs
     constexpr int cw = 32 * CPL;
     constexpr int nwarp = kBlock / 32;
     using Gm = VecGeom<CPL>;
-    int *wpre = smem;                                  // [words + 1]
-    int *list = smem + a.words + 1;                    // [kDListMax]
+    int *list = smem;                                  // [kDListMax]
     // the spike-bit row of the step, read once from global memory
-    unsigned *s_bits = (unsigned *)(smem + a.words + 1 + kDListMax);   // [words]
+    unsigned *s_bits = (unsigned *)(smem + kDListMax);  // [words]
     // [nwarp][cw], vector path [nwarp][RPI][cw]; 16-byte aligned
-    float *wpart = (float *)(smem + ((2 * a.words + 1 + kDListMax + 3) & ~3));
+    float *wpart = (float *)(smem + ((a.words + kDListMax + 3) & ~3));
     __shared__ int s_scan[kBlock / 32];
     __shared__ int s_stop;
     __shared__ float s_x[STDP ? kBlock : 1];           // pre-step traces of the slab's neurons
@@ -638,8 +633,8 @@ __global__ void __launch_bounds__(kBlock, CPL <= 2 ? 4 : 3) dense_kernel(NetArgs
             __syncthreads();
         }
         const unsigned *row_bits = s_bits;
-        popcount_prefix(row_bits, a.words, wpre, s_scan);
-        const int k = wpre[a.words];
+        RankSpan span;
+        const int k = block_spike_ranks(row_bits, a.words, s_scan, span);
         const float *xo = STDP ? a.trace + (size_t)((t + 2) % 3) * n : nullptr;   // x(t-1)
         float acc[CPL];
         bool sc[CPL];
@@ -658,7 +653,7 @@ __global__ void __launch_bounds__(kBlock, CPL <= 2 ? 4 : 3) dense_kernel(NetArgs
         for (int base = 0; base < k; base += kDListMax) {
             const int cnt = min(kDListMax, k - base);
             __syncthreads();
-            extract_ranks(row_bits, wpre, a.words, base, base + cnt, list);
+            emit_ranks(row_bits, span, base, base + cnt, list);
             __syncthreads();
             int r = warp;
             if constexpr (VEC) {
@@ -834,12 +829,12 @@ cudaError_t launch_barrier_selftest(Control *ctl, int blocks, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// Shared memory of a dense block: spike-count prefix, list chunk, warp
+// Shared memory of a dense block: list chunk, the step's spike-bit row, warp
 // partials (the vector path keeps RPI partials per warp: at most 4 * 32 * 4 B
 // per warp for any CPL, as much as CPL = 4's scalar partials).
 static size_t dense_smem(int words, int cpl) {
     const size_t part = (size_t)(kBlock / 32) * 32 * (cpl > 4 ? cpl : 4) * sizeof(float);
-    return (size_t)((2 * words + 1 + kDListMax + 3) & ~3) * sizeof(int) + part;
+    return (size_t)((words + kDListMax + 3) & ~3) * sizeof(int) + part;
 }
 
 // vec: the vector gather (no STDP, n % 4 == 0, W 16-byte aligned)
