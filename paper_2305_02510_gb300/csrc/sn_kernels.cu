@@ -423,20 +423,25 @@ cudaError_t max_grid_sparse(int dtype, int stdp, int block, int *grid) {
 
 constexpr int kDListMax = 4096;                    // spikers held in shared memory
 
-// Spike ranks of a spike-bit row in shared memory: each thread takes the
-// contiguous words [w0, w0 + per) and counts their spikes; an exclusive block
-// scan gives the rank (position in ascending neuron order) of the thread's
-// first spike.  Returns the row's spike count; two block barriers.
+// Spike ranks of a spike-bit row: each thread copies the contiguous words
+// [w0, w0 + per) from global memory into the shared copy `bits` and counts
+// their spikes; an exclusive block scan gives the rank (position in ascending
+// neuron order) of the thread's first spike.  Returns the row's spike count;
+// two block barriers, after which the whole shared copy is visible.
 struct RankSpan {
     int w0, w1, base;
 };
-__device__ int block_spike_ranks(const unsigned *bits, int words, int *s_scan, RankSpan &sp) {
+__device__ int block_spike_ranks(const unsigned *g_bits, unsigned *bits, int words, int *s_scan, RankSpan &sp) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int per = (words + blockDim.x - 1) / blockDim.x;
     sp.w0 = min(words, (int)threadIdx.x * per);
     sp.w1 = min(words, sp.w0 + per);
     int c = 0;
-    for (int w = sp.w0; w < sp.w1; ++w) c += __popc(bits[w]);
+    for (int w = sp.w0; w < sp.w1; ++w) {
+        const unsigned b = g_bits[w];
+        bits[w] = b;
+        c += __popc(b);
+    }
     int incl = c;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -627,14 +632,9 @@ __global__ void __launch_bounds__(kBlock, CPL <= 2 ? 4 : 3) dense_kernel(NetArgs
         if (!grid_barrier(a.ctl)) break;
 
         // ---- gather(t): input of t + delay (and STDP of step t)
-        {
-            const unsigned *g_bits = a.spk + (size_t)(t & 1) * a.words;
-            for (int w = threadIdx.x; w < a.words; w += blockDim.x) s_bits[w] = g_bits[w];
-            __syncthreads();
-        }
         const unsigned *row_bits = s_bits;
         RankSpan span;
-        const int k = block_spike_ranks(row_bits, a.words, s_scan, span);
+        const int k = block_spike_ranks(a.spk + (size_t)(t & 1) * a.words, s_bits, a.words, s_scan, span);
         const float *xo = STDP ? a.trace + (size_t)((t + 2) % 3) * n : nullptr;   // x(t-1)
         float acc[CPL];
         bool sc[CPL];
