@@ -61,6 +61,14 @@ __device__ __forceinline__ unsigned bar_arrive(Control *ctl) {
     return (old / gridDim.x + 1u) * gridDim.x;
 }
 
+// Arrival at the k-th barrier of a launch (k = 0, 1, ...): the target is
+// (k + 1) * gridDim.x, so the add is issued without waiting for its return
+// (one round trip fewer before the arriving block starts polling).
+__device__ __forceinline__ unsigned bar_arrive_k(Control *ctl, unsigned k) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], 1;" : : "l"(&ctl->bar.count) : "memory");
+    return (k + 1u) * gridDim.x;
+}
+
 // Thread 0: wait until the count reaches `target` (bounded: wall-clock limit,
 // or a status latched by another block).  Returns false if it gave up.
 __device__ __forceinline__ bool bar_wait(Control *ctl, unsigned target) {

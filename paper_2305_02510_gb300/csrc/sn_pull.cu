@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(kPullMaxBlock, 1) sparse_pull_kernel(NetArgs a
         // grid barrier, split: arrive, do this block's independent work, wait
         __syncthreads();                              // every warp's words of step t are stored
         unsigned gen = 0;
-        if (threadIdx.x == 0 && gridDim.x > 1) gen = bar_arrive(a.ctl);
+        if (threadIdx.x == 0 && gridDim.x > 1) gen = bar_arrive_k(a.ctl, (unsigned)s);
         // a single block reads the status word now, so that the read overlaps
         // the work below (a grid reads it after the barrier)
         int stop_early = 0;
