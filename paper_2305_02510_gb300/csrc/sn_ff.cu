@@ -143,10 +143,25 @@ __device__ __forceinline__ float ff_leak(float v, float lk, float rs) {
     return rs;
 }
 
-__global__ void ff_scan_fwd_kernel(const float *__restrict__ I, int n, int words, int B, int T, int k,
-                                   FFNeuron p, unsigned *__restrict__ S, float *__restrict__ vck,
-                                   int *__restrict__ rck, float *__restrict__ counts,
+// The inputs of a thread's next kScanChunk steps are copied into its own
+// column of a shared-memory buffer by asynchronous 4-byte copies, one chunk
+// ahead of their use (they do not depend on the recurrence): up to
+// 2 * kScanChunk loads of a thread in flight without holding registers.
+constexpr int kScanChunk = 16;
+constexpr int kScanBlock = 256;
+
+__device__ __forceinline__ void cp_async4(float *dst, const float *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n"
+                 :: "r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+__global__ void __launch_bounds__(kScanBlock) ff_scan_fwd_kernel(const float *__restrict__ I, int n, int words,
+                                   int B, int T, int k, FFNeuron p, unsigned *__restrict__ S,
+                                   float *__restrict__ vck, int *__restrict__ rck, float *__restrict__ counts,
                                    unsigned short *__restrict__ sbf, int ldbf) {
+    __shared__ float sI[2][kScanChunk][kScanBlock];
     const int lane = threadIdx.x & 31;
     const int per_b = words * 32;
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -157,36 +172,54 @@ __global__ void ff_scan_fwd_kernel(const float *__restrict__ I, int n, int words
     float v = p.reset;
     int r = 0;
     float cnt = 0.0f;
-    // the inputs of the next kPre steps are loaded ahead (they do not depend
-    // on the recurrence; 16 ahead measured slower than 4)
-    constexpr int kPre = 4;
     const size_t stride = (size_t)B * n;
     const float *Ip = I + (size_t)b * n + j;
-    float ahead[kPre];
-#pragma unroll
-    for (int q = 0; q < kPre; ++q) ahead[q] = (live && q < T) ? __ldg(Ip + (size_t)q * stride) : 0.0f;
-    for (int t0 = 0; t0 < T; t0 += kPre)
-#pragma unroll
-    for (int q = 0; q < kPre; ++q) {
-        const int t = t0 + q;
-        if (t >= T) break;
-        const float in = ahead[q];
-        ahead[q] = (live && t + kPre < T) ? __ldg(Ip + (size_t)(t + kPre) * stride) : 0.0f;
-        bool s = false;
-        if (live) {
-            const float u = __fadd_rn(ff_leak(v, p.leak, p.reset), in);
-            s = (u > p.theta) && (r == 0);
-            if (s) { v = p.reset; r = p.refractory; }
-            else { v = u; if (r > 0) r -= 1; }
-            if (s) cnt += 1.0f;
-        }
-        const unsigned word = __ballot_sync(0xffffffffu, s);
-        if (lane == 0) S[((size_t)t * B + b) * words + (j >> 5)] = word;
-        if (sbf && live) sbf[((size_t)t * B + b) * ldbf + j] = s ? kBf16One : 0;
-        if (live && (t % k) == k - 1) {
-            const size_t ci = ((size_t)(t / k) * B + b) * n + j;
-            vck[ci] = v;
-            rck[ci] = r;
+    // chunk c of steps [c * kScanChunk, ...) into buffer c & 1; an empty
+    // group past the last step keeps the wait count uniform
+    auto issue = [&](int c) {
+        const int t0 = c * kScanChunk;
+        if (live)
+            for (int q = 0; q < kScanChunk && t0 + q < T; ++q)
+                cp_async4(&sI[c & 1][q][threadIdx.x], Ip + (size_t)(t0 + q) * stride);
+        cp_async_commit();
+    };
+    issue(0);
+    // output pointers advance by one step's row (the per-step index
+    // arithmetic was most of the loop's instructions)
+    unsigned *Sp = S + (size_t)b * words + (j >> 5);
+    const size_t s_step = (size_t)B * words;
+    unsigned short *bp = sbf ? sbf + (size_t)b * ldbf + j : nullptr;
+    const size_t b_step = (size_t)B * ldbf;
+    float *vp = vck + (size_t)b * n + j;
+    int *rp = rck + (size_t)b * n + j;
+    int until_ck = k;                                  // steps to the next checkpoint
+    for (int c = 0; c * kScanChunk < T; ++c) {
+        issue(c + 1);
+        cp_async_wait_prev();                          // chunk c has landed (each thread reads its own copies)
+        const int qn = min(kScanChunk, T - c * kScanChunk);
+        for (int q = 0; q < qn; ++q) {
+            bool s = false;
+            if (live) {
+                const float in = sI[c & 1][q][threadIdx.x];
+                const float u = __fadd_rn(ff_leak(v, p.leak, p.reset), in);
+                s = (u > p.theta) && (r == 0);
+                if (s) { v = p.reset; r = p.refractory; }
+                else { v = u; if (r > 0) r -= 1; }
+                if (s) cnt += 1.0f;
+            }
+            const unsigned word = __ballot_sync(0xffffffffu, s);
+            if (lane == 0) *Sp = word;
+            Sp += s_step;
+            if (bp) {
+                if (live) *bp = s ? kBf16One : 0;
+                bp += b_step;
+            }
+            if (--until_ck == 0) {
+                until_ck = k;
+                if (live) { *vp = v; *rp = r; }
+                vp += stride;
+                rp += stride;
+            }
         }
     }
     if (live && counts) counts[(size_t)b * n + j] = cnt;
@@ -264,7 +297,8 @@ __global__ void __launch_bounds__(128) ff_scan_bwd_kernel(const float *__restric
             if (t >= T) continue;
             const float x = fabsf(u[q] - p.theta);
             const float den = 1.0f + p.slope * x;
-            const float sur = mk[q] ? 1.0f / (den * den) : 0.0f;
+            // 1 / den^2, correctly rounded (the same value as the division)
+            const float sur = mk[q] ? __frcp_rn(__fmul_rn(den, den)) : 0.0f;
             const float gu = (sp[q] ? 0.0f : gv) + Gc[q] * sur;
             gI[((size_t)t * B + b) * n + j] = gu;
             const float dv = vprev[q] - p.reset;
@@ -503,7 +537,7 @@ cudaError_t ff_scan_fwd(const float *I, int n, int B, int T, int k, float theta,
     FFNeuron p{theta, leak, reset, 0.0f, refractory};
     const int words = (n + 31) / 32;
     const long long threads = (long long)B * words * 32;
-    ff_scan_fwd_kernel<<<blocks_for(threads, 256), 256, 0, s>>>(I, n, words, B, T, k, p, S, vck, rck, counts,
+    ff_scan_fwd_kernel<<<blocks_for(threads, kScanBlock), kScanBlock, 0, s>>>(I, n, words, B, T, k, p, S, vck, rck, counts,
                                                                 (unsigned short *)sbf, ldbf);
     return cudaGetLastError();
 }
