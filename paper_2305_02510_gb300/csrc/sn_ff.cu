@@ -229,50 +229,61 @@ __global__ void __launch_bounds__(kScanBlock) ff_scan_fwd_kernel(const float *__
 // to the first; each is recomputed from its checkpoint (u kept in registers),
 // then walked backwards.  gs = gradient w.r.t. the layer's spikes: per step
 // ([T][B][n]) or, for the output layer, the count gradient gc [B][n] that
-// every step shares.  A segment's loads (checkpoint, inputs, spike
-// gradients) do not depend on the adjoint, so those of segment sg - 1 are in
-// flight while segment sg is computed.
-template <int K>
-__device__ __forceinline__ void ff_bwd_load(const float *__restrict__ I, const float *__restrict__ vck,
-                                            const int *__restrict__ rck, const float *__restrict__ gs,
-                                            float gcount, int n, int B, int T, int b, int j, int sg,
-                                            float reset, float (&Ix)[K], float (&Gx)[K], float &v0, int &r0) {
-    const int t0 = sg * K;
-    v0 = reset;
-    r0 = 0;
-    if (sg > 0) {
-        const size_t q = ((size_t)(sg - 1) * B + b) * n + j;
-        v0 = __ldg(vck + q);
-        r0 = __ldg(rck + q);
-    }
-#pragma unroll
-    for (int q = 0; q < K; ++q) {
-        const int t = t0 + q;
-        const size_t o = ((size_t)t * B + b) * n + j;
-        Ix[q] = t < T ? __ldg(I + o) : 0.0f;
-        Gx[q] = gs ? (t < T ? __ldg(gs + o) : 0.0f) : gcount;
-    }
-}
+// every step shares.  A segment's inputs and spike gradients do not depend on
+// the adjoint: those of segment sg - 1 are copied into the thread's own
+// column of a shared-memory buffer (asynchronous 4-byte copies) while segment
+// sg is computed, and its checkpoint is loaded into registers.
+constexpr int kBwdBlock = 128;
 
 template <int K>
-__global__ void __launch_bounds__(128) ff_scan_bwd_kernel(const float *__restrict__ I, int n, int B, int T, FFNeuron p,
-                                   const float *__restrict__ vck, const int *__restrict__ rck,
+__global__ void __launch_bounds__(kBwdBlock) ff_scan_bwd_kernel(const float *__restrict__ I, int n, int B, int T,
+                                   FFNeuron p, const float *__restrict__ vck, const int *__restrict__ rck,
                                    const float *__restrict__ gs, const float *__restrict__ gc,
                                    float *__restrict__ gI) {
+    __shared__ float sI[2][K][kBwdBlock], sG[2][K][kBwdBlock];
     const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (tid >= (long long)B * n) return;
     const int b = (int)(tid / n), j = (int)(tid - (long long)(tid / n) * n);
     const int segs = (T + K - 1) / K;
     const float gcount = gc ? gc[(size_t)b * n + j] : 0.0f;
-    float gv = 0.0f;
-    float Ic[K], Gc[K], vc;
+    const size_t stride = (size_t)B * n;
+    const float *Ib = I + (size_t)b * n + j;
+    const float *Gb = gs ? gs + (size_t)b * n + j : nullptr;
+    float *gIb = gI + (size_t)b * n + j;
+    // segment sg's inputs (and spike gradients) into buffer sg & 1; an empty
+    // group before the first segment keeps the wait count uniform
+    auto issue = [&](int sg) {
+        if (sg >= 0) {
+            const int t0 = sg * K;
+            for (int q = 0; q < K && t0 + q < T; ++q) {
+                cp_async4(&sI[sg & 1][q][threadIdx.x], Ib + (size_t)(t0 + q) * stride);
+                if (Gb) cp_async4(&sG[sg & 1][q][threadIdx.x], Gb + (size_t)(t0 + q) * stride);
+            }
+        }
+        cp_async_commit();
+    };
+    // checkpoint of segment sg: the state after step sg * K - 1
+    auto ckpt = [&](int sg, float &v0, int &r0) {
+        v0 = p.reset;
+        r0 = 0;
+        if (sg > 0) {
+            const size_t q = ((size_t)(sg - 1) * B + b) * n + j;
+            v0 = __ldg(vck + q);
+            r0 = __ldg(rck + q);
+        }
+    };
+    float gv = 0.0f, vc;
     int rc;
-    ff_bwd_load<K>(I, vck, rck, gs, gcount, n, B, T, b, j, segs - 1, p.reset, Ic, Gc, vc, rc);
+    issue(segs - 1);
+    ckpt(segs - 1, vc, rc);
     for (int sg = segs - 1; sg >= 0; --sg) {
         const int t0 = sg * K;
-        float In[K], Gn[K], vn = p.reset;
+        issue(sg - 1);
+        float vn = p.reset;
         int rn = 0;
-        if (sg > 0) ff_bwd_load<K>(I, vck, rck, gs, gcount, n, B, T, b, j, sg - 1, p.reset, In, Gn, vn, rn);
+        if (sg > 0) ckpt(sg - 1, vn, rn);
+        cp_async_wait_prev();                          // segment sg has landed (own copies)
+        const int buf = sg & 1;
         float v = vc;
         int r = rc;
         float u[K], vprev[K];
@@ -282,7 +293,7 @@ __global__ void __launch_bounds__(128) ff_scan_bwd_kernel(const float *__restric
             const int t = t0 + q;
             vprev[q] = v;
             if (t < T) {
-                u[q] = __fadd_rn(ff_leak(v, p.leak, p.reset), Ic[q]);
+                u[q] = __fadd_rn(ff_leak(v, p.leak, p.reset), sI[buf][q][threadIdx.x]);
                 mk[q] = (r == 0);
                 sp[q] = (u[q] > p.theta) && mk[q];
                 if (sp[q]) { v = p.reset; r = p.refractory; }
@@ -299,13 +310,12 @@ __global__ void __launch_bounds__(128) ff_scan_bwd_kernel(const float *__restric
             const float den = 1.0f + p.slope * x;
             // 1 / den^2, correctly rounded (the same value as the division)
             const float sur = mk[q] ? __frcp_rn(__fmul_rn(den, den)) : 0.0f;
-            const float gu = (sp[q] ? 0.0f : gv) + Gc[q] * sur;
-            gI[((size_t)t * B + b) * n + j] = gu;
+            const float g = Gb ? sG[buf][q][threadIdx.x] : gcount;
+            const float gu = (sp[q] ? 0.0f : gv) + g * sur;
+            gIb[(size_t)t * stride] = gu;
             const float dv = vprev[q] - p.reset;
             gv = (fabsf(dv) > p.leak) ? gu : 0.0f;
         }
-#pragma unroll
-        for (int q = 0; q < K; ++q) { Ic[q] = In[q]; Gc[q] = Gn[q]; }
         vc = vn;
         rc = rn;
     }
@@ -547,13 +557,13 @@ cudaError_t ff_scan_bwd(const float *I, int n, int B, int T, int k, float theta,
                         const float *gc, float *gI, cudaStream_t s) {
     FFNeuron p{theta, leak, reset, slope, refractory};
     const long long threads = (long long)B * n;
-    const int nb = blocks_for(threads, 128);
+    const int nb = blocks_for(threads, kBwdBlock);
     switch (k) {
-        case 1: ff_scan_bwd_kernel<1><<<nb, 128, 0, s>>>(I, n, B, T, p, vck, rck, gs, gc, gI); break;
-        case 2: ff_scan_bwd_kernel<2><<<nb, 128, 0, s>>>(I, n, B, T, p, vck, rck, gs, gc, gI); break;
-        case 5: ff_scan_bwd_kernel<5><<<nb, 128, 0, s>>>(I, n, B, T, p, vck, rck, gs, gc, gI); break;
-        case 10: ff_scan_bwd_kernel<10><<<nb, 128, 0, s>>>(I, n, B, T, p, vck, rck, gs, gc, gI); break;
-        case 20: ff_scan_bwd_kernel<20><<<nb, 128, 0, s>>>(I, n, B, T, p, vck, rck, gs, gc, gI); break;
+        case 1: ff_scan_bwd_kernel<1><<<nb, kBwdBlock, 0, s>>>(I, n, B, T, p, vck, rck, gs, gc, gI); break;
+        case 2: ff_scan_bwd_kernel<2><<<nb, kBwdBlock, 0, s>>>(I, n, B, T, p, vck, rck, gs, gc, gI); break;
+        case 5: ff_scan_bwd_kernel<5><<<nb, kBwdBlock, 0, s>>>(I, n, B, T, p, vck, rck, gs, gc, gI); break;
+        case 10: ff_scan_bwd_kernel<10><<<nb, kBwdBlock, 0, s>>>(I, n, B, T, p, vck, rck, gs, gc, gI); break;
+        case 20: ff_scan_bwd_kernel<20><<<nb, kBwdBlock, 0, s>>>(I, n, B, T, p, vck, rck, gs, gc, gI); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
