@@ -77,6 +77,20 @@ __device__ __forceinline__ void pull_batch(typename PullAcc<MODE>::T &acc, const
     }
 }
 
+// The pairs u < valid of a unit only (valid is the same for the whole warp);
+// for a region's last, partly used unit.
+template <int MODE>
+__device__ __forceinline__ void pull_batch_part(typename PullAcc<MODE>::T &acc, const uint4 (&e)[kPullUnroll],
+                                                const unsigned char *win, unsigned row0, int valid) {
+#pragma unroll
+    for (int u = 0; u < kPullUnroll; ++u) {
+        if (u < valid) {
+            pull_one<MODE>(acc, e[u].x, e[u].y, win, row0);
+            pull_one<MODE>(acc, e[u].z, e[u].w, win, row0);
+        }
+    }
+}
+
 __device__ __forceinline__ void pull_load(uint4 (&e)[kPullUnroll], const uint4 *ent, int p0, int np) {
 #pragma unroll
     for (int u = 0; u < kPullUnroll; ++u)
@@ -129,11 +143,22 @@ __device__ __forceinline__ void pull_region(typename PullAcc<MODE>::T &acc, uint
                                             uint4 (&e1)[kPullUnroll], const uint4 *ent, int np, int npmax,
                                             const unsigned char *win, unsigned row0) {
     constexpr int P = kPullUnroll;
-    for (int p0 = 0; p0 < npmax; p0 += 2 * P) {
+    int p0 = 0;
+    for (; p0 + 2 * P <= npmax; p0 += 2 * P) {
         pull_load(e1, ent, p0 + P, np);
         pull_batch<MODE>(acc, e0, win, row0);
         pull_load(e0, ent, p0 + 2 * P, np);
         pull_batch<MODE>(acc, e1, win, row0);
+    }
+    // the last pairs, fewer than 2P: only those before the warp's longest
+    // list's end are tested
+    const int rem = npmax - p0;
+    if (rem > P) {
+        pull_load(e1, ent, p0 + P, np);
+        pull_batch<MODE>(acc, e0, win, row0);
+        pull_batch_part<MODE>(acc, e1, win, row0, rem - P);
+    } else if (rem > 0) {
+        pull_batch_part<MODE>(acc, e0, win, row0, rem);
     }
 }
 
