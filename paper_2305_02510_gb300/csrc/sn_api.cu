@@ -144,13 +144,33 @@ sn_status build_pull_store(sn_ctx *c) {
         else lenc[r][j] += (int)std::max(1u, (y - ylast[(size_t)r * n + j] + 65534u) / 65535u);
         ylast[(size_t)r * n + j] = y;
     }
+    // Positions: thread p of the launch sums the lists of neuron perm[p].
+    // Within each block's range of neurons the lists are sorted longest
+    // first, so that the 32 lists of a warp have about the same length (the
+    // warp runs to its longest); the block hands each sum to the neuron's
+    // own thread through shared memory.  Neurons outside the simulated range
+    // (other shards') keep their own positions.
+    std::vector<int> perm(n), pos_of(n);
+    for (int j = 0; j < n; ++j) perm[j] = j;
+    {
+        const int j0 = c->shard_end ? c->shard_first : 0, j1 = c->shard_end ? c->shard_end : n;
+        const int chunk = std::max(c->pull_chunk, 32);
+        for (int b0 = j0; b0 < j1; b0 += chunk) {
+            const int b1 = std::min(j1, b0 + chunk);
+            std::stable_sort(perm.begin() + b0, perm.begin() + b1, [&](int x, int y) {
+                return len[0][x] + len[1][x] > len[0][y] + len[1][y];
+            });
+        }
+    }
+    for (int q = 0; q < n; ++q) pos_of[perm[q]] = q;
     const int slices = (n + 31) / 32;
     long long total[2] = {0, 0};                          // uint4s: plain, coded
     std::vector<long long> off[2] = {std::vector<long long>(slices), std::vector<long long>(slices)};
     std::vector<long long> offB[2] = {std::vector<long long>(slices), std::vector<long long>(slices)};
     for (int sl = 0; sl < slices; ++sl) {
         int LA[2] = {0, 0}, LB[2] = {0, 0};
-        for (int j = sl * 32; j < std::min(n, sl * 32 + 32); ++j) {
+        for (int q = sl * 32; q < std::min(n, sl * 32 + 32); ++q) {
+            const int j = perm[q];
             LA[0] = std::max(LA[0], len[0][j]);  LB[0] = std::max(LB[0], len[1][j]);
             LA[1] = std::max(LA[1], lenc[0][j]); LB[1] = std::max(LB[1], lenc[1][j]);
         }
@@ -175,9 +195,9 @@ sn_status build_pull_store(sn_ctx *c) {
     std::vector<int> fill[2] = {std::vector<int>(n, 0), std::vector<int>(n, 0)};
     for (long long k = 0; k < m; ++k) {
         const uint32_t p = byd[k];
-        const int j = (int)(syn[p].x & kPostMask), r = region_of(p), l = j & 31;
+        const int j = (int)(syn[p].x & kPostMask), r = region_of(p), ps = pos_of[j], l = ps & 31;
         const unsigned y = y_of(p);
-        const long long start = (r ? offB[f] : off[f])[j >> 5];
+        const long long start = (r ? offB[f] : off[f])[ps >> 5];
         if (f == 0) {
             const int q = fill[r][j]++;
             uint4 &u = pin[start + (long long)(q >> 1) * 32 + l];
@@ -208,15 +228,26 @@ sn_status build_pull_store(sn_ctx *c) {
     }
     if (!c->pin_off) {
         if ((s = dalloc(c, &c->pin_off, (size_t)slices * 8)) || (s = dalloc(c, &c->pin_len, (size_t)n * 4)) ||
-            (s = dalloc(c, &c->pin_len1, (size_t)n * 4)) || (s = dalloc(c, &c->pin_y0, (size_t)n * 8)))
+            (s = dalloc(c, &c->pin_len1, (size_t)n * 4)) || (s = dalloc(c, &c->pin_y0, (size_t)n * 8)) ||
+            (s = dalloc(c, &c->pin_perm, (size_t)n * 4)))
             return s;
     }
-    const std::vector<int> &lA = f ? lenc[0] : len[0], &lB = f ? lenc[1] : len[1];
+    // list lengths and first offsets by position
+    std::vector<int> lA(n), lB(n);
+    std::vector<unsigned> y0p(2 * (size_t)n);
+    for (int q = 0; q < n; ++q) {
+        const int j = perm[q];
+        lA[q] = (f ? lenc[0] : len[0])[j];
+        lB[q] = (f ? lenc[1] : len[1])[j];
+        y0p[q] = y0[j];
+        y0p[(size_t)n + q] = y0[(size_t)n + j];
+    }
     SN_CUDA(c, cudaMemcpy(c->pin, pin.data(), bytes, cudaMemcpyHostToDevice));
     SN_CUDA(c, cudaMemcpy(c->pin_off, off[f].data(), (size_t)slices * 8, cudaMemcpyHostToDevice));
     SN_CUDA(c, cudaMemcpy(c->pin_len, lA.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
     SN_CUDA(c, cudaMemcpy(c->pin_len1, lB.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
-    SN_CUDA(c, cudaMemcpy(c->pin_y0, y0.data(), (size_t)n * 8, cudaMemcpyHostToDevice));
+    SN_CUDA(c, cudaMemcpy(c->pin_y0, y0p.data(), (size_t)n * 8, cudaMemcpyHostToDevice));
+    SN_CUDA(c, cudaMemcpy(c->pin_perm, perm.data(), (size_t)n * 4, cudaMemcpyHostToDevice));
     c->pin_coded = f;
     c->pin_bytes = (long long)bytes;
     c->pin_entries = 0;
@@ -795,7 +826,7 @@ sn_status sn_run(sn_ctx *c, int32_t steps) {
             if (st) return st;
         }
         a.pin = c->pin; a.pin_off = c->pin_off; a.pin_len = c->pin_len; a.pin_len1 = c->pin_len1;
-        a.pin_y0 = c->pin_y0;
+        a.pin_y0 = c->pin_y0; a.pin_perm = c->pin_perm;
         a.ring_until = (int)std::min<long long>(c->ring_live_until, 2147483647ll);
         a.hL = c->pull_rows;
         a.chunk = c->pull_chunk;

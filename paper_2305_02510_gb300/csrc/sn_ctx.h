@@ -42,6 +42,7 @@ struct sn_ctx {
     int *pin_len = nullptr;            // synapses of delay >= 2 of each neuron
     int *pin_len1 = nullptr;           // synapses of delay 1 of each neuron
     unsigned *pin_y0 = nullptr;        // coded store: [2][n] bit offset of each region's first entry
+    int *pin_perm = nullptr;           // [n] the neuron whose lists thread position p sums
     size_t pin_cap = 0;                // bytes allocated for pin
     int pin_coded = 0;                 // 1: the store holds 16-bit offset steps (coded form)
     int pin_format = 0;                // 0 = the smaller of the two forms, 1 = plain, 2 = coded

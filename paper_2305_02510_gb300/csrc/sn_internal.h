@@ -73,6 +73,8 @@ struct NetArgs {
     const int *pin_len;               // [n] incoming synapses of delay >= 2 of each neuron
     const int *pin_len1;              // [n] incoming synapses of delay 1 (the region after them)
     const unsigned *pin_y0;           // coded store: [2][n] window bit offset of each region's first entry
+    const int *pin_perm;              // [n] the neuron whose lists thread position p sums (the store,
+                                      // pin_len, pin_len1 and pin_y0 are indexed by position)
     unsigned *hist;                   // [hD][words] spike bits of step tau in row tau % hD
     int hD;                           // history depth (the maximum delay D)
     int hL;                           // rows of the pull kernel's shared-memory window

@@ -217,6 +217,12 @@ __global__ void __launch_bounds__(kPullMaxBlock, 1) sparse_pull_kernel(NetArgs a
 
     const int j = a.j_first + blockIdx.x * a.chunk + threadIdx.x;
     const bool mine = j < a.j_end;
+    // this thread sums the lists of neuron pj (the store orders each block's
+    // neurons by list length) and hands the sum to pj's own thread through
+    // s_acc, which follows the window in shared memory
+    const int bfirst = a.j_first + blockIdx.x * a.chunk;
+    const int pj = mine ? a.pin_perm[j] : j;
+    Acc *s_acc = (Acc *)(s_win + (size_t)L * Wp);
     const int wbase = j - lane;                       // first neuron of this warp's slice
     V v = 0, th = 0, lk = 0, rs = 0, amp = 0;
     int rr = 0, R = 0, npA = 0, npB = 0;
@@ -267,6 +273,9 @@ __global__ void __launch_bounds__(kPullMaxBlock, 1) sparse_pull_kernel(NetArgs a
         bool fire = false;
         // the delay-1 part: row t - 1 is in the window
         region_sum<MODE>(acc, ea, eb, entB, npB, npBmax, win, row0, yB);
+        if (mine) s_acc[pj - bfirst] = acc;
+        __syncthreads();
+        const Acc sum = mine ? s_acc[threadIdx.x] : Acc(0);
         if (mine) {
             // input still pending in the ring from an earlier push run
             V ring_in = 0;
@@ -289,11 +298,11 @@ __global__ void __launch_bounds__(kPullMaxBlock, 1) sparse_pull_kernel(NetArgs a
                 if (MODE == SN_F32) ext = __fadd_rn(ext, amp); else ext = ext + amp;
             }
             if constexpr (MODE == SN_F32) {
-                const float in = t < a.ring_until ? __fadd_rn(acc, ring_in) : acc;
+                const float in = t < a.ring_until ? __fadd_rn(sum, ring_in) : sum;
                 fire = lif_update_f32(v, rr, in, ext, th, lk, rs, R);
             } else {
                 // the integrated state is checked against int32 before the threshold
-                const long long in = acc + (long long)ring_in;
+                const long long in = sum + (long long)ring_in;
                 long long u;
                 if (v > rs) { u = (long long)v - lk; u = u > rs ? u : rs; }
                 else if (v < rs) { u = (long long)v + lk; u = u < rs ? u : rs; }
@@ -459,14 +468,15 @@ cudaError_t plan_pull(int n, int D, long long m, int *grid, int *chunk, int *row
     const long long words = (n + 31) / 32, wp = (words + 3) & ~3ll;
     // one neuron per thread, at most one block per SM; a window of at least
     // D rows must fit a block's shared memory next to the few static words
-    const long long L = std::min<long long>((optin - 64) / (wp * 4), 1 << 14);
-    if (L < D) return cudaSuccess;
     // slices per block: spread over the SMs; a small network (at most 1024
     // neurons and 64 Ki synapses) runs as one block, without a grid barrier
     const long long sl = own_slices >= 0 ? own_slices : words;
     const long long per = (sl * 32 <= kPullMaxBlock && m <= 65536) ? sl : (sl + sms - 1) / sms;
     if (per * 32 > kPullMaxBlock) return cudaSuccess;
-    const long long bytes = L * wp * 4;
+    // the window rows, and after them one 8-byte sum per thread
+    const long long L = std::min<long long>((optin - 64 - per * 32 * 8) / (wp * 4), 1 << 14);
+    if (L < D) return cudaSuccess;
+    const long long bytes = L * wp * 4 + per * 32 * 8;
     const int block = (int)(per * 32);
     for (const void *fn : {pull_fn(SN_F32, false), pull_fn(SN_I32, false), pull_fn(SN_F32, true),
                            pull_fn(SN_I32, true)}) {
