@@ -809,6 +809,10 @@ def main():
         kernel = "sparse_pull_kernel<SN_F32>" if pull else "sparse_reg_kernel<SN_F32>"
         achieved = abytes / (ms / 1e3) / 1e9
         traffic, traffic_src = recorded_traffic(kernel, f"large-sparse T={T}")
+        store = None
+        if pull:
+            fmt, sbytes, sentries = S.sn_pull_store_info(ctx)
+            store = {"form": "coded" if fmt == S.SN_PULL_CODED else "plain", "bytes": sbytes, "entries": sentries}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_all, "higher_is_better": True, "scaling": "weak",
@@ -829,9 +833,10 @@ def main():
                          "bytes_model": "event-proportional: 16 B per spike (row bounds), 16 B per synaptic "
                                         "event (synapse + accumulate), 56 B state and a raster bit per "
                                         "neuron and timestep",
-                         "kernel_bound": ("l2+barrier: the pull store of incoming synapses (98 MB) stays in "
-                                          "the 129 MB L2; each timestep streams it from L2 once, then one grid "
-                                          "barrier")
+                         "pull_store": store,
+                         "kernel_bound": (f"l2+barrier: the pull store of incoming synapses "
+                                          f"({store['bytes'] / 1e6:.0f} MB) stays in the L2; each timestep "
+                                          f"streams it from L2 once, then one grid barrier")
                                          if pull else "l2 atomics: scattered accumulates into the pending-input "
                                                       "ring, L2-resident",
                          "form_bytes_per_launch": form_bytes,
