@@ -160,6 +160,11 @@ sn_status build_pull_store(sn_ctx *c) {
             std::stable_sort(perm.begin() + b0, perm.begin() + b1, [&](int x, int y) {
                 return len[0][x] + len[1][x] > len[0][y] + len[1][y];
             });
+            // then, within runs of two warps, by the delay-1 list (summed after
+            // the barrier, on the step's critical path)
+            for (int w0 = b0; w0 < b1; w0 += 64)
+                std::stable_sort(perm.begin() + w0, perm.begin() + std::min(b1, w0 + 64),
+                                 [&](int x, int y) { return len[1][x] > len[1][y]; });
         }
     }
     for (int q = 0; q < n; ++q) pos_of[perm[q]] = q;
