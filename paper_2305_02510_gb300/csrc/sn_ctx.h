@@ -39,8 +39,8 @@ struct sn_ctx {
     size_t pull_smem = 0;
     uint4 *pin = nullptr;              // incoming synapses in 32-neuron slices
     long long *pin_off = nullptr;
-    int *pin_len = nullptr;            // synapses of delay >= 2 of each neuron
-    int *pin_len1 = nullptr;           // synapses of delay 1 of each neuron
+    int *pin_len = nullptr;            // entries of delay >= 2 of each thread position's list
+    int *pin_len1 = nullptr;           // entries of delay 1 of each thread position's list
     unsigned *pin_y0 = nullptr;        // coded store: [2][n] bit offset of each region's first entry
     int *pin_perm = nullptr;           // [n] the neuron whose lists thread position p sums
     size_t pin_cap = 0;                // bytes allocated for pin

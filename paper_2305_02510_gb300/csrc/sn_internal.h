@@ -70,8 +70,8 @@ struct NetArgs {
     // (groups of 8 weights and 16-bit offset steps)
     const uint4 *pin;
     const long long *pin_off;         // [slices] first uint4 of each slice
-    const int *pin_len;               // [n] incoming synapses of delay >= 2 of each neuron
-    const int *pin_len1;              // [n] incoming synapses of delay 1 (the region after them)
+    const int *pin_len;               // [n] entries of delay >= 2 of each position's list
+    const int *pin_len1;              // [n] entries of delay 1 (the region after them)
     const unsigned *pin_y0;           // coded store: [2][n] window bit offset of each region's first entry
     const int *pin_perm;              // [n] the neuron whose lists thread position p sums (the store,
                                       // pin_len, pin_len1 and pin_y0 are indexed by position)

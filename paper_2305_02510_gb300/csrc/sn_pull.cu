@@ -4,13 +4,16 @@
 //
 // Every block keeps the spike bits of recent steps in a shared-memory window
 // of hL rows of Wp = roundup(ceil(n/32), 4) words: the row of step tau sits
-// at position tau - base.  Each thread owns one neuron, holds its state in
-// registers and walks the neuron's incoming synapses in descending delay,
-// then ascending pre and input index (the oldest spikes first), testing the
-// bit of pre at step t - d and adding the weight.  That bit lies
+// at position tau - base.  Each thread owns one neuron and holds its state in
+// registers; thread p of a block walks the incoming synapses of the block's
+// neuron pin_perm[p] (the host orders each block's neurons by list length, so
+// that a warp's 32 lists are about equally long: a warp runs to its longest)
+// in descending delay, then ascending pre and input index (the oldest spikes
+// first), testing the bit of pre at step t - d and adding the weight, and
+// hands the sum to that neuron's thread through shared memory.  That bit lies
 // y = (D - d) * Wp * 32 + pre bits after the row of step t - D, and y never
-// decreases along a neuron's list.  The synapses of 32 consecutive neurons
-// form a slice (one warp), stored in one of two forms (built on the host):
+// decreases along a list.  The lists of a slice of 32 thread positions (one
+// warp) are stored in one of two forms (built on the host):
 //  - plain, 8 bytes a synapse: x = (y / 32) << 7 | y % 32 and the weight bits;
 //    entry q of lane l sits in pair q / 2 of the slice, so that each 16-byte
 //    load of a warp reads 512 contiguous bytes; a test is one shift, one
@@ -31,8 +34,9 @@
 // synapses of delay >= 2 of step t + 1, which read rows up to t - 1 only; after
 // the wait it copies row t into the window and adds the synapses of delay 1.
 // The synapses of delay >= 2 and of delay 1 sit in two regions of the store,
-// so that both loops read whole 512-byte runs per warp.  The global history (row of step tau in slot tau % D) holds, between
-// runs, every spike of the last D steps whose deliveries are still due;
+// so that both loops read whole 512-byte runs per warp.  The global history
+// (row of step tau in slot tau % D) holds, between runs, every spike of the
+// last D steps whose deliveries are still due;
 // pull_flush_kernel turns them into pending ring input when the context
 // switches to push propagation.
 #include <cuda_runtime.h>
